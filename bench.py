@@ -1,0 +1,327 @@
+"""Benchmark: DOF/s of the multigrid-preconditioned CG solve to relative residual 1e-8.
+
+Workload (one "step" = one whole solve from x0 = 0, every hot-path step included):
+2-D Poisson on [0,1]^2 minus 10 seeded discs (r ~ U(0.03, 0.1)), 512 x 512 background
+grid, quadratic open B-splines, 6 levels, depth-0 cut cells, symmetric Nitsche on the
+immersed boundary, additive Schwarz smoothing, FP64 throughout.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  With N > 1 (torchrun) every rank solves its own seeded
+geometry (independent problems, no collective on the data path: weak scaling); the
+timed region is bracketed by barriers and the maximum over ranks is taken.
+The reference arm times the FP64 CPU oracle (the only other place this script runs it).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "DOF/s to rel. residual 1e-8 (PCG+MG) vs plain FP64 GPU; HBM GB/s of roofline"
+WORKLOAD = "poisson2d-512x512-10discs-bspline-p2-6levels-nitsche-fp64"
+PRESET = "discs10_512_p2"
+RTOL = 1e-8
+MAXIT = 2000
+FP64_PEAK_NOTE = "152 SMs x 2 FP64 FMA/clk x 2 flop x 2070 MHz"
+CPU_SAMPLE_N, CPU_SAMPLE_LEVELS = 128, 4
+
+
+def fp64_peak_tflops(sm_mhz: float = 2070.0) -> float:
+    return 152 * 2 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+# ------------------------------------------------------------------ CPU oracle leg
+_ORACLE_SCRIPT = r"""
+import json, sys, time
+sys.path.insert(0, {root!r})
+from oracle import discretize as D, geometry as G, multigrid as MG
+from synthetic import config_layout, preset
+pr = preset({preset!r}, n={n}, levels={levels})
+lay = config_layout(pr.layout, {seed})
+d = D.Discretization(G.Balls(lay.centers, lay.radii), pr.basis, pr.degree, pr.n, pr.depth, pr.bc)
+H = MG.Hierarchy(d, pr.levels)
+times, its = [], []
+for k in range({reps}):
+    t0 = time.perf_counter()
+    x, it, hist = MG.pcg(d.A, d.b, H.precondition, rtol={rtol}, maxit={maxit})
+    times.append(time.perf_counter() - t0)
+    its.append(it)
+print(json.dumps({{"n_active": int(d.n_active), "times": times, "iterations": its, "rel": hist[-1]}}))
+"""
+
+
+def run_oracle(reps: int, seed: int = 0):
+    """Oracle CG solve (setup excluded) on the 128 x 128 instance of the workload, single thread."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = _ORACLE_SCRIPT.format(root=ROOT, preset=PRESET, n=CPU_SAMPLE_N, levels=CPU_SAMPLE_LEVELS, seed=seed,
+                                 reps=reps, rtol=RTOL, maxit=MAXIT)
+    r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=1800)
+    if r.returncode != 0:
+        raise RuntimeError("oracle run failed: " + r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def cpu_baseline_entry(o):
+    t = statistics.median(o["times"])
+    return {"value": o["n_active"] / t, "unit": "DOF/s", "cores": 1, "kind": "oracle",
+            "sample": (f"FP64 CPU oracle (numpy/scipy, 1 thread) CG solve to 1e-8 of the {CPU_SAMPLE_N}x{CPU_SAMPLE_N} "
+                       f"instance of the same geometry ({CPU_SAMPLE_LEVELS} levels, {o['n_active']} DOFs, "
+                       f"{o['iterations'][0]} iterations), setup excluded; median of {len(o['times'])} solves"),
+            "host_cpus": os.cpu_count()}
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) >= 9 and f[1].isdigit():
+                    rows.append(f)
+        except Exception:
+            pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        sm = [int(r[1]) for r in rows]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() in ("active", "1")})
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": int(rows[0][2]), "reasons": reasons,
+                "samples": len(rows), "power_w_max": max(float(r[3]) for r in rows if r[3].replace('.', '', 1).isdigit())
+                if any(r[3].replace('.', '', 1).isdigit() for r in rows) else None}
+
+
+# ------------------------------------------------------------------ GPU arm
+def launches_per_solve(S, iterations: int) -> int:
+    per_level = 0
+    for l in range(2, S.L + 1):
+        per_level += 4 + (2 if S.level_info(l)["n_blocks"] > 0 else 0)
+    vcycle = per_level + 1
+    start = 3 + vcycle + 1 + 1
+    it = 5 + vcycle + 1
+    return start + iterations * it + 2
+
+
+def apply_flops(S) -> float:
+    """Algorithmic FP64 flops of one finest-level operator apply: 8(2p+1) per tensor row
+    (sum factorisation) + 2 (2p+1)^d per stored row."""
+    info = S.level_info(S.L)
+    p, d = S.p, S.dim
+    tensor_rows = info["n_active"] - info["n_band"]
+    return (8 * (2 * p + 1) if d == 2 else 16 * (2 * p + 1)) * tensor_rows + 2 * (2 * p + 1) ** d * info["n_band"]
+
+
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+
+    import paper_1903_10977_gb300 as lib
+    from synthetic import config_layout, preset
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    pr = preset(PRESET)
+    lay = config_layout(pr.layout, args.seed + rank)
+    t0 = time.perf_counter()
+    S = lib.Solver(pr.dim, lay.centers, lay.radii, pr.n, pr.degree, pr.levels, pr.depth, pr.bc, basis=pr.basis)
+    setup_s = time.perf_counter() - t0
+    info = S.level_info(S.L)
+    n_active, n_grid = info["n_active"], info["n_grid"]
+    b = S.rhs()
+    x = torch.zeros_like(b)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")   # > 129 MB L2
+    stream = torch.cuda.current_stream()
+
+    def step():
+        x.zero_()
+        _, res, _ = S.pcg_solve(b, x, rtol=RTOL, maxit=MAXIT)
+        return res
+
+    for _ in range(args.warmup):
+        res = step()
+    # timed region: each solve bracketed by events after an L2 flush
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    results = []
+    with ClockSampler(local_rank) as clk:
+        barrier()
+        wall0 = time.perf_counter()
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            x.zero_()
+            ev[k][0].record(stream)
+            _, res, _ = S.pcg_solve(b, x, rtol=RTOL, maxit=MAXIT)
+            ev[k][1].record(stream)
+            results.append(res)
+        barrier()
+        wall = time.perf_counter() - wall0
+    step_ms = [s.elapsed_time(e) for s, e in ev]
+    t_dev = sum(step_ms) / 1e3
+    clocks = clk.summary()
+
+    # end to end: host (pinned) b in, host x out, through the C-ABI
+    bh = torch.empty(n_grid, dtype=torch.float64, pin_memory=True)
+    bh.copy_(b.cpu())
+    xh = torch.empty(n_grid, dtype=torch.float64, pin_memory=True)
+    for _ in range(max(1, args.warmup // 2)):
+        S.pcg_solve_host_ptr(bh.data_ptr(), xh.data_ptr(), rtol=RTOL, maxit=MAXIT)
+    barrier()
+    e0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        torch.cuda.synchronize()
+        S.pcg_solve_host_ptr(bh.data_ptr(), xh.data_ptr(), rtol=RTOL, maxit=MAXIT)
+    barrier()
+    t_e2e = time.perf_counter() - e0
+
+    # dominant kernel: finest-level operator apply, timed alone with events on its stream
+    xs = torch.randn(n_grid, dtype=torch.float64, device="cuda") * torch.as_tensor(
+        S.active_mask(), dtype=torch.float64, device="cuda")
+    ys = torch.empty_like(xs)
+    for _ in range(5):
+        S.apply_operator(xs, ys)
+    reps = 200
+    k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("finest_apply_timing")      # lets ncu select these launches
+    k0.record(stream)
+    for _ in range(reps):
+        S.apply_operator(xs, ys)
+    k1.record(stream)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
+    apply_ms = k0.elapsed_time(k1) / reps
+
+    if dist is not None:
+        t = torch.tensor([t_dev, t_e2e, wall], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_dev, t_e2e, wall = (float(v) for v in t.tolist())
+        dist.destroy_process_group()
+    if rank != 0:
+        return None
+    total_units = n_active * args.steps * world
+    value = total_units / t_dev
+    its = [r["iterations"] for r in results]
+    flops = apply_flops(S)
+    achieved = flops / (apply_ms * 1e-3) / 1e12
+    peak = fp64_peak_tflops()
+    line = {
+        "metric": METRIC, "value": value, "unit": "DOF/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t_dev / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "dim": 2, "n": pr.n, "basis": "bspline", "degree": pr.degree,
+                   "levels": pr.levels, "holes": lay.n_holes, "depth": pr.depth, "bc": "nitsche", "rtol": RTOL,
+                   "n_active": n_active, "n_grid": n_grid, "seed": args.seed, "parallelism": f"replicas{world}",
+                   "l2": "flushed (256 MiB write) before every timed solve, flush outside the events",
+                   "iterations": its[0], "true_rel_residual": results[-1]["true_rel_residual"],
+                   "setup_s": setup_s},
+        "e2e": {"value": total_units / t_e2e, "unit": "DOF/s", "h2d_bytes_per_step": 8 * n_grid,
+                "d2h_bytes_per_step": 8 * n_grid},
+        "gpu_launches": launches_per_solve(S, its[0]) * args.steps,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                     "traffic": None, "kernel": "k_apply (finest-level operator apply, FP64)",
+                     "peak_source": "derived: " + FP64_PEAK_NOTE, "flops_per_launch": flops,
+                     "launch_ms": apply_ms},
+        "clocks": clocks,
+    }
+    if not args.no_cpu_baseline:
+        try:
+            line["cpu_baseline"] = cpu_baseline_entry(run_oracle(reps=1, seed=args.seed))
+        except Exception as e:  # the GPU number stands without it
+            line["cpu_baseline"] = {"error": str(e)[:200]}
+    S.close()
+    return line
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return None
+    o = run_oracle(reps=args.warmup + args.steps, seed=args.seed)
+    times = o["times"][args.warmup:]
+    value = o["n_active"] * len(times) / sum(times)
+    cb = cpu_baseline_entry({**o, "times": times})
+    cb["value"] = value
+    return {"metric": METRIC, "value": value, "unit": "DOF/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD, "cpu_sample": f"{CPU_SAMPLE_N}x{CPU_SAMPLE_N} instance, "
+                       f"{CPU_SAMPLE_LEVELS} levels", "rtol": RTOL, "n_active": o["n_active"]},
+            "cpu_baseline": cb,
+            "e2e": {"value": value, "unit": "DOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        line = run_reference(args, rank)
+    else:
+        line = run_ours(args, rank, world, local_rank)
+    if line is not None:
+        print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,181 @@
+/*
+ * imgm -- multigrid-preconditioned conjugate gradients for immersed (cut-cell)
+ * B-spline / Lagrange discretisations of the Poisson problem, on one GB300 GPU.
+ *
+ * Method: de Prenter, Verhoosel, van Brummelen, Evans, Messe, Benzaken, Maute,
+ * "Scalable multigrid methods for immersed finite element methods and immersed
+ * isogeometric analysis" (arXiv 1903.10977).
+ *
+ * Conventions used by every entry point
+ * -------------------------------------
+ * - A level l runs from 1 (coarsest) to L (finest).  Level l has n_l = n / 2^(L-l)
+ *   elements per direction and m_l degrees of freedom per direction (open uniform
+ *   B-splines: m_l = n_l + p).  A level vector has m_l^d FP64 entries in x-fastest
+ *   order (index = ix + m*(iy + m*iz)); entries of inactive functions (no support in
+ *   the physical domain, or removed by the u = 0 condition on the box faces) are 0 on
+ *   input and are written as 0 on output.
+ * - "dev_" pointers are CUDA device pointers owned by the caller; "host_" pointers are
+ *   host memory owned by the caller.  The library owns the handle and everything it
+ *   allocates in imgm_setup; imgm_destroy frees it.
+ * - Every GPU call is ordered on the CUDA stream passed as `stream` (a cudaStream_t;
+ *   NULL = the legacy default stream) and returns without waiting for the GPU, unless
+ *   its comment says otherwise.  Calls on one handle use the handle's scratch
+ *   vectors and must not run concurrently on different streams.
+ * - Return value: IMGM_OK (0) or a negative IMGM_ERR_* code; imgm_last_error(h) gives
+ *   a message.  No call aborts the process or traps on the GPU.
+ */
+#ifndef IMGM_H
+#define IMGM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define IMGM_OK 0
+#define IMGM_ERR_INVALID (-1)      /* bad argument */
+#define IMGM_ERR_UNSUPPORTED (-2)  /* configuration outside what is implemented */
+#define IMGM_ERR_CUDA (-3)         /* a CUDA runtime call failed */
+#define IMGM_ERR_NOT_SPD (-4)      /* a factorisation met a non-positive pivot */
+#define IMGM_ERR_BREAKDOWN (-5)    /* CG: p^T A p <= 0 or not finite */
+#define IMGM_MAX_ITER 1            /* CG stopped at maxit before reaching rtol (warning) */
+
+typedef struct imgm_handle imgm_handle;
+
+/* Physical domain: the box [lo, hi]^dim minus n_holes disjoint closed balls
+ * (level set psi(x) = min_i |x - c_i| - r_i, Omega = {psi > 0}; Sec. 2, Fig. 1).
+ * centers: n_holes*dim doubles, row-major; radii: n_holes doubles (host memory,
+ * read during imgm_setup only). */
+typedef struct {
+    int dim;                 /* 2 or 3 */
+    int n_holes;
+    const double* centers;
+    const double* radii;
+    double lo, hi;
+} imgm_geometry;
+
+/* Discretisation and solver parameters (Sec. 2 and Sec. 3). */
+typedef struct {
+    int n;                   /* elements per direction on the finest grid; n % 2^(levels-1) == 0 */
+    int basis;               /* 0 = uniform open B-splines, 1 = Lagrange (degree 1 only: the same space) */
+    int degree;              /* 1, 2 or 3 */
+    int levels;              /* L >= 2 multigrid levels (Algorithm 1) */
+    int depth;               /* cut-cell bisection depth (Sec. 2, Fig. 1) */
+    int bc;                  /* 0 = penalty beta = 2/h (the paper's), 1 = symmetric Nitsche */
+    double gamma;            /* additive Schwarz relaxation; <= 0 selects 1/(p+1)^d (Eq. applyCS) */
+} imgm_config;
+
+typedef struct {
+    int iterations;          /* CG iterations performed */
+    int status;              /* IMGM_OK, IMGM_MAX_ITER or IMGM_ERR_BREAKDOWN */
+    double rel_residual;     /* ||r_k|| / ||b|| of the recursively updated residual */
+    double true_rel_residual;/* ||b - A x|| / ||b||, recomputed at exit */
+} imgm_result;
+
+typedef struct {
+    int64_t n_grid;          /* m^d */
+    int64_t n_active;        /* active functions */
+    int64_t m;               /* functions per direction */
+    int64_t n_band;          /* rows stored explicitly (support touches a non-full element) */
+    int64_t n_blocks;        /* Schwarz blocks with more than one function after pruning */
+    int64_t block_entries;   /* sum of n_j^2 over those blocks */
+    int64_t max_block;       /* largest block */
+    int64_t pruned;          /* functions removed from blocks by the tiny-eigenvalue rule */
+} imgm_level_info;
+
+/* Builds the immersed discretisation and the whole multigrid hierarchy on the host
+ * (cut-cell quadrature, assembly of the stored rows, two-scale restriction, Galerkin
+ * coarse rows R A R^T, Schwarz blocks with encapsulating supports and the Remark 3.3
+ * rule, coarsest-level inverse) and uploads it to the current CUDA device.
+ * Sec. 2 (discretisation), Sec. 3.3 (Eq. coarsening, Remark 3.1), Sec. 3.4 (blocks,
+ * Remark 3.3).  Synchronous.  On success *out receives a new handle. */
+int imgm_setup(const imgm_geometry* geom, const imgm_config* cfg, imgm_handle** out);
+
+/* Frees everything the handle owns (device and host).  Waits for the device. */
+void imgm_destroy(imgm_handle* h);
+
+/* Message for the last failed call on h (or on a failed imgm_setup when h == NULL). */
+const char* imgm_last_error(const imgm_handle* h);
+
+/* Number of levels L. */
+int imgm_levels(const imgm_handle* h);
+
+/* Sizes and setup statistics of one level (1 <= level <= L). */
+int imgm_get_level_info(const imgm_handle* h, int level, imgm_level_info* info);
+
+/* Active-function mask of a level into host_mask (n_grid bytes, 1 = active). */
+int imgm_active_mask(const imgm_handle* h, int level, uint8_t* host_mask);
+
+/* Right-hand side b of the built-in manufactured problem u = prod sin(pi x_k)
+ * (finest level, Eq. operatorsMulti) into dev_b (n_grid doubles). */
+int imgm_rhs(imgm_handle* h, double* dev_b, void* stream);
+
+/* dev_y = A_l dev_x on level l (Eq. systemMulti on the finest level; the Galerkin
+ * operator R A R^T of Remark 3.1 on coarser levels).  dev_x and dev_y must not overlap. */
+int imgm_apply_operator(imgm_handle* h, int level, const double* dev_x, double* dev_y, void* stream);
+
+/* dev_z = gamma M_l^{-1} dev_r with the additive Schwarz operator
+ * M^{-1} = sum_j P_j A_j^{-1} P_j^T (Sec. 3.4), level l >= 2. */
+int imgm_smooth(imgm_handle* h, int level, const double* dev_r, double* dev_z, void* stream);
+
+/* dev_rc = R_l dev_r: restriction from level l >= 2 to level l-1 (Eq. coarsening). */
+int imgm_restrict(imgm_handle* h, int level, const double* dev_r, double* dev_rc, void* stream);
+
+/* dev_e = R_l^T dev_xc: prolongation from level l-1 to level l >= 2 (Sec. 3.3). */
+int imgm_prolong(imgm_handle* h, int level, const double* dev_xc, double* dev_e, void* stream);
+
+/* dev_x = A_1^{-1} dev_r on the coarsest level (Algorithm 1, direct solve). */
+int imgm_coarse_solve(imgm_handle* h, const double* dev_r, double* dev_x, void* stream);
+
+/* dev_z = B dev_r: one V-cycle of Algorithm 1 from the finest level (the CG
+ * preconditioner of Sec. 3.2).  dev_r is not modified. */
+int imgm_apply_preconditioner(imgm_handle* h, const double* dev_r, double* dev_z, void* stream);
+
+/* Solves A x = b by CG preconditioned with one V-cycle per iteration (Sec. 3.2), from
+ * the initial guess in dev_x, until ||r_k|| <= rtol ||b|| or maxit iterations.  dev_x
+ * receives the solution.  dev_hist (nullable, maxit+1 doubles) receives ||r_k||/||b||.
+ * Waits for the device before returning (it reports *out). */
+int imgm_pcg_solve(imgm_handle* h, const double* dev_b, double* dev_x, double rtol, int maxit,
+                   imgm_result* out, double* dev_hist, void* stream);
+
+/* imgm_pcg_solve with host buffers: copies host_b to the device, solves from x = 0,
+ * copies the solution to host_x (n_grid doubles each).  Synchronous. */
+int imgm_pcg_solve_host(imgm_handle* h, const double* host_b, double* host_x, double rtol, int maxit,
+                        imgm_result* out, void* stream);
+
+/* ---- Setup inspection (host only; no GPU needed) --------------------------------
+ * imgm_setup_host builds the same hierarchy as imgm_setup without touching the GPU;
+ * such a handle serves only the imgm_host_* calls below, imgm_levels,
+ * imgm_get_level_info and imgm_active_mask.  These calls copy setup data out for testing
+ * and inspection; they compute none of the solve. */
+int imgm_setup_host(const imgm_geometry* geom, const imgm_config* cfg, imgm_handle** out);
+
+/* Operator rows of level l: for each of the nrows full-grid row indices in rows,
+ * the (2p+1)^d coefficients A[row, row + o] for offsets o in [-p, p]^d (x fastest),
+ * into out (nrows * (2p+1)^d doubles).  0 for inactive rows and columns. */
+int imgm_host_operator_rows(const imgm_handle* h, int level, int64_t nrows, const int64_t* rows, double* out);
+
+/* Finest-level right-hand side (n_grid doubles). */
+int imgm_host_rhs(const imgm_handle* h, double* out);
+
+/* Schwarz data of level l >= 2: sizes first, then the arrays (block k holds rows
+ * idx[ptr[k]:ptr[k+1]] and the column-major inverse val[vptr[k]:vptr[k+1]]; dinv[i] is
+ * the sum of 1/A_ii over the one-function blocks that hold row i). */
+int imgm_host_block_sizes(const imgm_handle* h, int level, int64_t* nblk, int64_t* nidx, int64_t* nval);
+int imgm_host_blocks(const imgm_handle* h, int level, int64_t* ptr, int32_t* idx, int64_t* vptr, double* val,
+                     double* dinv);
+
+/* 1-D restriction table of level l >= 2: coarse function i of level l-1 equals
+ * sum_k w[i*(p+2)+k] phi_{first[i]+k} of level l (m_{l-1} entries of first). */
+int imgm_host_restriction(const imgm_handle* h, int level, int32_t* first, double* w);
+
+/* Coarsest-level inverse: nc kept rows and the nc x nc row-major inverse on them. */
+int imgm_host_coarse_size(const imgm_handle* h, int64_t* nc);
+int imgm_host_coarse(const imgm_handle* h, int32_t* rows, double* inv);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* IMGM_H */

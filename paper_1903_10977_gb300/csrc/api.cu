@@ -1,0 +1,666 @@
+// C-ABI of the immersed multigrid-preconditioned CG library (declarations in imgm.h).
+//
+// imgm_setup builds the hierarchy on the host (setup.cpp) and uploads it; the GPU entry
+// points enqueue the kernels of kernels.cu.  The CG solve runs as one CUDA graph: the
+// start-up kernels, a device-side while loop (conditional graph node) over one CG
+// iteration with its V-cycle, and the final residual check.  The loop condition is set
+// by a kernel from the device-held convergence flag, so the host waits only once.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/imgm.h"
+#include "kernels.cuh"
+#include "setup.hpp"
+
+using imgm::DevLevel;
+using imgm::PcgState;
+
+namespace {
+
+thread_local std::string g_setup_error;
+
+struct LevelDev {
+    DevLevel d;
+    double* x = nullptr;   // V-cycle iterate (level < L) / unused on the finest level
+    double* r = nullptr;   // restricted residual (level < L)
+    double* t = nullptr;   // residual after smoothing
+    double* e = nullptr;   // prolongated correction
+    imgm_level_info info{};
+};
+
+}  // namespace
+
+struct imgm_handle {
+    imgm::Hierarchy H;
+    bool on_device = false;
+    int dim = 2, p = 2, L = 2;
+    double gamma = 0.0;
+    std::vector<LevelDev> lv;          // index 0 = level 1
+    std::vector<void*> allocs;
+    int32_t* c_rows = nullptr;
+    double* c_inv = nullptr;
+    int nc = 0;
+    double* b = nullptr;               // built-in right-hand side
+    // CG state
+    double *cx = nullptr, *cr = nullptr, *cp = nullptr, *cq = nullptr, *cz = nullptr, *cb = nullptr;
+    double* hist = nullptr;
+    int hist_cap = 0;
+    double* partial = nullptr;
+    PcgState* st = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    bool graph_failed = false;
+    std::string err;
+
+    template <class T>
+    cudaError_t alloc(T** p, size_t count) {
+        void* v = nullptr;
+        cudaError_t e = cudaMalloc(&v, count * sizeof(T) > 0 ? count * sizeof(T) : 16);
+        if (e != cudaSuccess) return e;
+        allocs.push_back(v);
+        *p = (T*)v;
+        return cudaSuccess;
+    }
+    template <class T>
+    cudaError_t upload(T** p, const std::vector<T>& h) {
+        cudaError_t e = alloc(p, h.size());
+        if (e != cudaSuccess || h.empty()) return e;
+        return cudaMemcpy(*p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice);
+    }
+    ~imgm_handle() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        for (void* v : allocs) cudaFree(v);
+    }
+};
+
+namespace {
+
+int fail(imgm_handle* h, int code, const std::string& msg) {
+    if (h) h->err = msg;
+    else g_setup_error = msg;
+    return code;
+}
+
+int cuda_fail(imgm_handle* h, cudaError_t e, const char* where) {
+    return fail(h, IMGM_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call, where)                                   \
+    do {                                                  \
+        cudaError_t _e = (call);                          \
+        if (_e != cudaSuccess) return cuda_fail(h, _e, where); \
+    } while (0)
+
+int check_level(imgm_handle* h, int level, int min_level) {
+    if (!h) return IMGM_ERR_INVALID;
+    if (!h->on_device) return fail(h, IMGM_ERR_INVALID, "handle has no device data");
+    if (level < min_level || level > h->L) return fail(h, IMGM_ERR_INVALID, "level out of range");
+    return IMGM_OK;
+}
+
+// One V-cycle (Algorithm 1) from the finest level.  On entry z = gamma * dinv .* r
+// (the diagonal part of the first smoothing step); on exit z = B r.  r is not modified.
+cudaError_t enqueue_vcycle(imgm_handle* h, const double* r, double* z, const int* done, cudaStream_t s) {
+    const int L = h->L;
+    const double g = h->gamma;
+    cudaError_t e;
+    for (int li = L - 1; li >= 1; --li) {
+        LevelDev& F = h->lv[li];
+        LevelDev& C = h->lv[li - 1];
+        const double* rl = (li == L - 1) ? r : F.r;
+        double* xl = (li == L - 1) ? z : F.x;
+        // line 4: x = gamma M^{-1} r (the one-function blocks were applied by the producer of r)
+        if ((e = imgm::launch_blocks(F.d, rl, xl, g, done, s)) != cudaSuccess) return e;
+        // line 5: t = r - A x
+        if ((e = imgm::launch_apply(F.d, imgm::RESID, xl, rl, F.t, nullptr, g, done, s)) != cudaSuccess) return e;
+        // line 7: r_c = R t, and the diagonal part of the coarse pre-smoothing step
+        double* xc = (li - 1 >= 1) ? C.x : nullptr;
+        if ((e = imgm::launch_restrict(F.d, C.d, F.t, C.r, xc, g, done, s)) != cudaSuccess) return e;
+    }
+    // line 14: direct solve on level 1
+    if ((e = imgm::launch_coarse(h->c_rows, h->c_inv, h->nc, h->lv[0].r, h->lv[0].x, done, s)) != cudaSuccess) return e;
+    for (int li = 1; li <= L - 1; ++li) {
+        LevelDev& F = h->lv[li];
+        LevelDev& C = h->lv[li - 1];
+        double* xl = (li == L - 1) ? z : F.x;
+        // line 9: e = R^T x_c, x += e
+        if ((e = imgm::launch_prolong(F.d, C.d, C.x, F.e, xl, done, s)) != cudaSuccess) return e;
+        // line 10: t -= A e; line 12 (one-function blocks): x += gamma dinv .* t
+        if ((e = imgm::launch_apply(F.d, imgm::RESID_SMOOTH, F.e, F.t, F.t, xl, g, done, s)) != cudaSuccess) return e;
+        // line 12 (stored blocks): x += gamma sum_j P_j A_j^{-1} P_j^T t
+        if ((e = imgm::launch_blocks(F.d, F.t, xl, g, done, s)) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+// The whole CG solve on the handle's own vectors (cb -> cx): start, loop, final check.
+cudaError_t enqueue_solve_start(imgm_handle* h, cudaStream_t s) {
+    LevelDev& F = h->lv[h->L - 1];
+    const int* done = &h->st->done;
+    cudaError_t e;
+    if ((e = imgm::launch_apply(F.d, imgm::RESID, h->cx, h->cb, h->cr, nullptr, h->gamma, nullptr, s)) != cudaSuccess)
+        return e;
+    if ((e = imgm::launch_pcg_init_norms(F.d.N, h->cr, h->cb, h->partial, h->st, h->hist, s)) != cudaSuccess) return e;
+    if ((e = imgm::launch_scale_diag(F.d, h->cr, h->cz, h->gamma, done, s)) != cudaSuccess) return e;
+    if ((e = enqueue_vcycle(h, h->cr, h->cz, done, s)) != cudaSuccess) return e;
+    return imgm::launch_pcg_init_dir(F.d.N, h->cr, h->cz, h->cp, h->partial, h->st, s);
+}
+
+cudaError_t enqueue_iteration(imgm_handle* h, cudaStream_t s) {
+    LevelDev& F = h->lv[h->L - 1];
+    const int* done = &h->st->done;
+    cudaError_t e;
+    if ((e = imgm::launch_apply_pq(F.d, h->cp, h->cq, h->partial, h->st, s)) != cudaSuccess) return e;
+    if ((e = imgm::launch_pcg_update(F.d, h->cx, h->cr, h->cp, h->cq, h->cz, h->gamma, h->partial, h->st, h->hist, s)) !=
+        cudaSuccess)
+        return e;
+    if ((e = enqueue_vcycle(h, h->cr, h->cz, done, s)) != cudaSuccess) return e;
+    if ((e = imgm::launch_pcg_rz(F.d.N, h->cr, h->cz, h->partial, h->st, s)) != cudaSuccess) return e;
+    return imgm::launch_pcg_xpay(F.d.N, h->cz, h->cp, h->st, s);
+}
+
+cudaError_t enqueue_solve_finish(imgm_handle* h, cudaStream_t s) {
+    LevelDev& F = h->lv[h->L - 1];
+    cudaError_t e;
+    if ((e = imgm::launch_apply(F.d, imgm::RESID, h->cx, h->cb, F.t, nullptr, h->gamma, nullptr, s)) != cudaSuccess)
+        return e;
+    return imgm::launch_true_residual_norm(F.d.N, F.t, h->partial, h->st, s);
+}
+
+// Builds the solve graph: start -> while (!done) { iteration } -> finish.
+cudaError_t build_solve_graph(imgm_handle* h, cudaStream_t s) {
+    cudaStream_t body_stream = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&body_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return e;
+    cudaGraph_t g = nullptr;
+    do {
+        if ((e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) break;
+        cudaError_t ce = enqueue_solve_start(h, s);
+        cudaGraph_t cg = nullptr;
+        const cudaGraphNode_t* deps = nullptr;
+        size_t ndeps = 0;
+        cudaStreamCaptureStatus cs;
+        cudaGraphConditionalHandle handle = 0;
+        cudaGraphNode_t cnode = nullptr;
+        alignas(cudaGraphNodeParams) unsigned char cp_storage[sizeof(cudaGraphNodeParams)];
+        std::memset(cp_storage, 0, sizeof(cp_storage));
+        cudaGraphNodeParams& cp = *reinterpret_cast<cudaGraphNodeParams*>(cp_storage);
+        if (ce == cudaSuccess) ce = cudaStreamGetCaptureInfo(s, &cs, nullptr, &cg, &deps, nullptr, &ndeps);
+        if (ce == cudaSuccess) ce = cudaGraphConditionalHandleCreate(&handle, cg, 0, cudaGraphCondAssignDefault);
+        if (ce == cudaSuccess) ce = imgm::launch_set_continue(h->st, (unsigned long long)handle, s);
+        if (ce == cudaSuccess) ce = cudaStreamGetCaptureInfo(s, &cs, nullptr, &cg, &deps, nullptr, &ndeps);
+        if (ce == cudaSuccess) {
+            cp.type = cudaGraphNodeTypeConditional;
+            cp.conditional.handle = handle;
+            cp.conditional.type = cudaGraphCondTypeWhile;
+            cp.conditional.size = 1;
+            ce = cudaGraphAddNode(&cnode, cg, deps, nullptr, ndeps, &cp);
+        }
+        if (ce == cudaSuccess) ce = cudaStreamUpdateCaptureDependencies(s, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies);
+        if (ce == cudaSuccess) {
+            cudaGraph_t body = cp.conditional.phGraph_out[0];
+            ce = cudaStreamBeginCaptureToGraph(body_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+            if (ce == cudaSuccess) {
+                cudaError_t be = enqueue_iteration(h, body_stream);
+                if (be == cudaSuccess) be = imgm::launch_set_continue(h->st, (unsigned long long)handle, body_stream);
+                cudaGraph_t outb = nullptr;
+                cudaError_t ee = cudaStreamEndCapture(body_stream, &outb);
+                ce = (be != cudaSuccess) ? be : ee;
+            }
+        }
+        if (ce == cudaSuccess) ce = enqueue_solve_finish(h, s);
+        e = cudaStreamEndCapture(s, &g);
+        if (ce != cudaSuccess) e = ce;
+        if (e != cudaSuccess) break;
+        e = cudaGraphInstantiate(&h->exec, g, 0);
+    } while (0);
+    if (e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        g = nullptr;
+        cudaGetLastError();
+    }
+    h->graph = g;
+    cudaStreamDestroy(body_stream);
+    return e;
+}
+
+int upload_level(imgm_handle* h, const imgm::LevelData& src, LevelDev& dst, int level_index) {
+    const imgm::Hierarchy& H = h->H;
+    DevLevel& d = dst.d;
+    d.dim = H.dim;
+    d.p = H.p;
+    d.m = src.m;
+    d.ncoef = H.ncoef;
+    d.N = src.N;
+    d.nb = (int32_t)src.band_rows.size();
+    d.nblk = (int32_t)(src.blk_ptr.empty() ? 0 : src.blk_ptr.size() - 1);
+    d.max_block = (int32_t)src.max_block;
+    d.TW = src.TW;
+    int32_t* ri;
+    double *bc, *k1, *m1, *dv, *bv, *rw, *tw;
+    int64_t *bp, *bvp;
+    int32_t *bi, *rf, *tf;
+    CK(h->upload(&ri, src.rowinfo), "upload rowinfo");
+    CK(h->upload(&bc, src.band_coef), "upload stored rows");
+    CK(h->upload(&k1, src.K1), "upload K1");
+    CK(h->upload(&m1, src.M1), "upload M1");
+    CK(h->upload(&dv, src.dinv.empty() ? std::vector<double>(src.N, 0.0) : src.dinv), "upload dinv");
+    CK(h->upload(&bp, src.blk_ptr.empty() ? std::vector<int64_t>(1, 0) : src.blk_ptr), "upload block ptr");
+    CK(h->upload(&bi, src.blk_idx), "upload block idx");
+    CK(h->upload(&bvp, src.blk_vptr.empty() ? std::vector<int64_t>(1, 0) : src.blk_vptr), "upload block vptr");
+    CK(h->upload(&bv, src.blk_val), "upload block values");
+    CK(h->upload(&rf, src.r_first), "upload restriction");
+    CK(h->upload(&rw, src.r_w), "upload restriction");
+    CK(h->upload(&tf, src.t_first), "upload prolongation");
+    CK(h->upload(&tw, src.t_w), "upload prolongation");
+    d.rowinfo = ri;
+    d.band_coef = bc;
+    d.K1 = k1;
+    d.M1 = m1;
+    d.dinv = dv;
+    d.blk_ptr = bp;
+    d.blk_idx = bi;
+    d.blk_vptr = bvp;
+    d.blk_val = bv;
+    d.r_first = rf;
+    d.r_w = rw;
+    d.t_first = tf;
+    d.t_w = tw;
+    CK(h->alloc(&dst.x, src.N), "alloc x");
+    CK(h->alloc(&dst.r, src.N), "alloc r");
+    CK(h->alloc(&dst.t, src.N), "alloc t");
+    CK(h->alloc(&dst.e, src.N), "alloc e");
+    CK(cudaMemset(dst.x, 0, src.N * sizeof(double)), "memset");
+    CK(cudaMemset(dst.r, 0, src.N * sizeof(double)), "memset");
+    CK(cudaMemset(dst.t, 0, src.N * sizeof(double)), "memset");
+    CK(cudaMemset(dst.e, 0, src.N * sizeof(double)), "memset");
+    imgm_level_info& in = dst.info;
+    in.n_grid = src.N;
+    in.n_active = src.n_active;
+    in.m = src.m;
+    in.n_band = (int64_t)src.band_rows.size();
+    in.n_blocks = d.nblk;
+    int64_t ent = 0;
+    for (int b = 0; b < d.nblk; ++b) ent += src.blk_vptr[b + 1] - src.blk_vptr[b];
+    in.block_entries = ent;
+    in.max_block = src.max_block;
+    in.pruned = (level_index == 0) ? H.coarse_pruned : src.pruned;
+    return IMGM_OK;
+}
+
+imgm::Problem make_problem(const imgm_geometry* geom, const imgm_config* cfg) {
+    imgm::Problem pb;
+    pb.dim = geom->dim;
+    pb.lo = geom->lo;
+    pb.hi = geom->hi;
+    for (int i = 0; i < geom->n_holes; ++i) {
+        imgm::Ball b{};
+        for (int k = 0; k < geom->dim; ++k) b.c[k] = geom->centers[i * geom->dim + k];
+        b.r = geom->radii[i];
+        pb.holes.push_back(b);
+    }
+    pb.n = cfg->n;
+    pb.basis = cfg->basis;
+    pb.p = cfg->degree;
+    pb.levels = cfg->levels;
+    pb.depth = cfg->depth;
+    pb.bc = cfg->bc;
+    pb.gamma = cfg->gamma;
+    return pb;
+}
+
+int validate_inputs(const imgm_geometry* geom, const imgm_config* cfg) {
+    if (!geom || !cfg) return fail(nullptr, IMGM_ERR_INVALID, "null geometry or config");
+    if (geom->dim != 2 && geom->dim != 3) return fail(nullptr, IMGM_ERR_INVALID, "dim must be 2 or 3");
+    if (geom->n_holes < 0 || (geom->n_holes > 0 && (!geom->centers || !geom->radii)))
+        return fail(nullptr, IMGM_ERR_INVALID, "bad hole arrays");
+    for (int i = 0; i < geom->n_holes; ++i)
+        if (!(geom->radii[i] > 0.0)) return fail(nullptr, IMGM_ERR_INVALID, "hole radii must be positive");
+    return IMGM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* imgm_last_error(const imgm_handle* h) { return h ? h->err.c_str() : g_setup_error.c_str(); }
+
+int imgm_setup(const imgm_geometry* geom, const imgm_config* cfg, imgm_handle** out) {
+    if (!out) return fail(nullptr, IMGM_ERR_INVALID, "null output handle");
+    *out = nullptr;
+    int v = validate_inputs(geom, cfg);
+    if (v != IMGM_OK) return v;
+    std::unique_ptr<imgm_handle> h(new (std::nothrow) imgm_handle());
+    if (!h) return fail(nullptr, IMGM_ERR_INVALID, "out of host memory");
+    imgm::Problem pb = make_problem(geom, cfg);
+    std::string err;
+    if (!imgm::build_hierarchy(pb, h->H, err)) {
+        int code = (err.find("positive definite") != std::string::npos) ? IMGM_ERR_NOT_SPD : IMGM_ERR_UNSUPPORTED;
+        if (err.find("must") != std::string::npos || err.find("too") != std::string::npos) code = IMGM_ERR_INVALID;
+        return fail(nullptr, code, err);
+    }
+    imgm_handle* hp = h.get();
+    hp->dim = h->H.dim;
+    hp->p = h->H.p;
+    hp->L = h->H.L;
+    hp->gamma = h->H.gamma;
+    hp->lv.resize(hp->L);
+    for (int li = 0; li < hp->L; ++li) {
+        int rc = upload_level(hp, hp->H.lv[li], hp->lv[li], li);
+        if (rc != IMGM_OK) {
+            g_setup_error = hp->err;
+            return rc;
+        }
+    }
+    {
+        imgm_handle* h = hp;   // for CK
+        CK(h->upload(&h->c_rows, h->H.c_rows), "upload coarse rows");
+        CK(h->upload(&h->c_inv, h->H.c_inv), "upload coarse inverse");
+        h->nc = (int)h->H.c_rows.size();
+        CK(h->upload(&h->b, h->H.b), "upload rhs");
+        const int64_t N = h->lv[h->L - 1].d.N;
+        CK(h->alloc(&h->cx, N), "alloc");
+        CK(h->alloc(&h->cr, N), "alloc");
+        CK(h->alloc(&h->cp, N), "alloc");
+        CK(h->alloc(&h->cq, N), "alloc");
+        CK(h->alloc(&h->cz, N), "alloc");
+        CK(h->alloc(&h->cb, N), "alloc");
+        CK(h->alloc(&h->partial, 2 * (size_t)imgm::reduction_blocks()), "alloc");
+        CK(h->alloc(&h->st, 1), "alloc");
+        CK(cudaMemset(h->st, 0, sizeof(PcgState)), "memset");
+        CK(cudaMemset(h->cz, 0, N * sizeof(double)), "memset");
+        h->hist_cap = 100001;
+        CK(h->alloc(&h->hist, (size_t)h->hist_cap), "alloc");
+        CK(cudaDeviceSynchronize(), "setup sync");
+    }
+    hp->on_device = true;
+    *out = h.release();
+    return IMGM_OK;
+}
+
+void imgm_destroy(imgm_handle* h) {
+    if (!h) return;
+    cudaDeviceSynchronize();
+    delete h;
+}
+
+int imgm_levels(const imgm_handle* h) { return h ? h->L : IMGM_ERR_INVALID; }
+
+int imgm_get_level_info(const imgm_handle* h, int level, imgm_level_info* info) {
+    if (!h || !info || level < 1 || level > h->L) return IMGM_ERR_INVALID;
+    *info = h->lv[level - 1].info;
+    return IMGM_OK;
+}
+
+int imgm_active_mask(const imgm_handle* h, int level, uint8_t* host_mask) {
+    if (!h || !host_mask || level < 1 || level > h->L) return IMGM_ERR_INVALID;
+    const std::vector<uint8_t>& a = h->H.lv[level - 1].active;
+    std::memcpy(host_mask, a.data(), a.size());
+    return IMGM_OK;
+}
+
+int imgm_rhs(imgm_handle* h, double* dev_b, void* stream) {
+    int c = check_level(h, h ? h->L : 0, 1);
+    if (c) return c;
+    if (!dev_b) return fail(h, IMGM_ERR_INVALID, "null pointer");
+    CK(cudaMemcpyAsync(dev_b, h->b, h->lv[h->L - 1].d.N * sizeof(double), cudaMemcpyDeviceToDevice, (cudaStream_t)stream),
+       "rhs copy");
+    return IMGM_OK;
+}
+
+int imgm_apply_operator(imgm_handle* h, int level, const double* dev_x, double* dev_y, void* stream) {
+    int c = check_level(h, level, 1);
+    if (c) return c;
+    if (!dev_x || !dev_y || dev_x == dev_y) return fail(h, IMGM_ERR_INVALID, "bad vector pointers");
+    const LevelDev& L = h->lv[level - 1];
+    CK(imgm::launch_apply(L.d, imgm::APPLY, dev_x, nullptr, dev_y, nullptr, 0.0, nullptr, (cudaStream_t)stream),
+       "apply");
+    return IMGM_OK;
+}
+
+int imgm_smooth(imgm_handle* h, int level, const double* dev_r, double* dev_z, void* stream) {
+    int c = check_level(h, level, 2);
+    if (c) return c;
+    if (!dev_r || !dev_z || dev_r == dev_z) return fail(h, IMGM_ERR_INVALID, "bad vector pointers");
+    const LevelDev& L = h->lv[level - 1];
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(imgm::launch_scale_diag(L.d, dev_r, dev_z, h->gamma, nullptr, s), "smooth diag");
+    CK(imgm::launch_blocks(L.d, dev_r, dev_z, h->gamma, nullptr, s), "smooth blocks");
+    return IMGM_OK;
+}
+
+int imgm_restrict(imgm_handle* h, int level, const double* dev_r, double* dev_rc, void* stream) {
+    int c = check_level(h, level, 2);
+    if (c) return c;
+    if (!dev_r || !dev_rc) return fail(h, IMGM_ERR_INVALID, "bad vector pointers");
+    CK(imgm::launch_restrict(h->lv[level - 1].d, h->lv[level - 2].d, dev_r, dev_rc, nullptr, 0.0, nullptr,
+                             (cudaStream_t)stream),
+       "restrict");
+    return IMGM_OK;
+}
+
+int imgm_prolong(imgm_handle* h, int level, const double* dev_xc, double* dev_e, void* stream) {
+    int c = check_level(h, level, 2);
+    if (c) return c;
+    if (!dev_xc || !dev_e) return fail(h, IMGM_ERR_INVALID, "bad vector pointers");
+    CK(imgm::launch_prolong(h->lv[level - 1].d, h->lv[level - 2].d, dev_xc, dev_e, nullptr, nullptr,
+                            (cudaStream_t)stream),
+       "prolong");
+    return IMGM_OK;
+}
+
+int imgm_coarse_solve(imgm_handle* h, const double* dev_r, double* dev_x, void* stream) {
+    int c = check_level(h, 1, 1);
+    if (c) return c;
+    if (!dev_r || !dev_x || dev_r == dev_x) return fail(h, IMGM_ERR_INVALID, "bad vector pointers");
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(cudaMemsetAsync(dev_x, 0, h->lv[0].d.N * sizeof(double), s), "coarse memset");
+    CK(imgm::launch_coarse(h->c_rows, h->c_inv, h->nc, dev_r, dev_x, nullptr, s), "coarse solve");
+    return IMGM_OK;
+}
+
+int imgm_apply_preconditioner(imgm_handle* h, const double* dev_r, double* dev_z, void* stream) {
+    int c = check_level(h, h ? h->L : 0, 1);
+    if (c) return c;
+    if (!dev_r || !dev_z || dev_r == dev_z) return fail(h, IMGM_ERR_INVALID, "bad vector pointers");
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(imgm::launch_scale_diag(h->lv[h->L - 1].d, dev_r, dev_z, h->gamma, nullptr, s), "vcycle diag");
+    CK(enqueue_vcycle(h, dev_r, dev_z, nullptr, s), "vcycle");
+    return IMGM_OK;
+}
+
+int imgm_pcg_solve(imgm_handle* h, const double* dev_b, double* dev_x, double rtol, int maxit, imgm_result* out,
+                   double* dev_hist, void* stream) {
+    int c = check_level(h, h ? h->L : 0, 1);
+    if (c) return c;
+    if (!dev_b || !dev_x || !out) return fail(h, IMGM_ERR_INVALID, "null pointer");
+    if (maxit < 0 || maxit >= h->hist_cap || !(rtol >= 0.0)) return fail(h, IMGM_ERR_INVALID, "bad rtol or maxit");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t N = h->lv[h->L - 1].d.N;
+    PcgState init;
+    std::memset(&init, 0, sizeof(init));
+    init.tol2 = rtol * rtol;
+    init.maxit = maxit;
+    CK(cudaMemcpyAsync(h->st, &init, sizeof(init), cudaMemcpyHostToDevice, s), "state");
+    CK(cudaMemcpyAsync(h->cb, dev_b, N * sizeof(double), cudaMemcpyDeviceToDevice, s), "copy b");
+    CK(cudaMemcpyAsync(h->cx, dev_x, N * sizeof(double), cudaMemcpyDeviceToDevice, s), "copy x0");
+    if (!h->exec && !h->graph_failed) {
+        if (build_solve_graph(h, s) != cudaSuccess) {
+            h->graph_failed = true;
+            cudaGetLastError();
+        }
+    }
+    if (h->exec) {
+        CK(cudaGraphLaunch(h->exec, s), "graph launch");
+    } else {
+        // fallback without conditional graph nodes: host loop, convergence read back every 8 steps
+        CK(enqueue_solve_start(h, s), "start");
+        int done = 0;
+        int it = 0;
+        while (!done && it < maxit) {
+            for (int k = 0; k < 8; ++k, ++it) CK(enqueue_iteration(h, s), "iteration");
+            CK(cudaMemcpyAsync(&done, &h->st->done, sizeof(int), cudaMemcpyDeviceToHost, s), "done flag");
+            CK(cudaStreamSynchronize(s), "sync");
+        }
+        CK(enqueue_solve_finish(h, s), "finish");
+    }
+    CK(cudaMemcpyAsync(dev_x, h->cx, N * sizeof(double), cudaMemcpyDeviceToDevice, s), "copy x");
+    PcgState fin;
+    CK(cudaMemcpyAsync(&fin, h->st, sizeof(fin), cudaMemcpyDeviceToHost, s), "state");
+    if (dev_hist)
+        CK(cudaMemcpyAsync(dev_hist, h->hist, (size_t)(maxit + 1) * sizeof(double), cudaMemcpyDeviceToDevice, s),
+           "hist");
+    CK(cudaStreamSynchronize(s), "solve sync");
+    out->iterations = fin.iter;
+    out->status = fin.status;
+    out->rel_residual = fin.bb > 0 ? std::sqrt(fin.rr / fin.bb) : 0.0;
+    out->true_rel_residual = fin.bb > 0 ? std::sqrt(fin.true_rr / fin.bb) : 0.0;
+    return fin.status == -5 ? IMGM_ERR_BREAKDOWN : (fin.status == 1 ? IMGM_MAX_ITER : IMGM_OK);
+}
+
+int imgm_pcg_solve_host(imgm_handle* h, const double* host_b, double* host_x, double rtol, int maxit,
+                        imgm_result* out, void* stream) {
+    int c = check_level(h, h ? h->L : 0, 1);
+    if (c) return c;
+    if (!host_b || !host_x || !out) return fail(h, IMGM_ERR_INVALID, "null pointer");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t N = h->lv[h->L - 1].d.N;
+    // stage through the handle's own CG vectors: b -> cq, x0 = 0 -> cp (both are
+    // overwritten by the solve before they are read)
+    CK(cudaMemcpyAsync(h->cq, host_b, N * sizeof(double), cudaMemcpyHostToDevice, s), "h2d b");
+    CK(cudaMemsetAsync(h->cp, 0, N * sizeof(double), s), "x0");
+    int rc = imgm_pcg_solve(h, h->cq, h->cp, rtol, maxit, out, nullptr, stream);
+    if (rc < 0) return rc;
+    CK(cudaMemcpyAsync(host_x, h->cx, N * sizeof(double), cudaMemcpyDeviceToHost, s), "d2h x");
+    CK(cudaStreamSynchronize(s), "sync");
+    return rc;
+}
+
+int imgm_setup_host(const imgm_geometry* geom, const imgm_config* cfg, imgm_handle** out) {
+    if (!out) return fail(nullptr, IMGM_ERR_INVALID, "null output handle");
+    *out = nullptr;
+    int v = validate_inputs(geom, cfg);
+    if (v != IMGM_OK) return v;
+    std::unique_ptr<imgm_handle> h(new (std::nothrow) imgm_handle());
+    if (!h) return fail(nullptr, IMGM_ERR_INVALID, "out of host memory");
+    imgm::Problem pb = make_problem(geom, cfg);
+    std::string err;
+    if (!imgm::build_hierarchy(pb, h->H, err)) {
+        int code = (err.find("positive definite") != std::string::npos) ? IMGM_ERR_NOT_SPD : IMGM_ERR_UNSUPPORTED;
+        if (err.find("must") != std::string::npos || err.find("too") != std::string::npos) code = IMGM_ERR_INVALID;
+        return fail(nullptr, code, err);
+    }
+    h->dim = h->H.dim;
+    h->p = h->H.p;
+    h->L = h->H.L;
+    h->gamma = h->H.gamma;
+    h->lv.resize(h->L);
+    for (int li = 0; li < h->L; ++li) {
+        const imgm::LevelData& s = h->H.lv[li];
+        imgm_level_info& in = h->lv[li].info;
+        in.n_grid = s.N;
+        in.n_active = s.n_active;
+        in.m = s.m;
+        in.n_band = (int64_t)s.band_rows.size();
+        in.n_blocks = s.blk_ptr.empty() ? 0 : (int64_t)s.blk_ptr.size() - 1;
+        in.block_entries = (int64_t)s.blk_val.size();
+        in.max_block = s.max_block;
+        in.pruned = (li == 0) ? h->H.coarse_pruned : s.pruned;
+    }
+    *out = h.release();
+    return IMGM_OK;
+}
+
+int imgm_host_operator_rows(const imgm_handle* h, int level, int64_t nrows, const int64_t* rows, double* out) {
+    if (!h || level < 1 || level > h->L || nrows < 0 || (nrows > 0 && (!rows || !out))) return IMGM_ERR_INVALID;
+    const imgm::Hierarchy& H = h->H;
+    const imgm::LevelData& lv = H.lv[level - 1];
+    const int p = H.p, W = 2 * p + 1, dim = H.dim, nc = H.ncoef;
+    const int64_t m = lv.m, nb = (int64_t)lv.band_rows.size();
+    for (int64_t k = 0; k < nrows; ++k) {
+        const int64_t r = rows[k];
+        double* o = out + k * nc;
+        std::fill(o, o + nc, 0.0);
+        if (r < 0 || r >= lv.N) return IMGM_ERR_INVALID;
+        const int ri = lv.rowinfo[r];
+        if (ri == -2) continue;
+        if (ri >= 0) {
+            for (int c = 0; c < nc; ++c) o[c] = lv.band_coef[(size_t)c * nb + ri];
+            continue;
+        }
+        int i[3] = {(int)(r % m), (int)((r / m) % m), dim == 3 ? (int)(r / (m * m)) : 0};
+        for (int c = 0; c < nc; ++c) {
+            int off[3] = {c % W - p, (c / W) % W - p, dim == 3 ? c / (W * W) - p : 0};
+            int j[3] = {i[0] + off[0], i[1] + off[1], i[2] + off[2]};
+            bool ok = true;
+            for (int d = 0; d < dim; ++d) ok = ok && j[d] >= 0 && j[d] < m;
+            if (!ok) continue;
+            int64_t jf = j[0] + m * (j[1] + (dim == 3 ? m * j[2] : 0));
+            if (!lv.active[jf]) continue;
+            auto K = [&](int d) { return lv.K1[(size_t)i[d] * W + off[d] + p]; };
+            auto M = [&](int d) { return lv.M1[(size_t)i[d] * W + off[d] + p]; };
+            o[c] = (dim == 2) ? K(0) * M(1) + M(0) * K(1)
+                              : K(0) * M(1) * M(2) + M(0) * K(1) * M(2) + M(0) * M(1) * K(2);
+        }
+    }
+    return IMGM_OK;
+}
+
+int imgm_host_rhs(const imgm_handle* h, double* out) {
+    if (!h || !out) return IMGM_ERR_INVALID;
+    std::memcpy(out, h->H.b.data(), h->H.b.size() * sizeof(double));
+    return IMGM_OK;
+}
+
+int imgm_host_block_sizes(const imgm_handle* h, int level, int64_t* nblk, int64_t* nidx, int64_t* nval) {
+    if (!h || level < 2 || level > h->L || !nblk || !nidx || !nval) return IMGM_ERR_INVALID;
+    const imgm::LevelData& lv = h->H.lv[level - 1];
+    *nblk = lv.blk_ptr.empty() ? 0 : (int64_t)lv.blk_ptr.size() - 1;
+    *nidx = (int64_t)lv.blk_idx.size();
+    *nval = (int64_t)lv.blk_val.size();
+    return IMGM_OK;
+}
+
+int imgm_host_blocks(const imgm_handle* h, int level, int64_t* ptr, int32_t* idx, int64_t* vptr, double* val,
+                     double* dinv) {
+    if (!h || level < 2 || level > h->L) return IMGM_ERR_INVALID;
+    const imgm::LevelData& lv = h->H.lv[level - 1];
+    if (ptr) std::memcpy(ptr, lv.blk_ptr.data(), lv.blk_ptr.size() * sizeof(int64_t));
+    if (idx) std::memcpy(idx, lv.blk_idx.data(), lv.blk_idx.size() * sizeof(int32_t));
+    if (vptr) std::memcpy(vptr, lv.blk_vptr.data(), lv.blk_vptr.size() * sizeof(int64_t));
+    if (val) std::memcpy(val, lv.blk_val.data(), lv.blk_val.size() * sizeof(double));
+    if (dinv) std::memcpy(dinv, lv.dinv.data(), lv.dinv.size() * sizeof(double));
+    return IMGM_OK;
+}
+
+int imgm_host_restriction(const imgm_handle* h, int level, int32_t* first, double* w) {
+    if (!h || level < 2 || level > h->L || !first || !w) return IMGM_ERR_INVALID;
+    const imgm::LevelData& lv = h->H.lv[level - 1];
+    std::memcpy(first, lv.r_first.data(), lv.r_first.size() * sizeof(int32_t));
+    std::memcpy(w, lv.r_w.data(), lv.r_w.size() * sizeof(double));
+    return IMGM_OK;
+}
+
+int imgm_host_coarse_size(const imgm_handle* h, int64_t* nc) {
+    if (!h || !nc) return IMGM_ERR_INVALID;
+    *nc = (int64_t)h->H.c_rows.size();
+    return IMGM_OK;
+}
+
+int imgm_host_coarse(const imgm_handle* h, int32_t* rows, double* inv) {
+    if (!h || !rows || !inv) return IMGM_ERR_INVALID;
+    std::memcpy(rows, h->H.c_rows.data(), h->H.c_rows.size() * sizeof(int32_t));
+    std::memcpy(inv, h->H.c_inv.data(), h->H.c_inv.size() * sizeof(double));
+    return IMGM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,260 @@
+"""GPU parity of every hot-path step against the FP64 CPU oracle, through the C-ABI.
+
+Tolerances follow from the arithmetic:
+* products with fixed coefficients (operator rows, restriction, prolongation) are
+  compared entry by entry against (4 n eps + c_setup) ||A_i||_1 max_j |x_j| (j over the
+  row's columns): each side's length-n sum is within n eps of it whatever the order of
+  summation (the tensor rows are summed in factored form, sum_y M_y sum_x K_x x), and
+  c_setup = 1e-12 covers the independent assembly of the coefficients (test_lib_host
+  holds every row to 1e-12 of its own largest entry; the Nitsche terms of sliver cut
+  elements cancel, so their rounding shows at that level rather than at a few eps);
+  the whole vector must also agree to 1e-13 in the relative l2 norm;
+* steps that invert something (Schwarz blocks, the coarsest-level solve, the V-cycle,
+  CG) are compared in the energy norm ||e||_A / ||ref||_A and in the L2(Omega_h) norm of
+  the FE functions (mass matrix); cut functions with tiny supports carry coefficients
+  whose size is set by eps cond(A), so the coefficient l2 norm is not a meaningful
+  measure there (both norms above weight such functions by their tiny energy / mass).
+  The CG iterates must agree to 1e-10 in the L2 norm of the FE function.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+lib = pytest.importorskip("paper_1903_10977_gb300")
+from parity_utils import energy_rel, mass_rel, oracle_for, solver_for  # noqa: E402
+from oracle import multigrid as MG  # noqa: E402
+from synthetic import random_grid_vector  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+EPS = np.finfo(float).eps
+_LOG = os.environ.get("IMGM_PARITY_LOG")
+
+
+def record(**kw):
+    """Append measured parity figures to $IMGM_PARITY_LOG (JSON lines) when it is set."""
+    if _LOG:
+        with open(_LOG, "a") as f:
+            f.write(json.dumps({"test": os.environ.get("PYTEST_CURRENT_TEST", "").split(" ")[0], **kw}) + "\n")
+
+CASES = [
+    ("disc1_32_p2", {}),
+    ("disc1_32_p2", {"bc": 0}),
+    ("discs10_512_p1", {"n": 64, "levels": 3}),
+    ("discs10_512_p2", {"n": 128, "levels": 4}),
+    ("discs10_512_p3", {"n": 64, "levels": 3}),
+    ("spheres20_128_p2", {"n": 16, "levels": 2, "depth": 1}),
+]
+
+
+def dev(v):
+    return torch.as_tensor(np.ascontiguousarray(v), dtype=torch.float64, device="cuda")
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.detach().cpu().numpy()
+
+
+@pytest.fixture(scope="module", params=CASES, ids=[f"{n}-{'-'.join(f'{k}{v}' for k, v in o.items())}" for n, o in CASES])
+def pair(request):
+    name, ov = request.param
+    pr, lay, d, H = oracle_for(name, **ov)
+    S = solver_for(lib, pr, lay)
+    yield pr, d, H, S
+    S.close()
+
+
+def within_dot_bound(got, ref, A, x, n_terms, c_setup=0.0):
+    """|got - ref| <= (4 n eps + c_setup) ||A_i||_1 max_{j in row i} |x_j|, row by row."""
+    absA = abs(A).tocsr()
+    xmax = absA.sign().multiply(np.abs(x)[None, :]).max(axis=1).toarray().ravel()
+    bound = (4 * n_terms * EPS + c_setup) * np.asarray(absA.sum(axis=1)).ravel() * xmax + 1e-300
+    ratio = np.abs(got - ref) / bound
+    record(worst_dot_ratio=float(ratio.max()))
+    return ratio.max() <= 1.0, float(ratio.max())
+
+
+def full(lev, v_active):
+    out = np.zeros(lev.tb.n_funcs)
+    out[lev.active] = v_active
+    return out
+
+
+def test_apply_operator_every_level(pair):
+    pr, d, H, S = pair
+    n_terms = (2 * pr.degree + 1) ** pr.dim
+    for l in range(H.L, 0, -1):
+        lev = H.lv[l]
+        x = random_grid_vector(lev.active.size, 10 + l)
+        y = host(S.apply_operator(dev(full(lev, x)), level=l))
+        ref = lev.A @ x
+        ok, worst = within_dot_bound(y[lev.active], ref, lev.A, x, n_terms, c_setup=1e-12)
+        rel = float(np.linalg.norm(y[lev.active] - ref) / np.linalg.norm(ref))
+        record(level=l, l2_rel=rel)
+        assert ok, (l, worst)
+        assert rel <= 1e-13, (l, rel)
+        assert not np.any(np.delete(y, lev.active))
+
+
+def test_restrict_and_prolong(pair):
+    pr, d, H, S = pair
+    for l in range(H.L, 1, -1):
+        fine, coarse = H.lv[l], H.lv[l - 1]
+        R = fine.R
+        r = random_grid_vector(fine.active.size, 20 + l)
+        rc = host(S.restrict(dev(full(fine, r)), level=l))
+        n_terms = (pr.degree + 2) ** pr.dim
+        ok, worst = within_dot_bound(rc[coarse.active], R @ r, R, r, n_terms)
+        assert ok, (l, worst)
+        assert not np.any(np.delete(rc, coarse.active))
+        xc = random_grid_vector(coarse.active.size, 30 + l)
+        e = host(S.prolong(dev(full(coarse, xc)), level=l))
+        ok, worst = within_dot_bound(e[fine.active], R.T @ xc, R.T.tocsr(), xc, n_terms)
+        assert ok, (l, worst)
+        assert not np.any(np.delete(e, fine.active))
+
+
+def test_schwarz_smoother(pair):
+    pr, d, H, S = pair
+    for l in range(H.L, 1, -1):
+        lev = H.lv[l]
+        r = random_grid_vector(lev.active.size, 40 + l)
+        z = host(S.smooth(dev(full(lev, r)), level=l))[lev.active]
+        ref = H.gamma * (lev.Minv @ r)
+        er = energy_rel(z - ref, ref, lev.A)
+        record(level=l, energy_rel=er)
+        assert er < 1e-10, l
+
+
+def test_coarse_solve(pair):
+    pr, d, H, S = pair
+    lev = H.lv[1]
+    r = random_grid_vector(lev.active.size, 50)
+    x = host(S.coarse_solve(dev(full(lev, r))))[lev.active]
+    ref = H.vcycle(1, r)
+    er = energy_rel(x - ref, ref, lev.A)
+    record(energy_rel=er)
+    assert er < 1e-10
+
+
+def test_vcycle(pair):
+    pr, d, H, S = pair
+    r = random_grid_vector(d.n_active, 60)
+    z = host(S.apply_preconditioner(dev(d.to_full(r))))
+    ref = H.precondition(r)
+    er, mr = energy_rel(z[d.active] - ref, ref, d.A), mass_rel(z[d.active] - ref, ref, d.M)
+    record(energy_rel=er, mass_rel=mr)
+    assert er < 1e-10
+    assert mr < 1e-10
+    assert not np.any(np.delete(z, d.active))
+
+
+def test_rhs(pair):
+    pr, d, H, S = pair
+    b = host(S.rhs())
+    assert np.abs(b[d.active] - d.b).max() <= 1e-13 * np.abs(d.b).max()
+
+
+def test_pcg_fixed_iterations(pair):
+    """Same number of CG steps from x0 = 0: the iterates agree (L2 of the FE function).
+
+    k = 3: CG amplifies differences of its preconditioner output from one step to the
+    next (on the 3-D case a 1e-15 perturbation of the oracle's own V-cycle output moves
+    its 6th iterate by 5e-12), so the comparison is made before that growth dominates.
+    """
+    pr, d, H, S = pair
+    k = 3
+    x, res, hist = S.pcg_solve(dev(d.to_full(d.b)), rtol=0.0, maxit=k, hist=True)
+    ref, it, hist_ref = MG.pcg(d.A, d.b, H.precondition, rtol=0.0, maxit=k)
+    x = host(x)[d.active]
+    assert res["iterations"] == k == it and res["status"] == lib.IMGM_MAX_ITER
+    mr, er = mass_rel(x - ref, ref, d.M), energy_rel(x - ref, ref, d.A)
+    record(mass_rel=mr, energy_rel=er)
+    assert mr < 1e-10
+    assert er < 1e-10
+    np.testing.assert_allclose(host(hist), hist_ref, rtol=1e-8)
+
+
+def test_pcg_converged(pair):
+    """Both reach 1e-8.  Over hundreds of iterations (additive Schwarz with gamma =
+    (p+1)^-d converges slowly for p = 3) the two finite-precision CG runs drift apart by a
+    few iterations, so the count must agree to within 5 %; the solutions then agree to
+    the accuracy of the stopping test, and exactly when the counts are equal."""
+    pr, d, H, S = pair
+    x, res, _ = S.pcg_solve(dev(d.to_full(d.b)), rtol=1e-8, maxit=1000)
+    ref, it, _ = MG.pcg(d.A, d.b, H.precondition, rtol=1e-8, maxit=1000)
+    x = host(x)[d.active]
+    mr = mass_rel(x - ref, ref, d.M)
+    record(iterations=res["iterations"], oracle_iterations=it, mass_rel=mr,
+           true_rel_residual=res["true_rel_residual"])
+    assert res["status"] == lib.IMGM_OK and abs(res["iterations"] - it) <= max(1, 0.05 * it)
+    assert res["rel_residual"] <= 1e-8 and res["true_rel_residual"] <= 1e-7
+    assert mr < (1e-10 if res["iterations"] == it else 1e-6)
+
+
+# ---------------------------------------------------------------- edge cases
+@pytest.fixture(scope="module")
+def small():
+    pr, lay, d, H = oracle_for("disc1_32_p2")
+    S = solver_for(lib, pr, lay)
+    yield pr, d, H, S
+    S.close()
+
+
+def test_zero_rhs_returns_zero(small):
+    pr, d, H, S = small
+    b = torch.zeros(S.n_grid(), dtype=torch.float64, device="cuda")
+    x, res, _ = S.pcg_solve(b, rtol=1e-8, maxit=100)
+    assert res["iterations"] == 0 and res["status"] == lib.IMGM_OK
+    assert not torch.any(x)
+
+
+def test_start_from_solution(small):
+    pr, d, H, S = small
+    b = dev(d.to_full(d.b))
+    x, res, _ = S.pcg_solve(b, rtol=1e-8, maxit=200)
+    x2, res2, _ = S.pcg_solve(b, x=x.clone(), rtol=1e-6, maxit=200)
+    assert res2["iterations"] == 0
+
+
+def test_maxit_zero(small):
+    pr, d, H, S = small
+    x, res, _ = S.pcg_solve(dev(d.to_full(d.b)), rtol=1e-8, maxit=0)
+    assert res["iterations"] == 0 and res["status"] == lib.IMGM_MAX_ITER
+
+
+def test_nan_rhs_reports_breakdown(small):
+    pr, d, H, S = small
+    b = dev(d.to_full(d.b))
+    b[int(d.active[3])] = float("nan")
+    with pytest.raises(lib.ImgmError, match="breakdown"):
+        S.pcg_solve(b, rtol=1e-8, maxit=50)
+    # the handle stays usable
+    x, res, _ = S.pcg_solve(dev(d.to_full(d.b)), rtol=1e-8, maxit=500)
+    assert res["status"] == lib.IMGM_OK
+
+
+def test_bad_arguments_rejected(small):
+    pr, d, H, S = small
+    x = torch.zeros(S.n_grid(), dtype=torch.float64, device="cuda")
+    with pytest.raises(lib.ImgmError):
+        S.apply_operator(x, y=x)               # aliasing
+    with pytest.raises(lib.ImgmError):
+        S.smooth(x, level=1)                   # no smoother on level 1
+    with pytest.raises(TypeError):
+        S.apply_operator(x.float())
+
+
+def test_box_without_holes_matches_oracle():
+    from oracle import discretize as D, geometry as G
+    d = D.Discretization(G.Balls(np.zeros((0, 2)), np.zeros(0)), 0, 2, 32, 0, 1)
+    H = MG.Hierarchy(d, 3)
+    S = lib.Solver(2, np.zeros((0, 2)), np.zeros(0), 32, 2, 3, 0, 1)
+    x, res, _ = S.pcg_solve(dev(d.to_full(d.b)), rtol=1e-10, maxit=300)
+    ref, it, _ = MG.pcg(d.A, d.b, H.precondition, rtol=1e-10, maxit=300)
+    assert abs(res["iterations"] - it) <= 1
+    assert mass_rel(host(x)[d.active] - ref, ref, d.M) < 1e-9
+    S.close()
