@@ -144,6 +144,12 @@ int imgm_pcg_solve(imgm_handle* h, const double* dev_b, double* dev_x, double rt
 int imgm_pcg_solve_host(imgm_handle* h, const double* host_b, double* host_x, double rtol, int maxit,
                         imgm_result* out, void* stream);
 
+/* dev_out[0] = ||dev_b - A dev_x||_2^2 on the finest level (the residual of Eq.
+ * residualMulti, whose norm is the stopping quantity of the CG solve of Sec. 3.2).
+ * dev_b and dev_x: n_grid doubles; dev_out: one double.  Uses the handle's scratch
+ * vectors, so it must not overlap other calls on the same handle. */
+int imgm_residual_norm2(imgm_handle* h, const double* dev_b, const double* dev_x, double* dev_out, void* stream);
+
 /* ---- Setup inspection (host only; no GPU needed) --------------------------------
  * imgm_setup_host builds the same hierarchy as imgm_setup without touching the GPU;
  * such a handle serves only the imgm_host_* calls below, imgm_levels,

@@ -22,9 +22,9 @@ of the box, ``geom.box_dirichlet``), they carry the homogeneous condition u = 0
 strongly: every function that is non-zero on the box boundary is removed (reading; the
 paper's own domains are immersed and never touch the box).
 
-Activity (Sec. 2: "basis functions that are supported on the physical domain"):
-an element is active when |K cap Omega_h| > 0 and a function is active when one of its
-support elements is active.  Vectors in this module are indexed by active function
+Activity (Sec. 2: the approximation space is spanned by the functions whose support
+reaches into the physical domain): an element is active when |K cap Omega_h| > 0 and a
+function is active when one of its support elements is active.  Vectors in this module are indexed by active function
 (increasing full-grid index); ``Discretization.active`` maps them to the full grid.
 """
 from __future__ import annotations

@@ -55,6 +55,8 @@ struct imgm_handle {
     int hist_cap = 0;
     double* partial = nullptr;
     PcgState* st = nullptr;
+    double* partial_aux = nullptr;     // reductions outside the CG solve
+    PcgState* st_aux = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     bool graph_failed = false;
@@ -346,6 +348,7 @@ int imgm_setup(const imgm_geometry* geom, const imgm_config* cfg, imgm_handle** 
     if (!imgm::build_hierarchy(pb, h->H, err)) {
         int code = (err.find("positive definite") != std::string::npos) ? IMGM_ERR_NOT_SPD : IMGM_ERR_UNSUPPORTED;
         if (err.find("must") != std::string::npos || err.find("too") != std::string::npos) code = IMGM_ERR_INVALID;
+        if (err.find("coarsest level has") != std::string::npos) code = IMGM_ERR_UNSUPPORTED;
         return fail(nullptr, code, err);
     }
     imgm_handle* hp = h.get();
@@ -377,6 +380,9 @@ int imgm_setup(const imgm_geometry* geom, const imgm_config* cfg, imgm_handle** 
         CK(h->alloc(&h->partial, 2 * (size_t)imgm::reduction_blocks()), "alloc");
         CK(h->alloc(&h->st, 1), "alloc");
         CK(cudaMemset(h->st, 0, sizeof(PcgState)), "memset");
+        CK(h->alloc(&h->partial_aux, 2 * (size_t)imgm::reduction_blocks()), "alloc");
+        CK(h->alloc(&h->st_aux, 1), "alloc");
+        CK(cudaMemset(h->st_aux, 0, sizeof(PcgState)), "memset");
         CK(cudaMemset(h->cz, 0, N * sizeof(double)), "memset");
         h->hist_cap = 100001;
         CK(h->alloc(&h->hist, (size_t)h->hist_cap), "alloc");
@@ -525,6 +531,18 @@ int imgm_pcg_solve(imgm_handle* h, const double* dev_b, double* dev_x, double rt
     out->rel_residual = fin.bb > 0 ? std::sqrt(fin.rr / fin.bb) : 0.0;
     out->true_rel_residual = fin.bb > 0 ? std::sqrt(fin.true_rr / fin.bb) : 0.0;
     return fin.status == -5 ? IMGM_ERR_BREAKDOWN : (fin.status == 1 ? IMGM_MAX_ITER : IMGM_OK);
+}
+
+int imgm_residual_norm2(imgm_handle* h, const double* dev_b, const double* dev_x, double* dev_out, void* stream) {
+    int c = check_level(h, h ? h->L : 0, 1);
+    if (c) return c;
+    if (!dev_b || !dev_x || !dev_out) return fail(h, IMGM_ERR_INVALID, "null pointer");
+    cudaStream_t s = (cudaStream_t)stream;
+    LevelDev& F = h->lv[h->L - 1];
+    CK(imgm::launch_apply(F.d, imgm::RESID, dev_x, dev_b, F.t, nullptr, h->gamma, nullptr, s), "residual");
+    CK(imgm::launch_true_residual_norm(F.d.N, F.t, h->partial_aux, h->st_aux, s), "residual norm");
+    CK(cudaMemcpyAsync(dev_out, &h->st_aux->true_rr, sizeof(double), cudaMemcpyDeviceToDevice, s), "norm copy");
+    return IMGM_OK;
 }
 
 int imgm_pcg_solve_host(imgm_handle* h, const double* host_b, double* host_x, double rtol, int maxit,

@@ -15,6 +15,8 @@
 // by the last block to finish.
 #include "kernels.cuh"
 
+#include <algorithm>
+
 namespace imgm {
 namespace {
 
@@ -155,8 +157,8 @@ __global__ void __launch_bounds__(TPB) k_apply(DevLevel L, int mode, const doubl
                                                const double* rin, double* out, double* __restrict__ xs,
                                                double gamma, const int* done) {
     if (done && *done) return;
-    const int64_t stride = (int64_t)gridDim.x * TPB;
-    for (int64_t i = (int64_t)blockIdx.x * TPB + threadIdx.x; i < L.N; i += stride) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < L.N; i += stride) {
         const double ax = row_apply<DIM, P>(L, i, x);
         if (mode == APPLY) {
             out[i] = ax;
@@ -164,6 +166,109 @@ __global__ void __launch_bounds__(TPB) k_apply(DevLevel L, int mode, const doubl
             const double v = (L.rowinfo[i] == -2) ? 0.0 : rin[i] - ax;
             out[i] = v;
             if (mode == RESID_SMOOTH) xs[i] = fma(gamma * L.dinv[i], v, xs[i]);
+        }
+    }
+}
+
+
+// ---------------------------------------------------------------------------------
+// 2-D operator apply on TX x TY tiles with sum factorisation.  The x values of the tile
+// and a p-wide halo are staged in shared memory; the tensor rows then cost
+//   u = M_y x, v = K_y x  on the (TX+2p) x TY strip   (2 (2p+1) FMA per point)
+//   y = K_x u + M_x v     on the TX x TY outputs      (2 (2p+1) FMA per point)
+// i.e. about 4(2p+1) FMA per row instead of 2(2p+1)^2 + 2(2p+1) for the direct sum.
+// Stored rows read their (2p+1)^2 coefficients and take x from the same staged tile.
+// MODE: APPLY, RESID, RESID_SMOOTH as in k_apply; DOT also accumulates sum_i x_i (A x)_i
+// and finishes with alpha = rz / (p^T A p) (the CG step length).
+constexpr int TX = 32, TY = 16;
+
+template <int P, int MODE, bool DOT>
+__global__ void __launch_bounds__(TPB) k_apply_tile2d(DevLevel L, const double* __restrict__ x,
+                                                      const double* rin, double* out, double* __restrict__ xs,
+                                                      double gamma, const int* done, double* partial, PcgState* st) {
+    constexpr int W = 2 * P + 1;
+    constexpr int SX = TX + 2 * P, SY = TY + 2 * P;
+    __shared__ double sx[SY][SX];
+    __shared__ double su[TY][SX];
+    __shared__ double sv[TY][SX];
+    if (done && *done) return;
+    const int m = L.m;
+    const int tiles_x = (m + TX - 1) / TX, tiles_y = (m + TY - 1) / TY;
+    const int ntiles = tiles_x * tiles_y;
+    double acc = 0.0;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int x0 = (tile % tiles_x) * TX, y0 = (tile / tiles_x) * TY;
+        __syncthreads();   // the previous tile's smem reads are done
+        for (int k = threadIdx.x; k < SX * SY; k += TPB) {
+            const int ly = k / SX, lx = k % SX;
+            const int gx = x0 + lx - P, gy = y0 + ly - P;
+            sx[ly][lx] = ((unsigned)gx < (unsigned)m && (unsigned)gy < (unsigned)m) ? x[(int64_t)gy * m + gx] : 0.0;
+        }
+        __syncthreads();
+        // stage 1: along y, for all columns of the strip
+        for (int k = threadIdx.x; k < TY * SX; k += TPB) {
+            const int ly = k / SX, lx = k % SX;
+            const int gy = y0 + ly;
+            double u = 0.0, v = 0.0;
+            if (gy < m) {
+                const double* My = L.M1 + (int64_t)gy * W;
+                const double* Ky = L.K1 + (int64_t)gy * W;
+#pragma unroll
+                for (int o = 0; o < W; ++o) {
+                    const double xv = sx[ly + o][lx];
+                    u = fma(My[o], xv, u);
+                    v = fma(Ky[o], xv, v);
+                }
+            }
+            su[ly][lx] = u;
+            sv[ly][lx] = v;
+        }
+        __syncthreads();
+        // stage 2: along x, one output per thread and step
+        for (int k = threadIdx.x; k < TX * TY; k += TPB) {
+            const int ly = k / TX, lx = k % TX;
+            const int gx = x0 + lx, gy = y0 + ly;
+            if (gx >= m || gy >= m) continue;
+            const int64_t i = (int64_t)gy * m + gx;
+            const int ri = L.rowinfo[i];
+            double y = 0.0;
+            if (ri == -1) {
+                const double* Kx = L.K1 + (int64_t)gx * W;
+                const double* Mx = L.M1 + (int64_t)gx * W;
+#pragma unroll
+                for (int o = 0; o < W; ++o) {
+                    y = fma(Kx[o], su[ly][lx + o], y);
+                    y = fma(Mx[o], sv[ly][lx + o], y);
+                }
+            } else if (ri >= 0) {
+                const double* __restrict__ c = L.band_coef + ri;
+                const int64_t nb = L.nb;
+#pragma unroll
+                for (int oy = 0; oy < W; ++oy)
+#pragma unroll
+                    for (int ox = 0; ox < W; ++ox) y = fma(c[(int64_t)(ox + W * oy) * nb], sx[ly + oy][lx + ox], y);
+            }
+            if (MODE == APPLY) {
+                out[i] = y;
+            } else {
+                const double r = (ri == -2) ? 0.0 : rin[i] - y;
+                out[i] = r;
+                if (MODE == RESID_SMOOTH) xs[i] = fma(gamma * L.dinv[i], r, xs[i]);
+            }
+            if (DOT) acc = fma(sx[ly + P][lx + P], y, acc);
+        }
+    }
+    if (DOT) {
+        double pq;
+        if (finish_reduction(acc, partial, &st->ticket[0], &pq) && threadIdx.x == 0) {
+            st->pq = pq;
+            if (!(pq > 0.0) || !isfinite(pq)) {
+                st->done = 1;
+                st->status = -5;
+                st->alpha = 0.0;
+            } else {
+                st->alpha = st->rz / pq;
+            }
         }
     }
 }
@@ -196,8 +301,8 @@ __global__ void __launch_bounds__(TPB) k_scale_diag(int64_t N, const double* __r
                                                     const double* __restrict__ r, double* __restrict__ x, double gamma,
                                                     const int* done) {
     if (done && *done) return;
-    const int64_t stride = (int64_t)gridDim.x * TPB;
-    for (int64_t i = (int64_t)blockIdx.x * TPB + threadIdx.x; i < N; i += stride) x[i] = gamma * dinv[i] * r[i];
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) x[i] = gamma * dinv[i] * r[i];
 }
 
 // one warp per stored block: gather r_j, z_j = A_j^{-1} r_j, x[idx_j] += gamma z_j
@@ -207,8 +312,8 @@ __global__ void __launch_bounds__(TPB) k_blocks(DevLevel L, const double* __rest
     if (done && *done) return;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     double* rs = sm + (int64_t)wib * L.max_block;
-    const int64_t nwarps = ((int64_t)gridDim.x * TPB) >> 5;
-    for (int64_t b = (((int64_t)blockIdx.x * TPB + threadIdx.x) >> 5); b < L.nblk; b += nwarps) {
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t b = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5); b < L.nblk; b += nwarps) {
         const int64_t s = L.blk_ptr[b];
         const int nj = (int)(L.blk_ptr[b + 1] - s);
         const double* __restrict__ A = L.blk_val + L.blk_vptr[b];
@@ -230,8 +335,8 @@ __global__ void __launch_bounds__(TPB) k_restrict(DevLevel F, DevLevel C, const 
     if (done && *done) return;
     constexpr int P2 = P + 2;
     const int mc = C.m, mf = F.m;
-    const int64_t stride = (int64_t)gridDim.x * TPB;
-    for (int64_t i = (int64_t)blockIdx.x * TPB + threadIdx.x; i < C.N; i += stride) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < C.N; i += stride) {
         if (C.rowinfo[i] == -2) {
             rc[i] = 0.0;
             if (xc) xc[i] = 0.0;
@@ -266,8 +371,8 @@ __global__ void __launch_bounds__(TPB) k_prolong(DevLevel F, DevLevel C, const d
                                                  double* __restrict__ e, double* __restrict__ x, const int* done) {
     if (done && *done) return;
     const int mc = C.m, mf = F.m, TW = F.TW;
-    const int64_t stride = (int64_t)gridDim.x * TPB;
-    for (int64_t a = (int64_t)blockIdx.x * TPB + threadIdx.x; a < F.N; a += stride) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; a < F.N; a += stride) {
         if (F.rowinfo[a] == -2) {
             e[a] = 0.0;
             continue;
@@ -299,8 +404,8 @@ __global__ void __launch_bounds__(TPB) k_coarse(const int32_t* __restrict__ rows
                                                 const int* done) {
     if (done && *done) return;
     const int lane = threadIdx.x & 31;
-    const int64_t nwarps = ((int64_t)gridDim.x * TPB) >> 5;
-    for (int64_t a = (((int64_t)blockIdx.x * TPB + threadIdx.x) >> 5); a < nc; a += nwarps) {
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t a = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5); a < nc; a += nwarps) {
         const double* row = Cinv + a * nc;
         double acc = 0.0;
         for (int b = lane; b < nc; b += 32) acc = fma(row[b], r[rows[b]], acc);
@@ -440,6 +545,37 @@ inline int grid_for(int64_t n) {
     return (int)g;
 }
 
+int num_sms() {
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 148;
+    }
+    return sms;
+}
+
+// One row per thread.  Large levels: 256-thread blocks.  Small levels: blocks just big
+// enough to give every SM about two of them, so that FP64 work (2 FMA/clk per SM) is
+// spread over the whole GPU instead of a handful of SMs.
+struct RowLaunch {
+    int grid, block;
+};
+inline RowLaunch row_launch(int64_t n) {
+    const int64_t want = 2LL * num_sms();
+    int64_t tpb = (n + want - 1) / want;
+    tpb = ((tpb + 31) / 32) * 32;
+    if (tpb < 32) tpb = 32;
+    if (tpb > TPB) tpb = TPB;
+    int64_t g = (n + tpb - 1) / tpb;
+    if (g < 1) g = 1;
+    if (g > 65535LL * 8) g = 65535LL * 8;
+    return {(int)g, (int)tpb};
+}
+
+inline int tiles_2d(int m) { return ((m + TX - 1) / TX) * ((m + TY - 1) / TY); }
+
 }  // namespace
 
 int reduction_blocks() {
@@ -463,52 +599,83 @@ int reduction_blocks() {
         else return cudaErrorInvalidValue;                             \
     } while (0)
 
+template <int P>
+cudaError_t launch_tile2d(const DevLevel& L, int mode, const double* x, const double* rin, double* out, double* xs,
+                          double gamma, const int* done, cudaStream_t s) {
+    const int g = tiles_2d(L.m);
+    if (mode == APPLY)
+        k_apply_tile2d<P, APPLY, false><<<g, TPB, 0, s>>>(L, x, rin, out, xs, gamma, done, nullptr, nullptr);
+    else if (mode == RESID)
+        k_apply_tile2d<P, RESID, false><<<g, TPB, 0, s>>>(L, x, rin, out, xs, gamma, done, nullptr, nullptr);
+    else
+        k_apply_tile2d<P, RESID_SMOOTH, false><<<g, TPB, 0, s>>>(L, x, rin, out, xs, gamma, done, nullptr, nullptr);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_apply(const DevLevel& L, int mode, const double* x, const double* rin, double* out, double* xs,
                          double gamma, const int* done, cudaStream_t s) {
-    IMGM_DISPATCH(L.dim, L.p, (k_apply<D, Q><<<grid_for(L.N), TPB, 0, s>>>(L, mode, x, rin, out, xs, gamma, done)));
+    // tiles when there are enough of them to fill the GPU; one row per thread otherwise
+    if (L.dim == 2 && tiles_2d(L.m) >= num_sms()) {
+        if (L.p == 1) return launch_tile2d<1>(L, mode, x, rin, out, xs, gamma, done, s);
+        if (L.p == 2) return launch_tile2d<2>(L, mode, x, rin, out, xs, gamma, done, s);
+        if (L.p == 3) return launch_tile2d<3>(L, mode, x, rin, out, xs, gamma, done, s);
+    }
+    const RowLaunch rl = row_launch(L.N);
+    IMGM_DISPATCH(L.dim, L.p, (k_apply<D, Q><<<rl.grid, rl.block, 0, s>>>(L, mode, x, rin, out, xs, gamma, done)));
     return cudaGetLastError();
 }
 
 cudaError_t launch_apply_pq(const DevLevel& L, const double* p, double* q, double* partial, PcgState* st,
                             cudaStream_t s) {
+    if (L.dim == 2) {
+        const int g = std::min(tiles_2d(L.m), reduction_blocks());
+        if (L.p == 1) k_apply_tile2d<1, APPLY, true><<<g, TPB, 0, s>>>(L, p, nullptr, q, nullptr, 0.0, &st->done, partial, st);
+        else if (L.p == 2) k_apply_tile2d<2, APPLY, true><<<g, TPB, 0, s>>>(L, p, nullptr, q, nullptr, 0.0, &st->done, partial, st);
+        else if (L.p == 3) k_apply_tile2d<3, APPLY, true><<<g, TPB, 0, s>>>(L, p, nullptr, q, nullptr, 0.0, &st->done, partial, st);
+        else return cudaErrorInvalidValue;
+        return cudaGetLastError();
+    }
     IMGM_DISPATCH(L.dim, L.p, (k_apply_pq<D, Q><<<reduction_blocks(), TPB, 0, s>>>(L, p, q, partial, st)));
     return cudaGetLastError();
 }
 
 cudaError_t launch_scale_diag(const DevLevel& L, const double* r, double* x, double gamma, const int* done,
                               cudaStream_t s) {
-    k_scale_diag<<<grid_for(L.N), TPB, 0, s>>>(L.N, L.dinv, r, x, gamma, done);
+    const RowLaunch rl = row_launch(L.N);
+    k_scale_diag<<<rl.grid, rl.block, 0, s>>>(L.N, L.dinv, r, x, gamma, done);
     return cudaGetLastError();
 }
 
 cudaError_t launch_blocks(const DevLevel& L, const double* r, double* x, double gamma, const int* done,
                           cudaStream_t s) {
     if (L.nblk == 0) return cudaSuccess;
-    const int warps = TPB / 32;
+    const int warps = 2;                        // small blocks: spread the FP64 work over all SMs
     int64_t g = (L.nblk + warps - 1) / warps;
-    if (g > 4096) g = 4096;
+    if (g > 65535) g = 65535;
     size_t smem = (size_t)warps * L.max_block * sizeof(double);
-    k_blocks<<<(int)g, TPB, smem, s>>>(L, r, x, gamma, done);
+    k_blocks<<<(int)g, 32 * warps, smem, s>>>(L, r, x, gamma, done);
     return cudaGetLastError();
 }
 
 cudaError_t launch_restrict(const DevLevel& F, const DevLevel& C, const double* rf, double* rc, double* xc,
                             double gamma, const int* done, cudaStream_t s) {
-    IMGM_DISPATCH(F.dim, F.p, (k_restrict<D, Q><<<grid_for(C.N), TPB, 0, s>>>(F, C, rf, rc, xc, gamma, done)));
+    const RowLaunch rl = row_launch(C.N);
+    IMGM_DISPATCH(F.dim, F.p, (k_restrict<D, Q><<<rl.grid, rl.block, 0, s>>>(F, C, rf, rc, xc, gamma, done)));
     return cudaGetLastError();
 }
 
 cudaError_t launch_prolong(const DevLevel& F, const DevLevel& C, const double* xc, double* e, double* x,
                            const int* done, cudaStream_t s) {
-    IMGM_DISPATCH(F.dim, F.p, (k_prolong<D, Q><<<grid_for(F.N), TPB, 0, s>>>(F, C, xc, e, x, done)));
+    const RowLaunch rl = row_launch(F.N);
+    IMGM_DISPATCH(F.dim, F.p, (k_prolong<D, Q><<<rl.grid, rl.block, 0, s>>>(F, C, xc, e, x, done)));
     return cudaGetLastError();
 }
 
 cudaError_t launch_coarse(const int32_t* rows, const double* Cinv, int nc, const double* r, double* x,
                           const int* done, cudaStream_t s) {
     if (nc == 0) return cudaSuccess;
-    const int warps = TPB / 32;
-    k_coarse<<<(nc + warps - 1) / warps, TPB, 0, s>>>(rows, Cinv, nc, r, x, done);
+    const int warps = 2;
+    k_coarse<<<(nc + warps - 1) / warps, 32 * warps, 0, s>>>(rows, Cinv, nc, r, x, done);
     return cudaGetLastError();
 }
 

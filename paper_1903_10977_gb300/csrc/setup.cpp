@@ -24,6 +24,7 @@ namespace {
 
 constexpr int FULL = 0, EMPTY = 1, CUT = 2;
 constexpr double PRUNE_RATIO = 1e-16;   // Remark 3.3
+constexpr int MAX_COARSE_ROWS = 8192;   // dense coarsest-level inverse: at most 512 MiB
 
 // ----------------------------------------------------------------------------------
 // Small dense linear algebra (row-major n x n)
@@ -1247,6 +1248,11 @@ struct Builder {
         for (int64_t r = 0; r < c.N; ++r)
             if (c.active[r]) rows.push_back(r);
         const int nr = (int)rows.size();
+        if (nr > MAX_COARSE_ROWS) {
+            err = "the coarsest level has " + std::to_string(nr) + " active functions; its dense inverse allows at most " +
+                  std::to_string(MAX_COARSE_ROWS) + " (use more levels)";
+            return false;
+        }
         std::vector<int64_t> pos(c.N, -1);
         for (int a = 0; a < nr; ++a) pos[rows[a]] = a;
         std::vector<double> A((size_t)nr * nr, 0.0), row(ncoef);
@@ -1295,9 +1301,10 @@ struct Builder {
             build_transfer(li);
             build_coarse(li - 1);
         }
+        if (!build_coarse_solve(err)) return false;
         for (int li = L - 1; li >= 1; --li)
             if (!build_blocks(li, err)) return false;
-        return build_coarse_solve(err);
+        return true;
     }
 };
 

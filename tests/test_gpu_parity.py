@@ -178,6 +178,16 @@ def test_pcg_fixed_iterations(pair):
     np.testing.assert_allclose(host(hist), hist_ref, rtol=1e-8)
 
 
+def test_residual_norm(pair):
+    pr, d, H, S = pair
+    x = random_grid_vector(d.n_active, 70)
+    got = float(host(S.residual_norm2(dev(d.to_full(d.b)), dev(d.to_full(x))))[0])
+    r = d.b - d.A @ x
+    ref = float(r @ r)
+    record(rel=abs(got - ref) / ref)
+    assert abs(got - ref) <= 1e-12 * ref
+
+
 def test_pcg_converged(pair):
     """Both reach 1e-8.  Over hundreds of iterations (additive Schwarz with gamma =
     (p+1)^-d converges slowly for p = 3) the two finite-precision CG runs drift apart by a

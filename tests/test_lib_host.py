@@ -141,6 +141,7 @@ def test_coarse_inverse(pair):
     (dict(degree=4), "degree"),
     (dict(basis=1, degree=2), "Lagrange"),
     (dict(levels=1), "levels"),
+    (dict(n=256, levels=2), "dense inverse allows at most"),   # coarsest level too large to invert densely
 ])
 def test_invalid_configurations_are_rejected(kw, err):
     args = dict(dim=2, centers=[[0.5, 0.5]], radii=[0.2], n=32, degree=2, levels=3, depth=0, bc=1, host_only=True)
