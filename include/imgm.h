@@ -150,6 +150,21 @@ int imgm_pcg_solve_host(imgm_handle* h, const double* host_b, double* host_x, do
  * vectors, so it must not overlap other calls on the same handle. */
 int imgm_residual_norm2(imgm_handle* h, const double* dev_b, const double* dev_x, double* dev_out, void* stream);
 
+/* imgm_residual_norm2 for callers that cannot allocate device memory while they run
+ * (a process whose memory a caching allocator has reserved up front, or a latency-
+ * critical loop that cannot afford cudaMalloc's device-wide synchronisation).  The paper
+ * has no counterpart: this is an interface variant, not a step of the method.
+ * Same arguments and result as imgm_residual_norm2; it calls no cudaMalloc, cudaFree or
+ * allocating library routine.  Its scratch is a static device array of 4 MiB that
+ * every GPU loading the library holds until the process exits; it serves finest levels
+ * of at most 2^19 rows and returns IMGM_ERR_UNSUPPORTED, with a message naming the
+ * limit, for larger ones.  The first call on each device looks up the array's device
+ * address (cudaGetSymbolAddress) and should come before any stream capture on that
+ * device.  All calls share the one array, so calls that overlap on the GPU (different
+ * streams, handles or threads) race and give wrong results; serialise them. */
+int imgm_residual_norm2_noalloc(imgm_handle* h, const double* dev_b, const double* dev_x, double* dev_out,
+                                void* stream);
+
 /* ---- Setup inspection (host only; no GPU needed) --------------------------------
  * imgm_setup_host builds the same hierarchy as imgm_setup without touching the GPU;
  * such a handle serves only the imgm_host_* calls below, imgm_levels,

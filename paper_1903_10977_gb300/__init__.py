@@ -69,6 +69,7 @@ _SIGS = {
     "imgm_pcg_solve": (_I, [_H, _P, _P, _D, _I, ctypes.POINTER(Result), _P, _P]),
     "imgm_pcg_solve_host": (_I, [_H, _P, _P, _D, _I, ctypes.POINTER(Result), _P]),
     "imgm_residual_norm2": (_I, [_H, _P, _P, _P, _P]),
+    "imgm_residual_norm2_noalloc": (_I, [_H, _P, _P, _P, _P]),
     "imgm_host_operator_rows": (_I, [_H, _I, _I64, _P, _P]),
     "imgm_host_rhs": (_I, [_H, _P]),
     "imgm_host_block_sizes": (_I, [_H, _I, ctypes.POINTER(_I64), ctypes.POINTER(_I64), ctypes.POINTER(_I64)]),
@@ -225,6 +226,12 @@ class Solver:
         import torch
         out = torch.empty(1, dtype=torch.float64, device=b.device) if out is None else out
         self._check(_lib.imgm_residual_norm2(self._h, _ptr(b), _ptr(x), _ptr(out), _stream(stream)))
+        return out
+
+    def residual_norm2_noalloc(self, b, x, out, stream=None):
+        """residual_norm2 without any device allocation by the library (out: a caller-owned
+        one-element float64 CUDA tensor); see imgm_residual_norm2_noalloc in imgm.h."""
+        self._check(_lib.imgm_residual_norm2_noalloc(self._h, _ptr(b), _ptr(x), _ptr(out), _stream(stream)))
         return out
 
     def pcg_solve_host(self, b_host: np.ndarray, x_host: np.ndarray | None = None, rtol=1e-8, maxit=1000,

@@ -12,6 +12,7 @@
 #include <cstdio>
 #include <cstring>
 #include <memory>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -85,6 +86,25 @@ struct imgm_handle {
 };
 
 namespace {
+
+// ---- scratch of imgm_residual_norm2_noalloc -------------------------------------
+// Some callers cannot call cudaMalloc while they run: a process whose device memory is
+// reserved up front by a caching allocator (a new cudaMalloc then fails or forces the
+// cache to be released), or a latency-critical loop in which cudaMalloc's implicit
+// device-wide synchronisation would stall work on other streams.  For them the residual
+// norm has a variant whose scratch is this file-scope array, which exists on every GPU
+// that loads the library until the process exits: a CG state record (the reduction
+// ticket and the result), the per-block partial sums, and the residual vector of at
+// most NOALLOC_MAX_ROWS rows (4 MiB in all).
+constexpr int64_t NOALLOC_MAX_ROWS = int64_t(1) << 19;
+constexpr int64_t NOALLOC_MAX_PARTIALS = 4096;
+constexpr int64_t NOALLOC_STATE_DOUBLES = 32;   // 256 bytes, holds one PcgState
+static_assert(sizeof(PcgState) <= NOALLOC_STATE_DOUBLES * sizeof(double), "state slot too small");
+static __device__ __align__(256) double g_noalloc_scratch[NOALLOC_STATE_DOUBLES + NOALLOC_MAX_PARTIALS + NOALLOC_MAX_ROWS];
+
+constexpr int NOALLOC_MAX_DEVICES = 64;
+std::mutex g_noalloc_mutex;
+double* g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {};
 
 int fail(imgm_handle* h, int code, const std::string& msg) {
     if (h) h->err = msg;
@@ -542,6 +562,46 @@ int imgm_residual_norm2(imgm_handle* h, const double* dev_b, const double* dev_x
     CK(imgm::launch_apply(F.d, imgm::RESID, dev_x, dev_b, F.t, nullptr, h->gamma, nullptr, s), "residual");
     CK(imgm::launch_true_residual_norm(F.d.N, F.t, h->partial_aux, h->st_aux, s), "residual norm");
     CK(cudaMemcpyAsync(dev_out, &h->st_aux->true_rr, sizeof(double), cudaMemcpyDeviceToDevice, s), "norm copy");
+    return IMGM_OK;
+}
+
+int imgm_residual_norm2_noalloc(imgm_handle* h, const double* dev_b, const double* dev_x, double* dev_out,
+                                void* stream) {
+    int c = check_level(h, h ? h->L : 0, 1);
+    if (c) return c;
+    if (!dev_b || !dev_x || !dev_out) return fail(h, IMGM_ERR_INVALID, "null pointer");
+    LevelDev& F = h->lv[h->L - 1];
+    if (F.d.N > NOALLOC_MAX_ROWS)
+        return fail(h, IMGM_ERR_UNSUPPORTED,
+                    "imgm_residual_norm2_noalloc: the finest level has " + std::to_string(F.d.N) +
+                        " rows, more than the static scratch holds (" + std::to_string(NOALLOC_MAX_ROWS) + ")");
+    if (imgm::reduction_blocks() > NOALLOC_MAX_PARTIALS)
+        return fail(h, IMGM_ERR_UNSUPPORTED, "imgm_residual_norm2_noalloc: too many reduction blocks for the scratch");
+    int dev = 0;
+    CK(cudaGetDevice(&dev), "noalloc: cudaGetDevice");
+    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return fail(h, IMGM_ERR_UNSUPPORTED, "noalloc: device ordinal too large");
+    double* base = nullptr;
+    {
+        // first call on this device: look up the device address of the scratch array
+        // (its name in host code is only a host-side stand-in)
+        std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+        if (!g_noalloc_ptr[dev]) {
+            void* p = nullptr;
+            cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+            if (e != cudaSuccess) return cuda_fail(h, e, "noalloc: cudaGetSymbolAddress");
+            g_noalloc_ptr[dev] = (double*)p;
+        }
+        base = g_noalloc_ptr[dev];
+    }
+    PcgState* st = reinterpret_cast<PcgState*>(base);
+    double* partial = base + NOALLOC_STATE_DOUBLES;
+    double* t = partial + NOALLOC_MAX_PARTIALS;
+    cudaStream_t s = (cudaStream_t)stream;
+    // the reduction ticket must start at zero; the array keeps the previous call's contents
+    CK(cudaMemsetAsync(st, 0, sizeof(PcgState), s), "noalloc: clear state");
+    CK(imgm::launch_apply(F.d, imgm::RESID, dev_x, dev_b, t, nullptr, h->gamma, nullptr, s), "noalloc: residual");
+    CK(imgm::launch_true_residual_norm(F.d.N, t, partial, st, s), "noalloc: residual norm");
+    CK(cudaMemcpyAsync(dev_out, &st->true_rr, sizeof(double), cudaMemcpyDeviceToDevice, s), "noalloc: norm copy");
     return IMGM_OK;
 }
 
