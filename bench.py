@@ -3,7 +3,9 @@
 Workload (one "step" = one whole solve from x0 = 0, every hot-path step included):
 2-D Poisson on [0,1]^2 minus 10 seeded discs (r ~ U(0.03, 0.1)), 512 x 512 background
 grid, quadratic open B-splines, 6 levels, depth-0 cut cells, symmetric Nitsche on the
-immersed boundary, additive Schwarz smoothing, FP64 throughout.
+immersed boundary, additive Schwarz smoothing.  The timed solves run the V-cycle in FP32
+on Jacobi-scaled data inside the FP64 CG (--precision mixed, default); the plain FP64
+path is timed the same way beside it ("fp64" in the JSON line, "speedup_vs_fp64").
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -28,7 +30,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "DOF/s to rel. residual 1e-8 (PCG+MG) vs plain FP64 GPU; HBM GB/s of roofline"
-WORKLOAD = "poisson2d-512x512-10discs-bspline-p2-6levels-nitsche-fp64"
+WORKLOAD = "poisson2d-512x512-10discs-bspline-p2-6levels-nitsche"
 PRESET = "discs10_512_p2"
 RTOL = 1e-8
 MAXIT = 2000
@@ -138,14 +140,15 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ GPU arm
-def launches_per_solve(S, iterations: int) -> int:
-    per_level = 0
-    for l in range(2, S.L + 1):
-        per_level += 4 + (2 if S.level_info(l)["n_blocks"] > 0 else 0)
-    vcycle = per_level + 1
-    start = 3 + vcycle + 1 + 1
-    it = 5 + vcycle + 1
-    return start + iterations * it + 2
+def launches_per_solve(S, iterations: int, cluster_coarse: bool) -> int:
+    """Kernel launches of one solve: start, `iterations` loop bodies, finish."""
+    if cluster_coarse:      # finest level: 6 kernels around one cluster launch for all coarse levels
+        vcycle = 4 + (2 if S.level_info(S.L)["n_blocks"] > 0 else 0) + 1
+    else:
+        vcycle = 1 + sum(4 + (2 if S.level_info(l)["n_blocks"] > 0 else 0) for l in range(2, S.L + 1))
+    start = 3 + vcycle + 1 + 1          # residual, norms, V-cycle input, V-cycle, direction, loop condition
+    it = 5 + vcycle + 1                 # apply+dot, update, V-cycle, rz, xpay, loop condition
+    return start + iterations * it + 2  # final residual and its norm
 
 
 def apply_flops(S) -> float:
@@ -177,9 +180,13 @@ def run_ours(args, rank, world, local_rank):
 
     pr = preset(PRESET)
     lay = config_layout(pr.layout, args.seed + rank)
+    mixed = args.precision == "mixed"
     t0 = time.perf_counter()
-    S = lib.Solver(pr.dim, lay.centers, lay.radii, pr.n, pr.degree, pr.levels, pr.depth, pr.bc, basis=pr.basis)
+    S = lib.Solver(pr.dim, lay.centers, lay.radii, pr.n, pr.degree, pr.levels, pr.depth, pr.bc, basis=pr.basis,
+                   precision=1 if mixed else 0)
     setup_s = time.perf_counter() - t0
+    S64 = S if not mixed else lib.Solver(pr.dim, lay.centers, lay.radii, pr.n, pr.degree, pr.levels, pr.depth,
+                                         pr.bc, basis=pr.basis, precision=0)
     info = S.level_info(S.L)
     n_active, n_grid = info["n_active"], info["n_grid"]
     b = S.rhs()
@@ -187,31 +194,28 @@ def run_ours(args, rank, world, local_rank):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")   # > 129 MB L2
     stream = torch.cuda.current_stream()
 
-    def step():
-        x.zero_()
-        _, res, _ = S.pcg_solve(b, x, rtol=RTOL, maxit=MAXIT)
-        return res
-
-    for _ in range(args.warmup):
-        res = step()
-    # timed region: each solve bracketed by events after an L2 flush
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    results = []
-    with ClockSampler(local_rank) as clk:
+    def timed_solves(solver, steps, warmup, clock=None):
+        """Device time of `steps` whole solves, each after an L2 flush (flush outside the events)."""
+        for _ in range(warmup):
+            x.zero_()
+            solver.pcg_solve(b, x, rtol=RTOL, maxit=MAXIT)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        res = []
         barrier()
-        wall0 = time.perf_counter()
-        for k in range(args.steps):
+        for k in range(steps):
             flush.fill_(float(k))
             x.zero_()
             ev[k][0].record(stream)
-            _, res, _ = S.pcg_solve(b, x, rtol=RTOL, maxit=MAXIT)
+            _, r, _ = solver.pcg_solve(b, x, rtol=RTOL, maxit=MAXIT)
             ev[k][1].record(stream)
-            results.append(res)
+            res.append(r)
         barrier()
-        wall = time.perf_counter() - wall0
-    step_ms = [s.elapsed_time(e) for s, e in ev]
-    t_dev = sum(step_ms) / 1e3
+        return sum(a.elapsed_time(c) for a, c in ev) / 1e3, res
+
+    with ClockSampler(local_rank) as clk:
+        t_dev, results = timed_solves(S, args.steps, args.warmup)
     clocks = clk.summary()
+    t64, res64 = (t_dev, results) if not mixed else timed_solves(S64, args.steps, args.warmup)
 
     # end to end: host (pinned) b in, host x out, through the C-ABI
     bh = torch.empty(n_grid, dtype=torch.float64, pin_memory=True)
@@ -228,7 +232,7 @@ def run_ours(args, rank, world, local_rank):
     barrier()
     t_e2e = time.perf_counter() - e0
 
-    # dominant kernel: finest-level operator apply, timed alone with events on its stream
+    # FP64 finest-level operator apply (run once per CG iteration in both paths), timed alone
     xs = torch.randn(n_grid, dtype=torch.float64, device="cuda") * torch.as_tensor(
         S.active_mask(), dtype=torch.float64, device="cuda")
     ys = torch.empty_like(xs)
@@ -246,14 +250,15 @@ def run_ours(args, rank, world, local_rank):
     apply_ms = k0.elapsed_time(k1) / reps
 
     if dist is not None:
-        t = torch.tensor([t_dev, t_e2e, wall], dtype=torch.float64, device="cuda")
+        t = torch.tensor([t_dev, t64, t_e2e], dtype=torch.float64, device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_dev, t_e2e, wall = (float(v) for v in t.tolist())
+        t_dev, t64, t_e2e = (float(v) for v in t.tolist())
         dist.destroy_process_group()
     if rank != 0:
         return None
     total_units = n_active * args.steps * world
     value = total_units / t_dev
+    value64 = total_units / t64
     its = [r["iterations"] for r in results]
     flops = apply_flops(S)
     achieved = flops / (apply_ms * 1e-3) / 1e12
@@ -261,18 +266,22 @@ def run_ours(args, rank, world, local_rank):
     line = {
         "metric": METRIC, "value": value, "unit": "DOF/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * t_dev / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32" if mixed else "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "dim": 2, "n": pr.n, "basis": "bspline", "degree": pr.degree,
                    "levels": pr.levels, "holes": lay.n_holes, "depth": pr.depth, "bc": "nitsche", "rtol": RTOL,
                    "n_active": n_active, "n_grid": n_grid, "seed": args.seed, "parallelism": f"replicas{world}",
+                   "vcycle": "fp32 (Jacobi-scaled) in fp64 flexible CG" if mixed else "fp64",
                    "l2": "flushed (256 MiB write) before every timed solve, flush outside the events",
                    "iterations": its[0], "true_rel_residual": results[-1]["true_rel_residual"],
                    "setup_s": setup_s},
+        "fp64": {"value": value64, "unit": "DOF/s", "ms_per_step": 1e3 * t64 / args.steps,
+                 "iterations": res64[0]["iterations"], "true_rel_residual": res64[-1]["true_rel_residual"]},
+        "speedup_vs_fp64": value / value64,
         "e2e": {"value": total_units / t_e2e, "unit": "DOF/s", "h2d_bytes_per_step": 8 * n_grid,
                 "d2h_bytes_per_step": 8 * n_grid},
-        "gpu_launches": launches_per_solve(S, its[0]) * args.steps,
+        "gpu_launches": launches_per_solve(S, its[0], cluster_coarse=mixed) * args.steps,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                     "traffic": None, "kernel": "k_apply (finest-level operator apply, FP64)",
+                     "traffic": None, "kernel": "k_apply_tile2d<double> (finest-level operator apply, FP64)",
                      "peak_source": "derived: " + FP64_PEAK_NOTE, "flops_per_launch": flops,
                      "launch_ms": apply_ms},
         "clocks": clocks,
@@ -282,6 +291,8 @@ def run_ours(args, rank, world, local_rank):
             line["cpu_baseline"] = cpu_baseline_entry(run_oracle(reps=1, seed=args.seed))
         except Exception as e:  # the GPU number stands without it
             line["cpu_baseline"] = {"error": str(e)[:200]}
+    if S64 is not S:
+        S64.close()
     S.close()
     return line
 
@@ -311,6 +322,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"],
+                    help="V-cycle arithmetic of the timed solves (the FP64 path is timed beside it)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

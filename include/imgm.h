@@ -64,6 +64,8 @@ typedef struct {
     int depth;               /* cut-cell bisection depth (Sec. 2, Fig. 1) */
     int bc;                  /* 0 = penalty beta = 2/h (the paper's), 1 = symmetric Nitsche */
     double gamma;            /* additive Schwarz relaxation; <= 0 selects 1/(p+1)^d (Eq. applyCS) */
+    int precision;           /* V-cycle arithmetic: 0 = FP64; 1 = FP32 on Jacobi-scaled data inside the
+                                FP64 CG, which then uses the flexible (Polak-Ribiere) beta */
 } imgm_config;
 
 typedef struct {

@@ -34,7 +34,30 @@ struct LevelDev {
     double* r = nullptr;   // restricted residual (level < L)
     double* t = nullptr;   // residual after smoothing
     double* e = nullptr;   // prolongated correction
+    // the same in FP32 and Jacobi-scaled variables (mixed-precision V-cycle)
+    imgm::DevLevelT<float> fd;
+    float *fx = nullptr, *fr = nullptr, *ft = nullptr, *fe = nullptr;
     imgm_level_info info{};
+};
+
+// typed access to a level's data and V-cycle vectors
+template <typename T>
+struct Acc;
+template <>
+struct Acc<double> {
+    static const imgm::DevLevelT<double>& d(const LevelDev& L) { return L.d; }
+    static double* x(LevelDev& L) { return L.x; }
+    static double* r(LevelDev& L) { return L.r; }
+    static double* t(LevelDev& L) { return L.t; }
+    static double* e(LevelDev& L) { return L.e; }
+};
+template <>
+struct Acc<float> {
+    static const imgm::DevLevelT<float>& d(const LevelDev& L) { return L.fd; }
+    static float* x(LevelDev& L) { return L.fx; }
+    static float* r(LevelDev& L) { return L.fr; }
+    static float* t(LevelDev& L) { return L.ft; }
+    static float* e(LevelDev& L) { return L.fe; }
 };
 
 }  // namespace
@@ -48,7 +71,13 @@ struct imgm_handle {
     std::vector<void*> allocs;
     int32_t* c_rows = nullptr;
     double* c_inv = nullptr;
+    float* f_c_inv = nullptr;
     int nc = 0;
+    int precision = 0;                 // 0: FP64 V-cycle, 1: FP32 V-cycle in the FP64 CG
+    float *zf = nullptr, *rf = nullptr, *zpf = nullptr;   // finest FP32 V-cycle output, input, previous output
+    imgm::VcycleCoarse* vc = nullptr;  // device copy of the coarse levels for the cluster V-cycle (FP32)
+    int vc_top = -1;                   // highest level index the cluster kernel handles (-1: not used)
+    int vc_max_block = 1;
     double* b = nullptr;               // built-in right-hand side
     // CG state
     double *cx = nullptr, *cr = nullptr, *cp = nullptr, *cq = nullptr, *cz = nullptr, *cb = nullptr;
@@ -129,37 +158,87 @@ int check_level(imgm_handle* h, int level, int min_level) {
     return IMGM_OK;
 }
 
+template <typename T>
+const T* coarse_inverse(const imgm_handle* h);
+template <>
+const double* coarse_inverse<double>(const imgm_handle* h) { return h->c_inv; }
+template <>
+const float* coarse_inverse<float>(const imgm_handle* h) { return h->f_c_inv; }
+
 // One V-cycle (Algorithm 1) from the finest level.  On entry z = gamma * dinv .* r
 // (the diagonal part of the first smoothing step); on exit z = B r.  r is not modified.
-cudaError_t enqueue_vcycle(imgm_handle* h, const double* r, double* z, const int* done, cudaStream_t s) {
+// T = float runs it in FP32 on the Jacobi-scaled data (r and z then are r^, z^).
+template <typename T>
+int cluster_top(const imgm_handle* h);
+template <>
+int cluster_top<double>(const imgm_handle*) { return -1; }
+template <>
+int cluster_top<float>(const imgm_handle* h) { return h->vc_top; }
+
+template <typename T>
+cudaError_t enqueue_vcycle(imgm_handle* h, const T* r, T* z, const int* done, cudaStream_t s) {
+    using A = Acc<T>;
     const int L = h->L;
     const double g = h->gamma;
     cudaError_t e;
+    const int ct = cluster_top<T>(h);
+    if (ct >= 0) {
+        // levels above the cluster's: separate kernels, then one cluster launch for the rest
+        for (int li = L - 1; li > ct; --li) {
+            LevelDev& F = h->lv[li];
+            LevelDev& C = h->lv[li - 1];
+            const T* rl = (li == L - 1) ? r : A::r(F);
+            T* xl = (li == L - 1) ? z : A::x(F);
+            if ((e = imgm::launch_blocks<T>(A::d(F), rl, xl, g, done, s)) != cudaSuccess) return e;
+            if ((e = imgm::launch_apply<T>(A::d(F), imgm::RESID, xl, rl, A::t(F), nullptr, g, done, s)) != cudaSuccess)
+                return e;
+            T* xc = (li - 1 >= 1) ? A::x(C) : nullptr;
+            if ((e = imgm::launch_restrict<T>(A::d(F), A::d(C), A::t(F), A::r(C), xc, g, done, s)) != cudaSuccess)
+                return e;
+        }
+        if ((e = imgm::launch_vcycle_cluster(h->dim, h->p, h->vc, h->vc_max_block, done, s)) != cudaSuccess) return e;
+        for (int li = ct + 1; li <= L - 1; ++li) {
+            LevelDev& F = h->lv[li];
+            LevelDev& C = h->lv[li - 1];
+            T* xl = (li == L - 1) ? z : A::x(F);
+            if ((e = imgm::launch_prolong<T>(A::d(F), A::d(C), A::x(C), A::e(F), xl, done, s)) != cudaSuccess) return e;
+            if ((e = imgm::launch_apply<T>(A::d(F), imgm::RESID_SMOOTH, A::e(F), A::t(F), A::t(F), xl, g, done, s)) !=
+                cudaSuccess)
+                return e;
+            if ((e = imgm::launch_blocks<T>(A::d(F), A::t(F), xl, g, done, s)) != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    }
     for (int li = L - 1; li >= 1; --li) {
         LevelDev& F = h->lv[li];
         LevelDev& C = h->lv[li - 1];
-        const double* rl = (li == L - 1) ? r : F.r;
-        double* xl = (li == L - 1) ? z : F.x;
+        const T* rl = (li == L - 1) ? r : A::r(F);
+        T* xl = (li == L - 1) ? z : A::x(F);
         // line 4: x = gamma M^{-1} r (the one-function blocks were applied by the producer of r)
-        if ((e = imgm::launch_blocks(F.d, rl, xl, g, done, s)) != cudaSuccess) return e;
+        if ((e = imgm::launch_blocks<T>(A::d(F), rl, xl, g, done, s)) != cudaSuccess) return e;
         // line 5: t = r - A x
-        if ((e = imgm::launch_apply(F.d, imgm::RESID, xl, rl, F.t, nullptr, g, done, s)) != cudaSuccess) return e;
+        if ((e = imgm::launch_apply<T>(A::d(F), imgm::RESID, xl, rl, A::t(F), nullptr, g, done, s)) != cudaSuccess)
+            return e;
         // line 7: r_c = R t, and the diagonal part of the coarse pre-smoothing step
-        double* xc = (li - 1 >= 1) ? C.x : nullptr;
-        if ((e = imgm::launch_restrict(F.d, C.d, F.t, C.r, xc, g, done, s)) != cudaSuccess) return e;
+        T* xc = (li - 1 >= 1) ? A::x(C) : nullptr;
+        if ((e = imgm::launch_restrict<T>(A::d(F), A::d(C), A::t(F), A::r(C), xc, g, done, s)) != cudaSuccess) return e;
     }
     // line 14: direct solve on level 1
-    if ((e = imgm::launch_coarse(h->c_rows, h->c_inv, h->nc, h->lv[0].r, h->lv[0].x, done, s)) != cudaSuccess) return e;
+    if ((e = imgm::launch_coarse<T>(h->c_rows, coarse_inverse<T>(h), h->nc, A::r(h->lv[0]), A::x(h->lv[0]), done, s)) !=
+        cudaSuccess)
+        return e;
     for (int li = 1; li <= L - 1; ++li) {
         LevelDev& F = h->lv[li];
         LevelDev& C = h->lv[li - 1];
-        double* xl = (li == L - 1) ? z : F.x;
+        T* xl = (li == L - 1) ? z : A::x(F);
         // line 9: e = R^T x_c, x += e
-        if ((e = imgm::launch_prolong(F.d, C.d, C.x, F.e, xl, done, s)) != cudaSuccess) return e;
+        if ((e = imgm::launch_prolong<T>(A::d(F), A::d(C), A::x(C), A::e(F), xl, done, s)) != cudaSuccess) return e;
         // line 10: t -= A e; line 12 (one-function blocks): x += gamma dinv .* t
-        if ((e = imgm::launch_apply(F.d, imgm::RESID_SMOOTH, F.e, F.t, F.t, xl, g, done, s)) != cudaSuccess) return e;
+        if ((e = imgm::launch_apply<T>(A::d(F), imgm::RESID_SMOOTH, A::e(F), A::t(F), A::t(F), xl, g, done, s)) !=
+            cudaSuccess)
+            return e;
         // line 12 (stored blocks): x += gamma sum_j P_j A_j^{-1} P_j^T t
-        if ((e = imgm::launch_blocks(F.d, F.t, xl, g, done, s)) != cudaSuccess) return e;
+        if ((e = imgm::launch_blocks<T>(A::d(F), A::t(F), xl, g, done, s)) != cudaSuccess) return e;
     }
     return cudaSuccess;
 }
@@ -168,32 +247,53 @@ cudaError_t enqueue_vcycle(imgm_handle* h, const double* r, double* z, const int
 cudaError_t enqueue_solve_start(imgm_handle* h, cudaStream_t s) {
     LevelDev& F = h->lv[h->L - 1];
     const int* done = &h->st->done;
+    const int64_t N = F.d.N;
     cudaError_t e;
-    if ((e = imgm::launch_apply(F.d, imgm::RESID, h->cx, h->cb, h->cr, nullptr, h->gamma, nullptr, s)) != cudaSuccess)
+    if ((e = imgm::launch_apply<double>(F.d, imgm::RESID, h->cx, h->cb, h->cr, nullptr, h->gamma, nullptr, s)) !=
+        cudaSuccess)
         return e;
-    if ((e = imgm::launch_pcg_init_norms(F.d.N, h->cr, h->cb, h->partial, h->st, h->hist, s)) != cudaSuccess) return e;
-    if ((e = imgm::launch_scale_diag(F.d, h->cr, h->cz, h->gamma, done, s)) != cudaSuccess) return e;
-    if ((e = enqueue_vcycle(h, h->cr, h->cz, done, s)) != cudaSuccess) return e;
-    return imgm::launch_pcg_init_dir(F.d.N, h->cr, h->cz, h->cp, h->partial, h->st, s);
+    if ((e = imgm::launch_pcg_init_norms(N, h->cr, h->cb, h->partial, h->st, h->hist, s)) != cudaSuccess) return e;
+    if (h->precision == 1) {
+        if ((e = imgm::launch_vcycle_in<float>(N, h->cr, F.fd.s, F.fd.dinv, h->gamma, h->rf, h->zf, done, s)) !=
+            cudaSuccess)
+            return e;
+        if ((e = enqueue_vcycle<float>(h, h->rf, h->zf, done, s)) != cudaSuccess) return e;
+        return imgm::launch_pcg_init_dir<float>(N, h->cr, h->zf, F.fd.s, h->cp, h->zpf, h->partial, h->st, s);
+    }
+    if ((e = imgm::launch_scale_diag<double>(F.d, h->cr, h->cz, h->gamma, done, s)) != cudaSuccess) return e;
+    if ((e = enqueue_vcycle<double>(h, h->cr, h->cz, done, s)) != cudaSuccess) return e;
+    return imgm::launch_pcg_init_dir<double>(N, h->cr, h->cz, nullptr, h->cp, nullptr, h->partial, h->st, s);
 }
 
 cudaError_t enqueue_iteration(imgm_handle* h, cudaStream_t s) {
     LevelDev& F = h->lv[h->L - 1];
     const int* done = &h->st->done;
+    const int64_t N = F.d.N;
     cudaError_t e;
     if ((e = imgm::launch_apply_pq(F.d, h->cp, h->cq, h->partial, h->st, s)) != cudaSuccess) return e;
-    if ((e = imgm::launch_pcg_update(F.d, h->cx, h->cr, h->cp, h->cq, h->cz, h->gamma, h->partial, h->st, h->hist, s)) !=
-        cudaSuccess)
+    if (h->precision == 1) {
+        if ((e = imgm::launch_pcg_update<float>(F.d, F.fd.dinv, h->cx, h->cr, h->cp, h->cq, h->zf, h->rf, F.fd.s,
+                                                h->gamma, h->partial, h->st, h->hist, s)) != cudaSuccess)
+            return e;
+        if ((e = enqueue_vcycle<float>(h, h->rf, h->zf, done, s)) != cudaSuccess) return e;
+        if ((e = imgm::launch_pcg_rz<float>(N, h->cr, h->zf, F.fd.s, h->zpf, h->partial, h->st, s)) != cudaSuccess)
+            return e;
+        return imgm::launch_pcg_xpay<float>(N, h->zf, F.fd.s, h->cp, h->zpf, h->st, s);
+    }
+    if ((e = imgm::launch_pcg_update<double>(F.d, F.d.dinv, h->cx, h->cr, h->cp, h->cq, h->cz, nullptr, nullptr,
+                                             h->gamma, h->partial, h->st, h->hist, s)) != cudaSuccess)
         return e;
-    if ((e = enqueue_vcycle(h, h->cr, h->cz, done, s)) != cudaSuccess) return e;
-    if ((e = imgm::launch_pcg_rz(F.d.N, h->cr, h->cz, h->partial, h->st, s)) != cudaSuccess) return e;
-    return imgm::launch_pcg_xpay(F.d.N, h->cz, h->cp, h->st, s);
+    if ((e = enqueue_vcycle<double>(h, h->cr, h->cz, done, s)) != cudaSuccess) return e;
+    if ((e = imgm::launch_pcg_rz<double>(N, h->cr, h->cz, nullptr, nullptr, h->partial, h->st, s)) != cudaSuccess)
+        return e;
+    return imgm::launch_pcg_xpay<double>(N, h->cz, nullptr, h->cp, nullptr, h->st, s);
 }
 
 cudaError_t enqueue_solve_finish(imgm_handle* h, cudaStream_t s) {
     LevelDev& F = h->lv[h->L - 1];
     cudaError_t e;
-    if ((e = imgm::launch_apply(F.d, imgm::RESID, h->cx, h->cb, F.t, nullptr, h->gamma, nullptr, s)) != cudaSuccess)
+    if ((e = imgm::launch_apply<double>(F.d, imgm::RESID, h->cx, h->cb, F.t, nullptr, h->gamma, nullptr, s)) !=
+        cudaSuccess)
         return e;
     return imgm::launch_true_residual_norm(F.d.N, F.t, h->partial, h->st, s);
 }
@@ -255,6 +355,60 @@ cudaError_t build_solve_graph(imgm_handle* h, cudaStream_t s) {
     return e;
 }
 
+// Chooses how many coarse levels of the FP32 V-cycle run in the cluster kernel (none,
+// or levels 1..top for some top) by timing whole V-cycles of each choice on this device.
+cudaError_t autotune_cluster(imgm_handle* h, imgm::VcycleCoarse& vc) {
+    cudaStream_t s = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return e;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    auto time_vcycles = [&](float* ms) -> cudaError_t {
+        cudaError_t err = cudaSuccess;
+        for (int k = 0; k < 5 && err == cudaSuccess; ++k) err = enqueue_vcycle<float>(h, h->rf, h->zf, nullptr, s);
+        if (err == cudaSuccess) err = cudaEventRecord(e0, s);
+        for (int k = 0; k < 20 && err == cudaSuccess; ++k) err = enqueue_vcycle<float>(h, h->rf, h->zf, nullptr, s);
+        if (err == cudaSuccess) err = cudaEventRecord(e1, s);
+        if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+        if (err == cudaSuccess) err = cudaEventElapsedTime(ms, e0, e1);
+        return err;
+    };
+    int best_top = -1;
+    float best = 0.0f;
+    h->vc_top = -1;
+    e = time_vcycles(&best);
+    for (int top = h->L - 2; top >= 0 && e == cudaSuccess; --top) {
+        int mb = 1;
+        for (int li = 1; li <= top; ++li) mb = std::max(mb, (int)h->lv[li].fd.max_block);
+        vc.top = top;
+        vc.max_block = mb;
+        e = cudaMemcpy(h->vc, &vc, sizeof(vc), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) break;
+        h->vc_top = top;
+        h->vc_max_block = mb;
+        float t = 0.0f;
+        e = time_vcycles(&t);
+        if (e == cudaSuccess && t < best) {
+            best = t;
+            best_top = top;
+        }
+    }
+    if (e == cudaSuccess && best_top >= 0) {
+        int mb = 1;
+        for (int li = 1; li <= best_top; ++li) mb = std::max(mb, (int)h->lv[li].fd.max_block);
+        vc.top = best_top;
+        vc.max_block = mb;
+        e = cudaMemcpy(h->vc, &vc, sizeof(vc), cudaMemcpyHostToDevice);
+        h->vc_max_block = mb;
+    }
+    h->vc_top = best_top;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaStreamDestroy(s);
+    return e;
+}
+
 int upload_level(imgm_handle* h, const imgm::LevelData& src, LevelDev& dst, int level_index) {
     const imgm::Hierarchy& H = h->H;
     DevLevel& d = dst.d;
@@ -305,6 +459,51 @@ int upload_level(imgm_handle* h, const imgm::LevelData& src, LevelDev& dst, int 
     CK(cudaMemset(dst.r, 0, src.N * sizeof(double)), "memset");
     CK(cudaMemset(dst.t, 0, src.N * sizeof(double)), "memset");
     CK(cudaMemset(dst.e, 0, src.N * sizeof(double)), "memset");
+    if (h->precision == 1) {
+        imgm::DevLevelT<float>& f = dst.fd;
+        f.dim = d.dim;
+        f.p = d.p;
+        f.m = d.m;
+        f.ncoef = d.ncoef;
+        f.N = d.N;
+        f.nb = d.nb;
+        f.nblk = d.nblk;
+        f.max_block = d.max_block;
+        f.TW = d.TW;
+        f.rowinfo = d.rowinfo;
+        f.blk_ptr = d.blk_ptr;
+        f.blk_idx = d.blk_idx;
+        f.blk_vptr = d.blk_vptr;
+        f.r_first = d.r_first;
+        f.t_first = d.t_first;
+        float *bcf, *k1f, *m1f, *dvf, *bvf, *rwf, *twf, *sf, *df;
+        CK(h->upload(&bcf, src.f_band_coef), "upload fp32 rows");
+        CK(h->upload(&k1f, src.f_K1), "upload fp32 K1");
+        CK(h->upload(&m1f, src.f_M1), "upload fp32 M1");
+        CK(h->upload(&dvf, src.f_dinv), "upload fp32 dinv");
+        CK(h->upload(&bvf, src.f_blk_val), "upload fp32 blocks");
+        CK(h->upload(&rwf, src.f_r_w), "upload fp32 restriction");
+        CK(h->upload(&twf, src.f_t_w), "upload fp32 prolongation");
+        CK(h->upload(&sf, src.f_s), "upload fp32 scale");
+        CK(h->upload(&df, src.f_d), "upload fp32 scale");
+        f.band_coef = bcf;
+        f.K1 = k1f;
+        f.M1 = m1f;
+        f.dinv = dvf;
+        f.blk_val = bvf;
+        f.r_w = rwf;
+        f.t_w = twf;
+        f.s = sf;
+        f.d = df;
+        CK(h->alloc(&dst.fx, src.N), "alloc x32");
+        CK(h->alloc(&dst.fr, src.N), "alloc r32");
+        CK(h->alloc(&dst.ft, src.N), "alloc t32");
+        CK(h->alloc(&dst.fe, src.N), "alloc e32");
+        CK(cudaMemset(dst.fx, 0, src.N * sizeof(float)), "memset");
+        CK(cudaMemset(dst.fr, 0, src.N * sizeof(float)), "memset");
+        CK(cudaMemset(dst.ft, 0, src.N * sizeof(float)), "memset");
+        CK(cudaMemset(dst.fe, 0, src.N * sizeof(float)), "memset");
+    }
     imgm_level_info& in = dst.info;
     in.n_grid = src.N;
     in.n_active = src.n_active;
@@ -337,6 +536,7 @@ imgm::Problem make_problem(const imgm_geometry* geom, const imgm_config* cfg) {
     pb.depth = cfg->depth;
     pb.bc = cfg->bc;
     pb.gamma = cfg->gamma;
+    pb.precision = cfg->precision;
     return pb;
 }
 
@@ -376,6 +576,7 @@ int imgm_setup(const imgm_geometry* geom, const imgm_config* cfg, imgm_handle** 
     hp->p = h->H.p;
     hp->L = h->H.L;
     hp->gamma = h->H.gamma;
+    hp->precision = cfg->precision;
     hp->lv.resize(hp->L);
     for (int li = 0; li < hp->L; ++li) {
         int rc = upload_level(hp, hp->H.lv[li], hp->lv[li], li);
@@ -388,6 +589,44 @@ int imgm_setup(const imgm_geometry* geom, const imgm_config* cfg, imgm_handle** 
         imgm_handle* h = hp;   // for CK
         CK(h->upload(&h->c_rows, h->H.c_rows), "upload coarse rows");
         CK(h->upload(&h->c_inv, h->H.c_inv), "upload coarse inverse");
+        h->nc = (int)h->H.c_rows.size();
+        if (h->precision == 1) {
+            CK(h->upload(&h->f_c_inv, h->H.f_c_inv), "upload fp32 coarse inverse");
+            {
+                const int64_t Nf0 = h->lv[h->L - 1].d.N;
+                CK(h->alloc(&h->zf, Nf0), "alloc");
+                CK(h->alloc(&h->rf, Nf0), "alloc");
+                CK(h->alloc(&h->zpf, Nf0), "alloc");
+                CK(cudaMemset(h->zf, 0, Nf0 * sizeof(float)), "memset");
+                CK(cudaMemset(h->rf, 0, Nf0 * sizeof(float)), "memset");
+                CK(cudaMemset(h->zpf, 0, Nf0 * sizeof(float)), "memset");
+            }
+            // the coarse levels of the FP32 V-cycle as one cluster launch, when the device has clusters
+            if (h->L >= 2 && h->L - 1 <= imgm::VCYCLE_MAX_LEVELS && imgm::vcycle_cluster_size() > 0) {
+                imgm::VcycleCoarse vc{};
+                vc.top = h->L - 2;
+                int mb = 1;
+                for (int li = 0; li <= vc.top; ++li) {
+                    LevelDev& Ld = h->lv[li];
+                    vc.lv[li] = Ld.fd;
+                    vc.x[li] = Ld.fx;
+                    vc.r[li] = Ld.fr;
+                    vc.t[li] = Ld.ft;
+                    vc.e[li] = Ld.fe;
+                    if (li >= 1) mb = std::max(mb, (int)Ld.fd.max_block);
+                }
+                vc.c_rows = h->c_rows;
+                vc.c_inv = h->f_c_inv;
+                vc.nc = h->nc;
+                vc.max_block = mb;
+                vc.gamma = h->gamma;
+                CK(h->alloc(&h->vc, 1), "alloc cluster levels");
+                CK(cudaMemcpy(h->vc, &vc, sizeof(vc), cudaMemcpyHostToDevice), "upload cluster levels");
+                h->vc_top = vc.top;
+                h->vc_max_block = mb;
+                CK(autotune_cluster(h, vc), "cluster autotune");
+            }
+        }
         h->nc = (int)h->H.c_rows.size();
         CK(h->upload(&h->b, h->H.b), "upload rhs");
         const int64_t N = h->lv[h->L - 1].d.N;
@@ -448,7 +687,7 @@ int imgm_apply_operator(imgm_handle* h, int level, const double* dev_x, double* 
     if (c) return c;
     if (!dev_x || !dev_y || dev_x == dev_y) return fail(h, IMGM_ERR_INVALID, "bad vector pointers");
     const LevelDev& L = h->lv[level - 1];
-    CK(imgm::launch_apply(L.d, imgm::APPLY, dev_x, nullptr, dev_y, nullptr, 0.0, nullptr, (cudaStream_t)stream),
+    CK(imgm::launch_apply<double>(L.d, imgm::APPLY, dev_x, nullptr, dev_y, nullptr, 0.0, nullptr, (cudaStream_t)stream),
        "apply");
     return IMGM_OK;
 }
@@ -459,8 +698,8 @@ int imgm_smooth(imgm_handle* h, int level, const double* dev_r, double* dev_z, v
     if (!dev_r || !dev_z || dev_r == dev_z) return fail(h, IMGM_ERR_INVALID, "bad vector pointers");
     const LevelDev& L = h->lv[level - 1];
     cudaStream_t s = (cudaStream_t)stream;
-    CK(imgm::launch_scale_diag(L.d, dev_r, dev_z, h->gamma, nullptr, s), "smooth diag");
-    CK(imgm::launch_blocks(L.d, dev_r, dev_z, h->gamma, nullptr, s), "smooth blocks");
+    CK(imgm::launch_scale_diag<double>(L.d, dev_r, dev_z, h->gamma, nullptr, s), "smooth diag");
+    CK(imgm::launch_blocks<double>(L.d, dev_r, dev_z, h->gamma, nullptr, s), "smooth blocks");
     return IMGM_OK;
 }
 
@@ -468,7 +707,7 @@ int imgm_restrict(imgm_handle* h, int level, const double* dev_r, double* dev_rc
     int c = check_level(h, level, 2);
     if (c) return c;
     if (!dev_r || !dev_rc) return fail(h, IMGM_ERR_INVALID, "bad vector pointers");
-    CK(imgm::launch_restrict(h->lv[level - 1].d, h->lv[level - 2].d, dev_r, dev_rc, nullptr, 0.0, nullptr,
+    CK(imgm::launch_restrict<double>(h->lv[level - 1].d, h->lv[level - 2].d, dev_r, dev_rc, nullptr, 0.0, nullptr,
                              (cudaStream_t)stream),
        "restrict");
     return IMGM_OK;
@@ -478,7 +717,7 @@ int imgm_prolong(imgm_handle* h, int level, const double* dev_xc, double* dev_e,
     int c = check_level(h, level, 2);
     if (c) return c;
     if (!dev_xc || !dev_e) return fail(h, IMGM_ERR_INVALID, "bad vector pointers");
-    CK(imgm::launch_prolong(h->lv[level - 1].d, h->lv[level - 2].d, dev_xc, dev_e, nullptr, nullptr,
+    CK(imgm::launch_prolong<double>(h->lv[level - 1].d, h->lv[level - 2].d, dev_xc, dev_e, nullptr, nullptr,
                             (cudaStream_t)stream),
        "prolong");
     return IMGM_OK;
@@ -490,7 +729,7 @@ int imgm_coarse_solve(imgm_handle* h, const double* dev_r, double* dev_x, void* 
     if (!dev_r || !dev_x || dev_r == dev_x) return fail(h, IMGM_ERR_INVALID, "bad vector pointers");
     cudaStream_t s = (cudaStream_t)stream;
     CK(cudaMemsetAsync(dev_x, 0, h->lv[0].d.N * sizeof(double), s), "coarse memset");
-    CK(imgm::launch_coarse(h->c_rows, h->c_inv, h->nc, dev_r, dev_x, nullptr, s), "coarse solve");
+    CK(imgm::launch_coarse<double>(h->c_rows, h->c_inv, h->nc, dev_r, dev_x, nullptr, s), "coarse solve");
     return IMGM_OK;
 }
 
@@ -499,8 +738,16 @@ int imgm_apply_preconditioner(imgm_handle* h, const double* dev_r, double* dev_z
     if (c) return c;
     if (!dev_r || !dev_z || dev_r == dev_z) return fail(h, IMGM_ERR_INVALID, "bad vector pointers");
     cudaStream_t s = (cudaStream_t)stream;
-    CK(imgm::launch_scale_diag(h->lv[h->L - 1].d, dev_r, dev_z, h->gamma, nullptr, s), "vcycle diag");
-    CK(enqueue_vcycle(h, dev_r, dev_z, nullptr, s), "vcycle");
+    LevelDev& F = h->lv[h->L - 1];
+    if (h->precision == 1) {
+        CK(imgm::launch_vcycle_in<float>(F.d.N, dev_r, F.fd.s, F.fd.dinv, h->gamma, h->rf, h->zf, nullptr, s),
+           "vcycle input");
+        CK(enqueue_vcycle<float>(h, h->rf, h->zf, nullptr, s), "vcycle");
+        CK(imgm::launch_vcycle_out<float>(F.d.N, h->zf, F.fd.s, dev_z, s), "vcycle output");
+        return IMGM_OK;
+    }
+    CK(imgm::launch_scale_diag<double>(F.d, dev_r, dev_z, h->gamma, nullptr, s), "vcycle diag");
+    CK(enqueue_vcycle<double>(h, dev_r, dev_z, nullptr, s), "vcycle");
     return IMGM_OK;
 }
 
@@ -559,7 +806,7 @@ int imgm_residual_norm2(imgm_handle* h, const double* dev_b, const double* dev_x
     if (!dev_b || !dev_x || !dev_out) return fail(h, IMGM_ERR_INVALID, "null pointer");
     cudaStream_t s = (cudaStream_t)stream;
     LevelDev& F = h->lv[h->L - 1];
-    CK(imgm::launch_apply(F.d, imgm::RESID, dev_x, dev_b, F.t, nullptr, h->gamma, nullptr, s), "residual");
+    CK(imgm::launch_apply<double>(F.d, imgm::RESID, dev_x, dev_b, F.t, nullptr, h->gamma, nullptr, s), "residual");
     CK(imgm::launch_true_residual_norm(F.d.N, F.t, h->partial_aux, h->st_aux, s), "residual norm");
     CK(cudaMemcpyAsync(dev_out, &h->st_aux->true_rr, sizeof(double), cudaMemcpyDeviceToDevice, s), "norm copy");
     return IMGM_OK;
@@ -599,7 +846,7 @@ int imgm_residual_norm2_noalloc(imgm_handle* h, const double* dev_b, const doubl
     cudaStream_t s = (cudaStream_t)stream;
     // the reduction ticket must start at zero; the array keeps the previous call's contents
     CK(cudaMemsetAsync(st, 0, sizeof(PcgState), s), "noalloc: clear state");
-    CK(imgm::launch_apply(F.d, imgm::RESID, dev_x, dev_b, t, nullptr, h->gamma, nullptr, s), "noalloc: residual");
+    CK(imgm::launch_apply<double>(F.d, imgm::RESID, dev_x, dev_b, t, nullptr, h->gamma, nullptr, s), "noalloc: residual");
     CK(imgm::launch_true_residual_norm(F.d.N, t, partial, st, s), "noalloc: residual norm");
     CK(cudaMemcpyAsync(dev_out, &st->true_rr, sizeof(double), cudaMemcpyDeviceToDevice, s), "noalloc: norm copy");
     return IMGM_OK;

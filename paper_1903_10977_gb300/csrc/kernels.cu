@@ -1,4 +1,4 @@
-// FP64 hot-path kernels of the immersed multigrid-preconditioned CG solve.
+// Hot-path kernels of the immersed multigrid-preconditioned CG solve.
 //
 //   operator apply   A_l x            (Eq. systemMulti; Galerkin rows of Remark 3.1)
 //   Schwarz smoother gamma M^{-1} r   (Sec. 3.4, additive Schwarz with stored block inverses)
@@ -7,15 +7,27 @@
 //   coarsest solve   A_1^{-1} r       (Algorithm 1, direct solve on level 1)
 //   CG updates and dot products       (Sec. 3.2, the V-cycle as CG preconditioner)
 //
-// Rows of a level are either "tensor" rows, whose whole support lies in full
-// elements, where A = K (x) M + M (x) K [+ ...] with the 1-D stiffness/mass rows K1/M1,
-// or "stored" rows (support touching a cut, empty or partly active element) whose
-// (2p+1)^d coefficients were assembled at setup.  Vectors hold 0 on inactive rows.
-// Reductions are deterministic: fixed grid, per-block partials summed in a fixed order
-// by the last block to finish.
+// Rows of a level are either "tensor" rows, whose whole support lies in full elements,
+// where A = K (x) M + M (x) K [+ ...] with the 1-D stiffness/mass rows K1/M1, or "stored"
+// rows (support touching a cut, empty or partly active element) whose (2p+1)^d
+// coefficients were assembled at setup.  Vectors hold 0 on inactive rows.
+//
+// The V-cycle kernels are templates on T.  T = double: the FP64 path, plain variables.
+// T = float: the mixed-precision V-cycle, which works in Jacobi-scaled variables
+// x^ = D x, r^ = D^{-1} r with D = diag(A_l)^{1/2} per level (L.s = 1/d, L.d = d): the
+// stored coefficients, block inverses and coarse inverse arrive pre-scaled from setup,
+// the tensor rows scale on the fly (y^ = s_i sum_j A_ij s_j x^_j), and the transfers use
+// D_c^{-1} R D_f.  Cut functions make diagonal entries span 40+ orders of magnitude,
+// which FP32 cannot hold unscaled.
+// Reductions are FP64 and deterministic: fixed grid, per-block partials summed in a
+// fixed order by the last block to finish.
 #include "kernels.cuh"
 
+#include <cooperative_groups.h>
+
 #include <algorithm>
+
+namespace cg = cooperative_groups;
 
 namespace imgm {
 namespace {
@@ -66,20 +78,58 @@ __device__ __forceinline__ bool finish_reduction(double v, double* partial, unsi
     return true;
 }
 
-// (A x)_i for one row
-template <int DIM, int P>
-__device__ __forceinline__ double row_apply(const DevLevel& L, int64_t i, const double* __restrict__ x) {
+// Two sums at once (partials at [0, G) and [G, 2G)); the last block sums both in parallel.
+__device__ __forceinline__ bool finish_reduction2(double v1, double v2, double* partial, unsigned int* ticket,
+                                                  double* t1, double* t2) {
+    __shared__ double ws[32];
+    __shared__ bool last;
+    double b1 = block_sum(v1, ws);
+    double b2 = block_sum(v2, ws);
+    if (threadIdx.x == 0) {
+        partial[blockIdx.x] = b1;
+        partial[gridDim.x + blockIdx.x] = b2;
+        __threadfence();
+        unsigned int t = atomicAdd(ticket, 1u);
+        last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!last) return false;
+    __threadfence();
+    double s1 = 0.0, s2 = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += TPB) {
+        s1 += ((volatile double*)partial)[b];
+        s2 += ((volatile double*)partial)[gridDim.x + b];
+    }
+    s1 = block_sum(s1, ws);
+    s2 = block_sum(s2, ws);
+    if (threadIdx.x == 0) {
+        *t1 = s1;
+        *t2 = s2;
+        *ticket = 0u;
+    }
+    return true;
+}
+
+template <typename T>
+__device__ __forceinline__ T fmaT(T a, T b, T c) {
+    return fma(a, b, c);
+}
+
+// (A x)_i for one row (scaled variables when L.s != nullptr)
+template <typename T, int DIM, int P>
+__device__ __forceinline__ T row_apply(const DevLevelT<T>& L, int64_t i, const T* __restrict__ x) {
     constexpr int W = 2 * P + 1;
     const int ri = L.rowinfo[i];
-    if (ri == -2) return 0.0;
+    if (ri == -2) return T(0);
     const int m = L.m;
     const int ix = (int)(i % m);
     const int iy = (int)((i / m) % m);
     const int iz = (DIM == 3) ? (int)(i / ((int64_t)m * m)) : 0;
     const int64_t sy = m, sz = (int64_t)m * m;
-    double y = 0.0;
+    const T* __restrict__ sc = L.s;
+    T y = T(0);
     if (ri >= 0) {
-        const double* __restrict__ c = L.band_coef + ri;
+        const T* __restrict__ c = L.band_coef + ri;
         const int64_t nb = L.nb;
 #pragma unroll
         for (int oz = (DIM == 3 ? -P : 0); oz <= (DIM == 3 ? P : 0); ++oz) {
@@ -91,17 +141,17 @@ __device__ __forceinline__ double row_apply(const DevLevel& L, int64_t i, const 
                 for (int ox = -P; ox <= P; ++ox) {
                     if ((unsigned)(ix + ox) >= (unsigned)m) continue;
                     const int ci = (ox + P) + W * ((oy + P) + (DIM == 3 ? W * (oz + P) : 0));
-                    y = fma(c[(int64_t)ci * nb], x[i + ox + oy * sy + (DIM == 3 ? oz * sz : 0)], y);
+                    y = fmaT(c[(int64_t)ci * nb], x[i + ox + oy * sy + (DIM == 3 ? oz * sz : 0)], y);
                 }
             }
         }
         return y;
     }
-    const double* __restrict__ Kx = L.K1 + (int64_t)ix * W + P;
-    const double* __restrict__ Mx = L.M1 + (int64_t)ix * W + P;
-    const double* __restrict__ Ky = L.K1 + (int64_t)iy * W + P;
-    const double* __restrict__ My = L.M1 + (int64_t)iy * W + P;
-    double kx[W], mx[W];
+    const T* __restrict__ Kx = L.K1 + (int64_t)ix * W + P;
+    const T* __restrict__ Mx = L.M1 + (int64_t)ix * W + P;
+    const T* __restrict__ Ky = L.K1 + (int64_t)iy * W + P;
+    const T* __restrict__ My = L.M1 + (int64_t)iy * W + P;
+    T kx[W], mx[W];
 #pragma unroll
     for (int ox = -P; ox <= P; ++ox) {
         kx[ox + P] = Kx[ox];
@@ -111,65 +161,69 @@ __device__ __forceinline__ double row_apply(const DevLevel& L, int64_t i, const 
 #pragma unroll
         for (int oy = -P; oy <= P; ++oy) {
             if ((unsigned)(iy + oy) >= (unsigned)m) continue;
-            double a = 0.0, b = 0.0;
-            const double* xr = x + i + oy * sy;
+            T a = T(0), b = T(0);
+            const int64_t rb = i + oy * sy;
 #pragma unroll
             for (int ox = -P; ox <= P; ++ox) {
                 if ((unsigned)(ix + ox) >= (unsigned)m) continue;
-                const double xv = xr[ox];
-                a = fma(kx[ox + P], xv, a);
-                b = fma(mx[ox + P], xv, b);
+                const T xv = sc ? x[rb + ox] * sc[rb + ox] : x[rb + ox];
+                a = fmaT(kx[ox + P], xv, a);
+                b = fmaT(mx[ox + P], xv, b);
             }
-            y = fma(My[oy], a, y);
-            y = fma(Ky[oy], b, y);
+            y = fmaT(My[oy], a, y);
+            y = fmaT(Ky[oy], b, y);
         }
-        return y;
+        return sc ? y * sc[i] : y;
     }
-    const double* __restrict__ Kz = L.K1 + (int64_t)iz * W + P;
-    const double* __restrict__ Mz = L.M1 + (int64_t)iz * W + P;
+    const T* __restrict__ Kz = L.K1 + (int64_t)iz * W + P;
+    const T* __restrict__ Mz = L.M1 + (int64_t)iz * W + P;
 #pragma unroll
     for (int oz = -P; oz <= P; ++oz) {
         if ((unsigned)(iz + oz) >= (unsigned)m) continue;
-        const double mz = Mz[oz], kz = Kz[oz];
+        const T mz = Mz[oz], kz = Kz[oz];
 #pragma unroll
         for (int oy = -P; oy <= P; ++oy) {
             if ((unsigned)(iy + oy) >= (unsigned)m) continue;
-            const double my = My[oy], ky = Ky[oy];
-            double a = 0.0, b = 0.0;
-            const double* xr = x + i + oy * sy + oz * sz;
+            const T my = My[oy], ky = Ky[oy];
+            T a = T(0), b = T(0);
+            const int64_t rb = i + oy * sy + oz * sz;
 #pragma unroll
             for (int ox = -P; ox <= P; ++ox) {
                 if ((unsigned)(ix + ox) >= (unsigned)m) continue;
-                const double xv = xr[ox];
-                a = fma(kx[ox + P], xv, a);
-                b = fma(mx[ox + P], xv, b);
+                const T xv = sc ? x[rb + ox] * sc[rb + ox] : x[rb + ox];
+                a = fmaT(kx[ox + P], xv, a);
+                b = fmaT(mx[ox + P], xv, b);
             }
             // sum_ox (kx my mz + mx ky mz + mx my kz) x = my mz a + (ky mz + my kz) b
-            y = fma(my * mz, a, y);
-            y = fma(fma(ky, mz, my * kz), b, y);
+            y = fmaT(my * mz, a, y);
+            y = fmaT(fmaT(ky, mz, my * kz), b, y);
         }
     }
-    return y;
+    return sc ? y * sc[i] : y;
 }
 
-template <int DIM, int P>
-__global__ void __launch_bounds__(TPB) k_apply(DevLevel L, int mode, const double* __restrict__ x,
-                                               const double* rin, double* out, double* __restrict__ xs,
-                                               double gamma, const int* done) {
-    if (done && *done) return;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < L.N; i += stride) {
-        const double ax = row_apply<DIM, P>(L, i, x);
+template <typename T, int DIM, int P>
+__device__ __forceinline__ void apply_rows(const DevLevelT<T>& L, int mode, const T* __restrict__ x, const T* rin,
+                                           T* out, T* __restrict__ xs, T gamma, int64_t start, int64_t stride) {
+    for (int64_t i = start; i < L.N; i += stride) {
+        const T ax = row_apply<T, DIM, P>(L, i, x);
         if (mode == APPLY) {
             out[i] = ax;
         } else {
-            const double v = (L.rowinfo[i] == -2) ? 0.0 : rin[i] - ax;
+            const T v = (L.rowinfo[i] == -2) ? T(0) : rin[i] - ax;
             out[i] = v;
-            if (mode == RESID_SMOOTH) xs[i] = fma(gamma * L.dinv[i], v, xs[i]);
+            if (mode == RESID_SMOOTH) xs[i] = fmaT(gamma * L.dinv[i], v, xs[i]);
         }
     }
 }
 
+template <typename T, int DIM, int P>
+__global__ void __launch_bounds__(TPB) k_apply(DevLevelT<T> L, int mode, const T* __restrict__ x, const T* rin,
+                                               T* out, T* __restrict__ xs, T gamma, const int* done) {
+    if (done && *done) return;
+    apply_rows<T, DIM, P>(L, mode, x, rin, out, xs, gamma, (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
+                          (int64_t)gridDim.x * blockDim.x);
+}
 
 // ---------------------------------------------------------------------------------
 // 2-D operator apply on TX x TY tiles with sum factorisation.  The x values of the tile
@@ -178,84 +232,114 @@ __global__ void __launch_bounds__(TPB) k_apply(DevLevel L, int mode, const doubl
 //   y = K_x u + M_x v     on the TX x TY outputs      (2 (2p+1) FMA per point)
 // i.e. about 4(2p+1) FMA per row instead of 2(2p+1)^2 + 2(2p+1) for the direct sum.
 // Stored rows read their (2p+1)^2 coefficients and take x from the same staged tile.
-// MODE: APPLY, RESID, RESID_SMOOTH as in k_apply; DOT also accumulates sum_i x_i (A x)_i
-// and finishes with alpha = rz / (p^T A p) (the CG step length).
+// MODE: APPLY, RESID, RESID_SMOOTH as in k_apply; DOT (FP64 only) also accumulates
+// sum_i x_i (A x)_i and finishes with alpha = rz / (p^T A p) (the CG step length).
 constexpr int TX = 32, TY = 16;
 
-template <int P, int MODE, bool DOT>
-__global__ void __launch_bounds__(TPB) k_apply_tile2d(DevLevel L, const double* __restrict__ x,
-                                                      const double* rin, double* out, double* __restrict__ xs,
-                                                      double gamma, const int* done, double* partial, PcgState* st) {
+template <typename T, int P, int MODE, bool DOT>
+__global__ void __launch_bounds__(TPB) k_apply_tile2d(DevLevelT<T> L, const T* __restrict__ x, const T* rin, T* out,
+                                                      T* __restrict__ xs, T gamma, const int* done, double* partial,
+                                                      PcgState* st) {
     constexpr int W = 2 * P + 1;
     constexpr int SX = TX + 2 * P, SY = TY + 2 * P;
-    __shared__ double sx[SY][SX];
-    __shared__ double su[TY][SX];
-    __shared__ double sv[TY][SX];
+    constexpr int OUT_PER_THREAD = (TX * TY) / TPB;
+    static_assert(OUT_PER_THREAD * TPB == TX * TY, "tile must be a multiple of the block");
+    __shared__ T sx[SY][SX];     // x (scaled variables x^ in the FP32 path)
+    __shared__ T ss[SY][SX];     // 1/d (FP32 path) or 1
+    __shared__ T su[TY][SX];
+    __shared__ T sv[TY][SX];
+    __shared__ T tMy[TY][W], tKy[TY][W];   // 1-D rows of the tile's y indices
+    __shared__ T tKx[TX][W], tMx[TX][W];   // 1-D rows of the tile's x indices
     if (done && *done) return;
     const int m = L.m;
+    const bool scaled = L.s != nullptr;
     const int tiles_x = (m + TX - 1) / TX, tiles_y = (m + TY - 1) / TY;
     const int ntiles = tiles_x * tiles_y;
     double acc = 0.0;
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int x0 = (tile % tiles_x) * TX, y0 = (tile / tiles_x) * TY;
         __syncthreads();   // the previous tile's smem reads are done
+        // one round of independent global loads: the x tile with its halo, the 1-D table
+        // rows, and everything the outputs of this thread need that does not depend on x
         for (int k = threadIdx.x; k < SX * SY; k += TPB) {
             const int ly = k / SX, lx = k % SX;
             const int gx = x0 + lx - P, gy = y0 + ly - P;
-            sx[ly][lx] = ((unsigned)gx < (unsigned)m && (unsigned)gy < (unsigned)m) ? x[(int64_t)gy * m + gx] : 0.0;
+            const bool in = (unsigned)gx < (unsigned)m && (unsigned)gy < (unsigned)m;
+            const int64_t g = (int64_t)gy * m + gx;
+            sx[ly][lx] = in ? x[g] : T(0);
+            ss[ly][lx] = in ? (scaled ? L.s[g] : T(1)) : T(0);
+        }
+        for (int k = threadIdx.x; k < TY * W; k += TPB) {
+            const int ly = k / W, o = k % W;
+            const int gy = y0 + ly;
+            tMy[ly][o] = gy < m ? L.M1[(int64_t)gy * W + o] : T(0);
+            tKy[ly][o] = gy < m ? L.K1[(int64_t)gy * W + o] : T(0);
+        }
+        for (int k = threadIdx.x; k < TX * W; k += TPB) {
+            const int lx = k / W, o = k % W;
+            const int gx = x0 + lx;
+            tKx[lx][o] = gx < m ? L.K1[(int64_t)gx * W + o] : T(0);
+            tMx[lx][o] = gx < m ? L.M1[(int64_t)gx * W + o] : T(0);
+        }
+        int ri[OUT_PER_THREAD];
+        T rv[OUT_PER_THREAD], dv[OUT_PER_THREAD], xv[OUT_PER_THREAD];
+#pragma unroll
+        for (int q = 0; q < OUT_PER_THREAD; ++q) {
+            const int k = threadIdx.x + q * TPB;
+            const int gx = x0 + k % TX, gy = y0 + k / TX;
+            const bool in = gx < m && gy < m;
+            const int64_t i = (int64_t)gy * m + gx;
+            ri[q] = in ? L.rowinfo[i] : -3;
+            rv[q] = (MODE != APPLY && in) ? rin[i] : T(0);
+            dv[q] = (MODE == RESID_SMOOTH && in) ? L.dinv[i] : T(0);
+            xv[q] = (MODE == RESID_SMOOTH && in) ? xs[i] : T(0);
         }
         __syncthreads();
         // stage 1: along y, for all columns of the strip
         for (int k = threadIdx.x; k < TY * SX; k += TPB) {
             const int ly = k / SX, lx = k % SX;
-            const int gy = y0 + ly;
-            double u = 0.0, v = 0.0;
-            if (gy < m) {
-                const double* My = L.M1 + (int64_t)gy * W;
-                const double* Ky = L.K1 + (int64_t)gy * W;
+            T u = T(0), v = T(0);
 #pragma unroll
-                for (int o = 0; o < W; ++o) {
-                    const double xv = sx[ly + o][lx];
-                    u = fma(My[o], xv, u);
-                    v = fma(Ky[o], xv, v);
-                }
+            for (int o = 0; o < W; ++o) {
+                const T xq = scaled ? sx[ly + o][lx] * ss[ly + o][lx] : sx[ly + o][lx];
+                u = fmaT(tMy[ly][o], xq, u);
+                v = fmaT(tKy[ly][o], xq, v);
             }
             su[ly][lx] = u;
             sv[ly][lx] = v;
         }
         __syncthreads();
-        // stage 2: along x, one output per thread and step
-        for (int k = threadIdx.x; k < TX * TY; k += TPB) {
+        // stage 2: along x; stored rows take their coefficients from global memory
+#pragma unroll
+        for (int q = 0; q < OUT_PER_THREAD; ++q) {
+            if (ri[q] == -3) continue;
+            const int k = threadIdx.x + q * TPB;
             const int ly = k / TX, lx = k % TX;
-            const int gx = x0 + lx, gy = y0 + ly;
-            if (gx >= m || gy >= m) continue;
-            const int64_t i = (int64_t)gy * m + gx;
-            const int ri = L.rowinfo[i];
-            double y = 0.0;
-            if (ri == -1) {
-                const double* Kx = L.K1 + (int64_t)gx * W;
-                const double* Mx = L.M1 + (int64_t)gx * W;
+            const int64_t i = (int64_t)(y0 + ly) * m + (x0 + lx);
+            T y = T(0);
+            if (ri[q] == -1) {
 #pragma unroll
                 for (int o = 0; o < W; ++o) {
-                    y = fma(Kx[o], su[ly][lx + o], y);
-                    y = fma(Mx[o], sv[ly][lx + o], y);
+                    y = fmaT(tKx[lx][o], su[ly][lx + o], y);
+                    y = fmaT(tMx[lx][o], sv[ly][lx + o], y);
                 }
-            } else if (ri >= 0) {
-                const double* __restrict__ c = L.band_coef + ri;
+                if (scaled) y *= ss[ly + P][lx + P];
+            } else if (ri[q] >= 0) {
+                const T* __restrict__ c = L.band_coef + ri[q];
                 const int64_t nb = L.nb;
 #pragma unroll
                 for (int oy = 0; oy < W; ++oy)
 #pragma unroll
-                    for (int ox = 0; ox < W; ++ox) y = fma(c[(int64_t)(ox + W * oy) * nb], sx[ly + oy][lx + ox], y);
+                    for (int ox = 0; ox < W; ++ox) y = fmaT(c[(int64_t)(ox + W * oy) * nb], sx[ly + oy][lx + ox], y);
             }
             if (MODE == APPLY) {
                 out[i] = y;
             } else {
-                const double r = (ri == -2) ? 0.0 : rin[i] - y;
+                const T r = (ri[q] == -2) ? T(0) : rv[q] - y;
                 out[i] = r;
-                if (MODE == RESID_SMOOTH) xs[i] = fma(gamma * L.dinv[i], r, xs[i]);
+                if (MODE == RESID_SMOOTH) xs[i] = fmaT(gamma * dv[q], r, xv[q]);
             }
-            if (DOT) acc = fma(sx[ly + P][lx + P], y, acc);
+            if (DOT) acc = fma((double)sx[ly + P][lx + P], (double)y, acc);
         }
     }
     if (DOT) {
@@ -280,7 +364,7 @@ __global__ void __launch_bounds__(TPB) k_apply_pq(DevLevel L, const double* __re
     double acc = 0.0;
     const int64_t stride = (int64_t)gridDim.x * TPB;
     for (int64_t i = (int64_t)blockIdx.x * TPB + threadIdx.x; i < L.N; i += stride) {
-        const double ax = row_apply<DIM, P>(L, i, p);
+        const double ax = row_apply<double, DIM, P>(L, i, p);
         q[i] = ax;
         acc = fma(p[i], ax, acc);
     }
@@ -297,126 +381,242 @@ __global__ void __launch_bounds__(TPB) k_apply_pq(DevLevel L, const double* __re
     }
 }
 
-__global__ void __launch_bounds__(TPB) k_scale_diag(int64_t N, const double* __restrict__ dinv,
-                                                    const double* __restrict__ r, double* __restrict__ x, double gamma,
-                                                    const int* done) {
+template <typename T>
+__global__ void __launch_bounds__(TPB) k_scale_diag(int64_t N, const T* __restrict__ dinv, const T* __restrict__ r,
+                                                    T* __restrict__ x, T gamma, const int* done) {
     if (done && *done) return;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) x[i] = gamma * dinv[i] * r[i];
 }
 
 // one warp per stored block: gather r_j, z_j = A_j^{-1} r_j, x[idx_j] += gamma z_j
-__global__ void __launch_bounds__(TPB) k_blocks(DevLevel L, const double* __restrict__ r, double* x, double gamma,
-                                                const int* done) {
-    extern __shared__ double sm[];
-    if (done && *done) return;
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    double* rs = sm + (int64_t)wib * L.max_block;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t b = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5); b < L.nblk; b += nwarps) {
+template <typename T>
+__device__ __forceinline__ void blocks_warps(const DevLevelT<T>& L, const T* __restrict__ r, T* x, T gamma,
+                                             int64_t warp0, int64_t nwarps, int lane, T* rs) {
+    for (int64_t b = warp0; b < L.nblk; b += nwarps) {
         const int64_t s = L.blk_ptr[b];
         const int nj = (int)(L.blk_ptr[b + 1] - s);
-        const double* __restrict__ A = L.blk_val + L.blk_vptr[b];
+        const T* __restrict__ A = L.blk_val + L.blk_vptr[b];
         for (int a = lane; a < nj; a += 32) rs[a] = r[L.blk_idx[s + a]];
         __syncwarp();
         for (int a = lane; a < nj; a += 32) {
-            double acc = 0.0;
-            for (int c = 0; c < nj; ++c) acc = fma(A[(int64_t)c * nj + a], rs[c], acc);
+            T acc = T(0);
+            for (int c = 0; c < nj; ++c) acc = fmaT(A[(int64_t)c * nj + a], rs[c], acc);
             atomicAdd(&x[L.blk_idx[s + a]], gamma * acc);
         }
         __syncwarp();
     }
 }
 
-template <int DIM, int P>
-__global__ void __launch_bounds__(TPB) k_restrict(DevLevel F, DevLevel C, const double* __restrict__ rf,
-                                                  double* __restrict__ rc, double* __restrict__ xc, double gamma,
-                                                  const int* done) {
+template <typename T>
+__global__ void __launch_bounds__(TPB) k_blocks(DevLevelT<T> L, const T* __restrict__ r, T* x, T gamma,
+                                                const int* done) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T* sm = reinterpret_cast<T*>(smraw);
     if (done && *done) return;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    blocks_warps<T>(L, r, x, gamma, ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5,
+                    ((int64_t)gridDim.x * blockDim.x) >> 5, lane, sm + (int64_t)wib * L.max_block);
+}
+
+template <typename T, int DIM, int P>
+__device__ __forceinline__ void restrict_rows(const DevLevelT<T>& F, const DevLevelT<T>& C, const T* __restrict__ rf,
+                                              T* __restrict__ rc, T* __restrict__ xc, T gamma, int64_t start,
+                                              int64_t stride) {
     constexpr int P2 = P + 2;
     const int mc = C.m, mf = F.m;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < C.N; i += stride) {
+    const T* __restrict__ df = F.d;      // fine scale d (FP32 path) or nullptr
+    for (int64_t i = start; i < C.N; i += stride) {
         if (C.rowinfo[i] == -2) {
-            rc[i] = 0.0;
-            if (xc) xc[i] = 0.0;
+            rc[i] = T(0);
+            if (xc) xc[i] = T(0);
             continue;
         }
         const int cx = (int)(i % mc), cy = (int)((i / mc) % mc), cz = (DIM == 3) ? (int)(i / ((int64_t)mc * mc)) : 0;
         const int fx = F.r_first[cx], fy = F.r_first[cy], fz = (DIM == 3) ? F.r_first[cz] : 0;
-        const double* wx = F.r_w + (int64_t)cx * P2;
-        const double* wy = F.r_w + (int64_t)cy * P2;
-        const double* wz = F.r_w + (int64_t)cz * P2;
-        double s = 0.0;
+        const T* wx = F.r_w + (int64_t)cx * P2;
+        const T* wy = F.r_w + (int64_t)cy * P2;
+        const T* wz = F.r_w + (int64_t)cz * P2;
+        T s = T(0);
 #pragma unroll
         for (int kz = 0; kz < (DIM == 3 ? P2 : 1); ++kz) {
-            const double wzk = (DIM == 3) ? wz[kz] : 1.0;
+            const T wzk = (DIM == 3) ? wz[kz] : T(1);
 #pragma unroll
             for (int ky = 0; ky < P2; ++ky) {
-                const double wyz = wy[ky] * wzk;
-                const double* rr = rf + (int64_t)(fx) + (int64_t)mf * ((fy + ky) + (DIM == 3 ? (int64_t)mf * (fz + kz) : 0));
-                double t = 0.0;
+                const T wyz = wy[ky] * wzk;
+                const int64_t rb = (int64_t)(fx) + (int64_t)mf * ((fy + ky) + (DIM == 3 ? (int64_t)mf * (fz + kz) : 0));
+                T t = T(0);
 #pragma unroll
-                for (int kx = 0; kx < P2; ++kx) t = fma(wx[kx], rr[kx], t);
-                s = fma(wyz, t, s);
+                for (int kx = 0; kx < P2; ++kx) t = fmaT(wx[kx], df ? rf[rb + kx] * df[rb + kx] : rf[rb + kx], t);
+                s = fmaT(wyz, t, s);
             }
         }
+        if (C.s) s *= C.s[i];
         rc[i] = s;
         if (xc) xc[i] = gamma * C.dinv[i] * s;
     }
 }
 
-template <int DIM, int P>
-__global__ void __launch_bounds__(TPB) k_prolong(DevLevel F, DevLevel C, const double* __restrict__ xc,
-                                                 double* __restrict__ e, double* __restrict__ x, const int* done) {
+template <typename T, int DIM, int P>
+__global__ void __launch_bounds__(TPB) k_restrict(DevLevelT<T> F, DevLevelT<T> C, const T* __restrict__ rf,
+                                                  T* __restrict__ rc, T* __restrict__ xc, T gamma, const int* done) {
     if (done && *done) return;
+    restrict_rows<T, DIM, P>(F, C, rf, rc, xc, gamma, (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
+                             (int64_t)gridDim.x * blockDim.x);
+}
+
+template <typename T, int DIM, int P>
+__device__ __forceinline__ void prolong_rows(const DevLevelT<T>& F, const DevLevelT<T>& C, const T* __restrict__ xc,
+                                             T* __restrict__ e, T* __restrict__ x, int64_t start, int64_t stride) {
     const int mc = C.m, mf = F.m, TW = F.TW;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; a < F.N; a += stride) {
+    const T* __restrict__ sc = C.s;      // coarse scale 1/d (FP32 path) or nullptr
+    for (int64_t a = start; a < F.N; a += stride) {
         if (F.rowinfo[a] == -2) {
-            e[a] = 0.0;
+            e[a] = T(0);
             continue;
         }
         const int ax = (int)(a % mf), ay = (int)((a / mf) % mf), az = (DIM == 3) ? (int)(a / ((int64_t)mf * mf)) : 0;
         const int cx = F.t_first[ax], cy = F.t_first[ay], cz = (DIM == 3) ? F.t_first[az] : 0;
-        const double* wx = F.t_w + (int64_t)ax * TW;
-        const double* wy = F.t_w + (int64_t)ay * TW;
-        const double* wz = F.t_w + (int64_t)az * TW;
-        double s = 0.0;
+        const T* wx = F.t_w + (int64_t)ax * TW;
+        const T* wy = F.t_w + (int64_t)ay * TW;
+        const T* wz = F.t_w + (int64_t)az * TW;
+        T s = T(0);
         for (int tz = 0; tz < (DIM == 3 ? TW : 1); ++tz) {
-            const double wzk = (DIM == 3) ? wz[tz] : 1.0;
+            const T wzk = (DIM == 3) ? wz[tz] : T(1);
             for (int ty = 0; ty < TW; ++ty) {
-                const double wyz = wy[ty] * wzk;
-                const double* xr = xc + (int64_t)cx + (int64_t)mc * ((cy + ty) + (DIM == 3 ? (int64_t)mc * (cz + tz) : 0));
-                double t = 0.0;
-                for (int tx = 0; tx < TW; ++tx) t = fma(wx[tx], xr[tx], t);
-                s = fma(wyz, t, s);
+                const T wyz = wy[ty] * wzk;
+                const int64_t rb = (int64_t)cx + (int64_t)mc * ((cy + ty) + (DIM == 3 ? (int64_t)mc * (cz + tz) : 0));
+                T t = T(0);
+                for (int tx = 0; tx < TW; ++tx) t = fmaT(wx[tx], sc ? xc[rb + tx] * sc[rb + tx] : xc[rb + tx], t);
+                s = fmaT(wyz, t, s);
             }
         }
+        if (F.d) s *= F.d[a];
         e[a] = s;
         if (x) x[a] += s;
     }
 }
 
-// one warp per kept coarse row
-__global__ void __launch_bounds__(TPB) k_coarse(const int32_t* __restrict__ rows, const double* __restrict__ Cinv,
-                                                int nc, const double* __restrict__ r, double* __restrict__ x,
-                                                const int* done) {
+template <typename T, int DIM, int P>
+__global__ void __launch_bounds__(TPB) k_prolong(DevLevelT<T> F, DevLevelT<T> C, const T* __restrict__ xc,
+                                                 T* __restrict__ e, T* __restrict__ x, const int* done) {
     if (done && *done) return;
-    const int lane = threadIdx.x & 31;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t a = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5); a < nc; a += nwarps) {
-        const double* row = Cinv + a * nc;
+    prolong_rows<T, DIM, P>(F, C, xc, e, x, (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
+                            (int64_t)gridDim.x * blockDim.x);
+}
+
+// one warp per kept coarse row
+template <typename T>
+__device__ __forceinline__ void coarse_warps(const int32_t* __restrict__ rows, const T* __restrict__ Cinv, int nc,
+                                             const T* __restrict__ r, T* __restrict__ x, int64_t warp0, int64_t nwarps,
+                                             int lane) {
+    for (int64_t a = warp0; a < nc; a += nwarps) {
+        const T* row = Cinv + a * nc;
         double acc = 0.0;
-        for (int b = lane; b < nc; b += 32) acc = fma(row[b], r[rows[b]], acc);
+        for (int b = lane; b < nc; b += 32) acc = fma((double)row[b], (double)r[rows[b]], acc);
         acc = warp_sum(acc);
-        if (lane == 0) x[rows[a]] = acc;
+        if (lane == 0) x[rows[a]] = (T)acc;
     }
 }
 
-__global__ void __launch_bounds__(TPB) k_pcg_update(int64_t N, const double* __restrict__ dinv, double* __restrict__ x,
-                                                    double* __restrict__ r, const double* __restrict__ p,
-                                                    const double* __restrict__ q, double* __restrict__ xv, double gamma,
+template <typename T>
+__global__ void __launch_bounds__(TPB) k_coarse(const int32_t* __restrict__ rows, const T* __restrict__ Cinv, int nc,
+                                                const T* __restrict__ r, T* __restrict__ x, const int* done) {
+    if (done && *done) return;
+    coarse_warps<T>(rows, Cinv, nc, r, x, ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5,
+                    ((int64_t)gridDim.x * blockDim.x) >> 5, threadIdx.x & 31);
+}
+
+// ---------------------------------------------------------------------------------
+// The coarse part of the FP32 V-cycle in one launch: one thread-block cluster runs
+// levels top .. 1 down (blocks, residual, restriction), the level-1 solve, and levels
+// 1 .. top up (prolongation, residual update, blocks), with a hardware cluster barrier
+// between the steps.  Coarse levels hold too few rows to fill the GPU, so one cluster of
+// up to 16 SMs does them back to back instead of ~6 launches per level.
+constexpr int CLUSTER_TPB = 1024;
+
+template <int DIM, int P>
+__global__ void __launch_bounds__(CLUSTER_TPB) k_vcycle_cluster(const VcycleCoarse* __restrict__ Vg, const int* done) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    __shared__ VcycleCoarse Vs;  // the level table in shared memory: field reads stay on chip
+    float* sm = reinterpret_cast<float*>(smraw);
+    if (done && *done) return;   // uniform over the cluster: nobody reaches a barrier
+    {
+        const int* src = reinterpret_cast<const int*>(Vg);
+        int* dst = reinterpret_cast<int*>(&Vs);
+        for (int k = threadIdx.x; k < (int)(sizeof(VcycleCoarse) / sizeof(int)); k += blockDim.x) dst[k] = src[k];
+    }
+    __syncthreads();
+    const VcycleCoarse* V = &Vs;
+    cg::cluster_group cl = cg::this_cluster();
+    const int64_t start = (int64_t)cl.block_rank() * blockDim.x + threadIdx.x;
+    const int64_t stride = (int64_t)cl.num_blocks() * blockDim.x;
+    const int lane = threadIdx.x & 31;
+    float* rs = sm + (int64_t)(threadIdx.x >> 5) * V->max_block;
+    const float g = (float)V->gamma;
+    const int top = V->top;
+    for (int li = top; li >= 1; --li) {
+        blocks_warps<float>(V->lv[li], V->r[li], V->x[li], g, start >> 5, stride >> 5, lane, rs);
+        cl.sync();
+        apply_rows<float, DIM, P>(V->lv[li], RESID, V->x[li], V->r[li], V->t[li], nullptr, g, start, stride);
+        cl.sync();
+        restrict_rows<float, DIM, P>(V->lv[li], V->lv[li - 1], V->t[li], V->r[li - 1], li - 1 >= 1 ? V->x[li - 1] : nullptr,
+                                     g, start, stride);
+        cl.sync();
+    }
+    coarse_warps<float>(V->c_rows, V->c_inv, V->nc, V->r[0], V->x[0], start >> 5, stride >> 5, lane);
+    for (int li = 1; li <= top; ++li) {
+        cl.sync();
+        prolong_rows<float, DIM, P>(V->lv[li], V->lv[li - 1], V->x[li - 1], V->e[li], V->x[li], start, stride);
+        cl.sync();
+        apply_rows<float, DIM, P>(V->lv[li], RESID_SMOOTH, V->e[li], V->t[li], V->t[li], V->x[li], g, start, stride);
+        cl.sync();
+        blocks_warps<float>(V->lv[li], V->t[li], V->x[li], g, start >> 5, stride >> 5, lane, rs);
+    }
+}
+
+template <typename TI, typename TO>
+__global__ void __launch_bounds__(TPB) k_convert(int64_t N, const TI* __restrict__ in, TO* __restrict__ out,
+                                                 const int* done) {
+    if (done && *done) return;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) out[i] = (TO)in[i];
+}
+
+// V-cycle input from an FP64 residual: r_lo = (TZ)(rs .* r) (or (TZ) r), xv = gamma dinv .* r_lo
+template <typename TZ>
+__global__ void __launch_bounds__(TPB) k_vcycle_in(int64_t N, const double* __restrict__ r, const TZ* __restrict__ rs,
+                                                   const TZ* __restrict__ dinv, TZ gamma, TZ* __restrict__ rlo,
+                                                   TZ* __restrict__ xv, const int* done) {
+    if (done && *done) return;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
+        const TZ rv = rs ? (TZ)(r[i] * (double)rs[i]) : (TZ)r[i];
+        rlo[i] = rv;
+        xv[i] = gamma * dinv[i] * rv;
+    }
+}
+
+// V-cycle output to FP64: out = zs .* z (or z)
+template <typename TZ>
+__global__ void __launch_bounds__(TPB) k_vcycle_out(int64_t N, const TZ* __restrict__ z, const TZ* __restrict__ zs,
+                                                    double* __restrict__ out) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride)
+        out[i] = zs ? (double)z[i] * (double)zs[i] : (double)z[i];
+}
+
+// z as the CG sees it: z_i = zs_i * z^_i in the scaled FP32 path, z_i otherwise
+template <typename TZ>
+__device__ __forceinline__ double zval(const TZ* z, const TZ* zs, int64_t i) {
+    return zs ? (double)z[i] * (double)zs[i] : (double)z[i];
+}
+
+template <typename TZ>
+__global__ void __launch_bounds__(TPB) k_pcg_update(int64_t N, const TZ* __restrict__ dinv, const TZ* __restrict__ rs,
+                                                    double* __restrict__ x, double* __restrict__ r,
+                                                    const double* __restrict__ p, const double* __restrict__ q,
+                                                    TZ* __restrict__ xv, TZ* __restrict__ rlo, double gamma,
                                                     double* partial, PcgState* st, double* hist) {
     if (st->done) return;
     const double alpha = st->alpha;
@@ -427,7 +627,10 @@ __global__ void __launch_bounds__(TPB) k_pcg_update(int64_t N, const double* __r
         const double ri = fma(-alpha, q[i], r[i]);
         r[i] = ri;
         acc = fma(ri, ri, acc);
-        xv[i] = gamma * dinv[i] * ri;
+        // the V-cycle's residual: r itself (FP64) or r^ = s .* r (scaled FP32)
+        const TZ rv = rs ? (TZ)(ri * (double)rs[i]) : (TZ)ri;
+        if (rlo) rlo[i] = rv;
+        xv[i] = (TZ)gamma * dinv[i] * rv;
     }
     double rr;
     if (finish_reduction(acc, partial, &st->ticket[1], &rr) && threadIdx.x == 0) {
@@ -447,15 +650,22 @@ __global__ void __launch_bounds__(TPB) k_pcg_update(int64_t N, const double* __r
     }
 }
 
-__global__ void __launch_bounds__(TPB) k_pcg_rz(int64_t N, const double* __restrict__ r, const double* __restrict__ z,
+// rz_new = r^T z; flexible CG (Polak-Ribiere) also needs r^T z_prev
+template <typename TZ>
+__global__ void __launch_bounds__(TPB) k_pcg_rz(int64_t N, const double* __restrict__ r, const TZ* __restrict__ z,
+                                                const TZ* __restrict__ zs, const TZ* __restrict__ zprev,
                                                 double* partial, PcgState* st) {
     if (st->done) return;
-    double acc = 0.0;
+    double acc = 0.0, accp = 0.0;
     const int64_t stride = (int64_t)gridDim.x * TPB;
-    for (int64_t i = (int64_t)blockIdx.x * TPB + threadIdx.x; i < N; i += stride) acc = fma(r[i], z[i], acc);
-    double rz;
-    if (finish_reduction(acc, partial, &st->ticket[2], &rz) && threadIdx.x == 0) {
-        st->beta = rz / st->rz;
+    for (int64_t i = (int64_t)blockIdx.x * TPB + threadIdx.x; i < N; i += stride) {
+        acc = fma(r[i], zval(z, zs, i), acc);
+        if (zprev) accp = fma(r[i], zval(zprev, zs, i), accp);
+    }
+    double rz, rzp;
+    if (finish_reduction2(acc, accp, partial, &st->ticket[2], &rz, &rzp) && threadIdx.x == 0) {
+        const double num = zprev ? rz - rzp : rz;
+        st->beta = num / st->rz;
         st->rz = rz;
         if (!isfinite(rz)) {
             st->done = 1;
@@ -464,30 +674,28 @@ __global__ void __launch_bounds__(TPB) k_pcg_rz(int64_t N, const double* __restr
     }
 }
 
-__global__ void __launch_bounds__(TPB) k_pcg_xpay(int64_t N, const double* __restrict__ z, double* __restrict__ p,
-                                                  PcgState* st) {
+template <typename TZ>
+__global__ void __launch_bounds__(TPB) k_pcg_xpay(int64_t N, const TZ* __restrict__ z, const TZ* __restrict__ zs,
+                                                  double* __restrict__ p, TZ* __restrict__ zprev, PcgState* st) {
     if (st->done) return;
     const double beta = st->beta;
-    const int64_t stride = (int64_t)gridDim.x * TPB;
-    for (int64_t i = (int64_t)blockIdx.x * TPB + threadIdx.x; i < N; i += stride) p[i] = fma(beta, p[i], z[i]);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
+        p[i] = fma(beta, p[i], zval(z, zs, i));
+        if (zprev) zprev[i] = z[i];
+    }
 }
 
 __global__ void __launch_bounds__(TPB) k_init_norms(int64_t N, const double* __restrict__ r, const double* __restrict__ b,
                                                     double* partial, PcgState* st, double* hist) {
-    __shared__ double ws[32];
     double a = 0.0, c = 0.0;
     const int64_t stride = (int64_t)gridDim.x * TPB;
     for (int64_t i = (int64_t)blockIdx.x * TPB + threadIdx.x; i < N; i += stride) {
         a = fma(r[i], r[i], a);
         c = fma(b[i], b[i], c);
     }
-    // two partial arrays: [0, G) for ||r||^2 and [G, 2G) for ||b||^2
-    double sb = block_sum(c, ws);
-    if (threadIdx.x == 0) partial[gridDim.x + blockIdx.x] = sb;
-    double rr;
-    if (finish_reduction(a, partial, &st->ticket[3], &rr) && threadIdx.x == 0) {
-        double bb = 0.0;
-        for (int k = 0; k < (int)gridDim.x; ++k) bb += ((volatile double*)partial)[gridDim.x + k];
+    double rr, bb;
+    if (finish_reduction2(a, c, partial, &st->ticket[3], &rr, &bb) && threadIdx.x == 0) {
         st->rr = rr;
         st->bb = bb;
         st->iter = 0;
@@ -507,14 +715,18 @@ __global__ void __launch_bounds__(TPB) k_init_norms(int64_t N, const double* __r
     }
 }
 
-__global__ void __launch_bounds__(TPB) k_init_dir(int64_t N, const double* __restrict__ r, const double* __restrict__ z,
-                                                  double* __restrict__ p, double* partial, PcgState* st) {
+template <typename TZ>
+__global__ void __launch_bounds__(TPB) k_init_dir(int64_t N, const double* __restrict__ r, const TZ* __restrict__ z,
+                                                  const TZ* __restrict__ zs, double* __restrict__ p,
+                                                  TZ* __restrict__ zprev, double* partial, PcgState* st) {
     if (st->done) return;
     double acc = 0.0;
     const int64_t stride = (int64_t)gridDim.x * TPB;
     for (int64_t i = (int64_t)blockIdx.x * TPB + threadIdx.x; i < N; i += stride) {
-        acc = fma(r[i], z[i], acc);
-        p[i] = z[i];
+        const double zi = zval(z, zs, i);
+        acc = fma(r[i], zi, acc);
+        p[i] = zi;
+        if (zprev) zprev[i] = z[i];
     }
     double rz;
     if (finish_reduction(acc, partial, &st->ticket[2], &rz) && threadIdx.x == 0) {
@@ -538,13 +750,6 @@ __global__ void k_set_continue(PcgState* st, cudaGraphConditionalHandle handle) 
     cudaGraphSetConditional(handle, st->done ? 0u : 1u);
 }
 
-inline int grid_for(int64_t n) {
-    int64_t g = (n + TPB - 1) / TPB;
-    if (g < 1) g = 1;
-    if (g > 65535LL * 8) g = 65535LL * 8;
-    return (int)g;
-}
-
 int num_sms() {
     static int sms = 0;
     if (sms == 0) {
@@ -557,8 +762,8 @@ int num_sms() {
 }
 
 // One row per thread.  Large levels: 256-thread blocks.  Small levels: blocks just big
-// enough to give every SM about two of them, so that FP64 work (2 FMA/clk per SM) is
-// spread over the whole GPU instead of a handful of SMs.
+// enough to give every SM about two of them, so that the work is spread over the whole
+// GPU instead of a handful of SMs (FP64 issues 2 FMA/clk per SM).
 struct RowLaunch {
     int grid, block;
 };
@@ -576,15 +781,23 @@ inline RowLaunch row_launch(int64_t n) {
 
 inline int tiles_2d(int m) { return ((m + TX - 1) / TX) * ((m + TY - 1) / TY); }
 
+template <typename T, int P>
+cudaError_t launch_tile2d(const DevLevelT<T>& L, int mode, const T* x, const T* rin, T* out, T* xs, T gamma,
+                          const int* done, cudaStream_t s) {
+    const int g = tiles_2d(L.m);
+    if (mode == APPLY)
+        k_apply_tile2d<T, P, APPLY, false><<<g, TPB, 0, s>>>(L, x, rin, out, xs, gamma, done, nullptr, nullptr);
+    else if (mode == RESID)
+        k_apply_tile2d<T, P, RESID, false><<<g, TPB, 0, s>>>(L, x, rin, out, xs, gamma, done, nullptr, nullptr);
+    else
+        k_apply_tile2d<T, P, RESID_SMOOTH, false><<<g, TPB, 0, s>>>(L, x, rin, out, xs, gamma, done, nullptr, nullptr);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 int reduction_blocks() {
-    if (g_red_blocks == 0) {
-        int dev = 0, sms = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        g_red_blocks = (sms > 0 ? sms : 148) * 4;
-    }
+    if (g_red_blocks == 0) g_red_blocks = num_sms() * 4;
     return g_red_blocks;
 }
 
@@ -599,29 +812,18 @@ int reduction_blocks() {
         else return cudaErrorInvalidValue;                             \
     } while (0)
 
-template <int P>
-cudaError_t launch_tile2d(const DevLevel& L, int mode, const double* x, const double* rin, double* out, double* xs,
-                          double gamma, const int* done, cudaStream_t s) {
-    const int g = tiles_2d(L.m);
-    if (mode == APPLY)
-        k_apply_tile2d<P, APPLY, false><<<g, TPB, 0, s>>>(L, x, rin, out, xs, gamma, done, nullptr, nullptr);
-    else if (mode == RESID)
-        k_apply_tile2d<P, RESID, false><<<g, TPB, 0, s>>>(L, x, rin, out, xs, gamma, done, nullptr, nullptr);
-    else
-        k_apply_tile2d<P, RESID_SMOOTH, false><<<g, TPB, 0, s>>>(L, x, rin, out, xs, gamma, done, nullptr, nullptr);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_apply(const DevLevel& L, int mode, const double* x, const double* rin, double* out, double* xs,
-                         double gamma, const int* done, cudaStream_t s) {
+template <typename T>
+cudaError_t launch_apply(const DevLevelT<T>& L, int mode, const T* x, const T* rin, T* out, T* xs, double gamma,
+                         const int* done, cudaStream_t s) {
     // tiles when there are enough of them to fill the GPU; one row per thread otherwise
     if (L.dim == 2 && tiles_2d(L.m) >= num_sms()) {
-        if (L.p == 1) return launch_tile2d<1>(L, mode, x, rin, out, xs, gamma, done, s);
-        if (L.p == 2) return launch_tile2d<2>(L, mode, x, rin, out, xs, gamma, done, s);
-        if (L.p == 3) return launch_tile2d<3>(L, mode, x, rin, out, xs, gamma, done, s);
+        if (L.p == 1) return launch_tile2d<T, 1>(L, mode, x, rin, out, xs, (T)gamma, done, s);
+        if (L.p == 2) return launch_tile2d<T, 2>(L, mode, x, rin, out, xs, (T)gamma, done, s);
+        if (L.p == 3) return launch_tile2d<T, 3>(L, mode, x, rin, out, xs, (T)gamma, done, s);
     }
     const RowLaunch rl = row_launch(L.N);
-    IMGM_DISPATCH(L.dim, L.p, (k_apply<D, Q><<<rl.grid, rl.block, 0, s>>>(L, mode, x, rin, out, xs, gamma, done)));
+    IMGM_DISPATCH(L.dim, L.p,
+                  (k_apply<T, D, Q><<<rl.grid, rl.block, 0, s>>>(L, mode, x, rin, out, xs, (T)gamma, done)));
     return cudaGetLastError();
 }
 
@@ -629,69 +831,161 @@ cudaError_t launch_apply_pq(const DevLevel& L, const double* p, double* q, doubl
                             cudaStream_t s) {
     if (L.dim == 2) {
         const int g = std::min(tiles_2d(L.m), reduction_blocks());
-        if (L.p == 1) k_apply_tile2d<1, APPLY, true><<<g, TPB, 0, s>>>(L, p, nullptr, q, nullptr, 0.0, &st->done, partial, st);
-        else if (L.p == 2) k_apply_tile2d<2, APPLY, true><<<g, TPB, 0, s>>>(L, p, nullptr, q, nullptr, 0.0, &st->done, partial, st);
-        else if (L.p == 3) k_apply_tile2d<3, APPLY, true><<<g, TPB, 0, s>>>(L, p, nullptr, q, nullptr, 0.0, &st->done, partial, st);
-        else return cudaErrorInvalidValue;
+        if (L.p == 1)
+            k_apply_tile2d<double, 1, APPLY, true><<<g, TPB, 0, s>>>(L, p, nullptr, q, nullptr, 0.0, &st->done, partial, st);
+        else if (L.p == 2)
+            k_apply_tile2d<double, 2, APPLY, true><<<g, TPB, 0, s>>>(L, p, nullptr, q, nullptr, 0.0, &st->done, partial, st);
+        else if (L.p == 3)
+            k_apply_tile2d<double, 3, APPLY, true><<<g, TPB, 0, s>>>(L, p, nullptr, q, nullptr, 0.0, &st->done, partial, st);
+        else
+            return cudaErrorInvalidValue;
         return cudaGetLastError();
     }
     IMGM_DISPATCH(L.dim, L.p, (k_apply_pq<D, Q><<<reduction_blocks(), TPB, 0, s>>>(L, p, q, partial, st)));
     return cudaGetLastError();
 }
 
-cudaError_t launch_scale_diag(const DevLevel& L, const double* r, double* x, double gamma, const int* done,
-                              cudaStream_t s) {
+template <typename T>
+cudaError_t launch_scale_diag(const DevLevelT<T>& L, const T* r, T* x, double gamma, const int* done, cudaStream_t s) {
     const RowLaunch rl = row_launch(L.N);
-    k_scale_diag<<<rl.grid, rl.block, 0, s>>>(L.N, L.dinv, r, x, gamma, done);
+    k_scale_diag<T><<<rl.grid, rl.block, 0, s>>>(L.N, L.dinv, r, x, (T)gamma, done);
     return cudaGetLastError();
 }
 
-cudaError_t launch_blocks(const DevLevel& L, const double* r, double* x, double gamma, const int* done,
-                          cudaStream_t s) {
+template <typename T>
+cudaError_t launch_blocks(const DevLevelT<T>& L, const T* r, T* x, double gamma, const int* done, cudaStream_t s) {
     if (L.nblk == 0) return cudaSuccess;
-    const int warps = 2;                        // small blocks: spread the FP64 work over all SMs
+    const int warps = 2;                        // small blocks: spread the work over all SMs
     int64_t g = (L.nblk + warps - 1) / warps;
     if (g > 65535) g = 65535;
-    size_t smem = (size_t)warps * L.max_block * sizeof(double);
-    k_blocks<<<(int)g, 32 * warps, smem, s>>>(L, r, x, gamma, done);
+    size_t smem = (size_t)warps * L.max_block * sizeof(T);
+    k_blocks<T><<<(int)g, 32 * warps, smem, s>>>(L, r, x, (T)gamma, done);
     return cudaGetLastError();
 }
 
-cudaError_t launch_restrict(const DevLevel& F, const DevLevel& C, const double* rf, double* rc, double* xc,
-                            double gamma, const int* done, cudaStream_t s) {
+template <typename T>
+cudaError_t launch_restrict(const DevLevelT<T>& F, const DevLevelT<T>& C, const T* rf, T* rc, T* xc, double gamma,
+                            const int* done, cudaStream_t s) {
     const RowLaunch rl = row_launch(C.N);
-    IMGM_DISPATCH(F.dim, F.p, (k_restrict<D, Q><<<rl.grid, rl.block, 0, s>>>(F, C, rf, rc, xc, gamma, done)));
+    IMGM_DISPATCH(F.dim, F.p, (k_restrict<T, D, Q><<<rl.grid, rl.block, 0, s>>>(F, C, rf, rc, xc, (T)gamma, done)));
     return cudaGetLastError();
 }
 
-cudaError_t launch_prolong(const DevLevel& F, const DevLevel& C, const double* xc, double* e, double* x,
-                           const int* done, cudaStream_t s) {
+template <typename T>
+cudaError_t launch_prolong(const DevLevelT<T>& F, const DevLevelT<T>& C, const T* xc, T* e, T* x, const int* done,
+                           cudaStream_t s) {
     const RowLaunch rl = row_launch(F.N);
-    IMGM_DISPATCH(F.dim, F.p, (k_prolong<D, Q><<<rl.grid, rl.block, 0, s>>>(F, C, xc, e, x, done)));
+    IMGM_DISPATCH(F.dim, F.p, (k_prolong<T, D, Q><<<rl.grid, rl.block, 0, s>>>(F, C, xc, e, x, done)));
     return cudaGetLastError();
 }
 
-cudaError_t launch_coarse(const int32_t* rows, const double* Cinv, int nc, const double* r, double* x,
-                          const int* done, cudaStream_t s) {
+template <typename T>
+cudaError_t launch_coarse(const int32_t* rows, const T* Cinv, int nc, const T* r, T* x, const int* done,
+                          cudaStream_t s) {
     if (nc == 0) return cudaSuccess;
     const int warps = 2;
-    k_coarse<<<(nc + warps - 1) / warps, 32 * warps, 0, s>>>(rows, Cinv, nc, r, x, done);
+    k_coarse<T><<<(nc + warps - 1) / warps, 32 * warps, 0, s>>>(rows, Cinv, nc, r, x, done);
     return cudaGetLastError();
 }
 
-cudaError_t launch_pcg_update(const DevLevel& L, double* x, double* r, const double* p, const double* q, double* xv,
-                              double gamma, double* partial, PcgState* st, double* hist, cudaStream_t s) {
-    k_pcg_update<<<reduction_blocks(), TPB, 0, s>>>(L.N, L.dinv, x, r, p, q, xv, gamma, partial, st, hist);
+int vcycle_cluster_size() {
+    static int cs = -1;
+    if (cs < 0) {
+        cs = 0;
+        auto kern = k_vcycle_cluster<2, 2>;
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) cudaGetLastError();
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(16, 1, 1);
+        cfg.blockDim = dim3(CLUSTER_TPB, 1, 1);
+        cfg.dynamicSmemBytes = 32 * 64 * sizeof(float);
+        cudaLaunchAttribute attr;
+        attr.id = cudaLaunchAttributeClusterDimension;
+        attr.val.clusterDim.x = 16;
+        attr.val.clusterDim.y = 1;
+        attr.val.clusterDim.z = 1;
+        cfg.attrs = &attr;
+        cfg.numAttrs = 1;
+        int n = 0;
+        if (cudaOccupancyMaxPotentialClusterSize(&n, kern, &cfg) == cudaSuccess && n > 0) cs = n >= 16 ? 16 : (n >= 8 ? 8 : n);
+        else cudaGetLastError();
+    }
+    return cs;
+}
+
+cudaError_t launch_vcycle_cluster(int dim, int p, const VcycleCoarse* V, int max_block, const int* done,
+                                  cudaStream_t s) {
+    const int cs = vcycle_cluster_size();
+    if (cs <= 0) return cudaErrorNotSupported;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(cs, 1, 1);
+    cfg.blockDim = dim3(CLUSTER_TPB, 1, 1);
+    cfg.dynamicSmemBytes = (size_t)(CLUSTER_TPB / 32) * max_block * sizeof(float);
+    cfg.stream = s;
+    cudaLaunchAttribute attr;
+    attr.id = cudaLaunchAttributeClusterDimension;
+    attr.val.clusterDim.x = cs;
+    attr.val.clusterDim.y = 1;
+    attr.val.clusterDim.z = 1;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+#define IMGM_CLUSTER_CASE(D_, P_)                                                                                 \
+    if (dim == D_ && p == P_) {                                                                                   \
+        auto kern = k_vcycle_cluster<D_, P_>;                                                                     \
+        if (cs > 8) cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);                \
+        return cudaLaunchKernelEx(&cfg, kern, V, done);                                                           \
+    }
+    IMGM_CLUSTER_CASE(2, 1)
+    IMGM_CLUSTER_CASE(2, 2)
+    IMGM_CLUSTER_CASE(2, 3)
+    IMGM_CLUSTER_CASE(3, 1)
+    IMGM_CLUSTER_CASE(3, 2)
+    IMGM_CLUSTER_CASE(3, 3)
+#undef IMGM_CLUSTER_CASE
+    return cudaErrorInvalidValue;
+}
+
+template <typename TI, typename TO>
+cudaError_t launch_convert(int64_t N, const TI* in, TO* out, const int* done, cudaStream_t s) {
+    const RowLaunch rl = row_launch(N);
+    k_convert<TI, TO><<<rl.grid, rl.block, 0, s>>>(N, in, out, done);
     return cudaGetLastError();
 }
 
-cudaError_t launch_pcg_rz(int64_t N, const double* r, const double* z, double* partial, PcgState* st, cudaStream_t s) {
-    k_pcg_rz<<<reduction_blocks(), TPB, 0, s>>>(N, r, z, partial, st);
+template <typename TZ>
+cudaError_t launch_vcycle_in(int64_t N, const double* r, const TZ* rs, const TZ* dinv, double gamma, TZ* r_lo, TZ* xv,
+                             const int* done, cudaStream_t s) {
+    const RowLaunch rl = row_launch(N);
+    k_vcycle_in<TZ><<<rl.grid, rl.block, 0, s>>>(N, r, rs, dinv, (TZ)gamma, r_lo, xv, done);
     return cudaGetLastError();
 }
 
-cudaError_t launch_pcg_xpay(int64_t N, const double* z, double* p, PcgState* st, cudaStream_t s) {
-    k_pcg_xpay<<<grid_for(N), TPB, 0, s>>>(N, z, p, st);
+template <typename TZ>
+cudaError_t launch_vcycle_out(int64_t N, const TZ* z, const TZ* zs, double* out, cudaStream_t s) {
+    const RowLaunch rl = row_launch(N);
+    k_vcycle_out<TZ><<<rl.grid, rl.block, 0, s>>>(N, z, zs, out);
+    return cudaGetLastError();
+}
+
+template <typename TZ>
+cudaError_t launch_pcg_update(const DevLevel& L, const TZ* dinv_z, double* x, double* r, const double* p,
+                              const double* q, TZ* xv, TZ* r_lo, const TZ* rs, double gamma, double* partial,
+                              PcgState* st, double* hist, cudaStream_t s) {
+    k_pcg_update<TZ><<<reduction_blocks(), TPB, 0, s>>>(L.N, dinv_z, rs, x, r, p, q, xv, r_lo, gamma, partial, st, hist);
+    return cudaGetLastError();
+}
+
+template <typename TZ>
+cudaError_t launch_pcg_rz(int64_t N, const double* r, const TZ* z, const TZ* zs, const TZ* zprev, double* partial,
+                          PcgState* st, cudaStream_t s) {
+    k_pcg_rz<TZ><<<reduction_blocks(), TPB, 0, s>>>(N, r, z, zs, zprev, partial, st);
+    return cudaGetLastError();
+}
+
+template <typename TZ>
+cudaError_t launch_pcg_xpay(int64_t N, const TZ* z, const TZ* zs, double* p, TZ* zprev, PcgState* st,
+                            cudaStream_t s) {
+    const RowLaunch rl = row_launch(N);
+    k_pcg_xpay<TZ><<<rl.grid, rl.block, 0, s>>>(N, z, zs, p, zprev, st);
     return cudaGetLastError();
 }
 
@@ -701,9 +995,10 @@ cudaError_t launch_pcg_init_norms(int64_t N, const double* r, const double* b, d
     return cudaGetLastError();
 }
 
-cudaError_t launch_pcg_init_dir(int64_t N, const double* r, const double* z, double* p, double* partial,
-                                PcgState* st, cudaStream_t s) {
-    k_init_dir<<<reduction_blocks(), TPB, 0, s>>>(N, r, z, p, partial, st);
+template <typename TZ>
+cudaError_t launch_pcg_init_dir(int64_t N, const double* r, const TZ* z, const TZ* zs, double* p, TZ* zprev,
+                                double* partial, PcgState* st, cudaStream_t s) {
+    k_init_dir<TZ><<<reduction_blocks(), TPB, 0, s>>>(N, r, z, zs, p, zprev, partial, st);
     return cudaGetLastError();
 }
 
@@ -716,5 +1011,32 @@ cudaError_t launch_set_continue(PcgState* st, unsigned long long handle, cudaStr
     k_set_continue<<<1, 1, 0, s>>>(st, (cudaGraphConditionalHandle)handle);
     return cudaGetLastError();
 }
+
+// explicit instantiations: FP64 path and mixed-precision (FP32) V-cycle
+#define IMGM_INST(T)                                                                                              \
+    template cudaError_t launch_apply<T>(const DevLevelT<T>&, int, const T*, const T*, T*, T*, double, const int*, \
+                                         cudaStream_t);                                                            \
+    template cudaError_t launch_scale_diag<T>(const DevLevelT<T>&, const T*, T*, double, const int*, cudaStream_t); \
+    template cudaError_t launch_blocks<T>(const DevLevelT<T>&, const T*, T*, double, const int*, cudaStream_t);     \
+    template cudaError_t launch_restrict<T>(const DevLevelT<T>&, const DevLevelT<T>&, const T*, T*, T*, double,     \
+                                            const int*, cudaStream_t);                                             \
+    template cudaError_t launch_prolong<T>(const DevLevelT<T>&, const DevLevelT<T>&, const T*, T*, T*, const int*,  \
+                                           cudaStream_t);                                                          \
+    template cudaError_t launch_coarse<T>(const int32_t*, const T*, int, const T*, T*, const int*, cudaStream_t);   \
+    template cudaError_t launch_pcg_update<T>(const DevLevel&, const T*, double*, double*, const double*,           \
+                                              const double*, T*, T*, const T*, double, double*, PcgState*,          \
+                                              double*, cudaStream_t);                                              \
+    template cudaError_t launch_pcg_rz<T>(int64_t, const double*, const T*, const T*, const T*, double*, PcgState*, \
+                                          cudaStream_t);                                                           \
+    template cudaError_t launch_pcg_xpay<T>(int64_t, const T*, const T*, double*, T*, PcgState*, cudaStream_t);     \
+    template cudaError_t launch_pcg_init_dir<T>(int64_t, const double*, const T*, const T*, double*, T*, double*,   \
+                                                PcgState*, cudaStream_t);                                          \
+    template cudaError_t launch_vcycle_in<T>(int64_t, const double*, const T*, const T*, double, T*, T*, const int*, \
+                                             cudaStream_t);                                                        \
+    template cudaError_t launch_vcycle_out<T>(int64_t, const T*, const T*, double*, cudaStream_t);
+IMGM_INST(double)
+IMGM_INST(float)
+template cudaError_t launch_convert<double, float>(int64_t, const double*, float*, const int*, cudaStream_t);
+template cudaError_t launch_convert<float, double>(int64_t, const float*, double*, const int*, cudaStream_t);
 
 }  // namespace imgm

@@ -1,6 +1,8 @@
 // Device-side data of one multigrid level and the launch wrappers of the hot-path
 // kernels (operator apply, Schwarz smoother, restriction, prolongation, coarse solve,
-// CG vector updates).  All arithmetic is FP64.
+// CG vector updates).  The V-cycle kernels are templated on the storage and arithmetic
+// type T (double for the FP64 path, float for the mixed-precision path); the CG kernels
+// are FP64 and read the preconditioned residual z in either type.
 #pragma once
 
 #include <cstdint>
@@ -9,28 +11,34 @@
 namespace imgm {
 
 // One level as the kernels see it (all pointers are device pointers).
-struct DevLevel {
+template <typename T>
+struct DevLevelT {
     int dim = 2, p = 2, m = 0, ncoef = 0;
     int64_t N = 0;
     const int32_t* rowinfo = nullptr;   // [N]: -2 inactive, -1 tensor-stencil row, >= 0 stored row id
-    const double* band_coef = nullptr;  // [ncoef][nb]
+    const T* band_coef = nullptr;       // [ncoef][nb]
     int32_t nb = 0;
-    const double* K1 = nullptr;         // [m][2p+1]
-    const double* M1 = nullptr;         // [m][2p+1]
-    const double* dinv = nullptr;       // [N]
+    const T* K1 = nullptr;              // [m][2p+1]
+    const T* M1 = nullptr;              // [m][2p+1]
+    const T* dinv = nullptr;            // [N]
     int32_t nblk = 0;
     int32_t max_block = 1;
     const int64_t* blk_ptr = nullptr;
     const int32_t* blk_idx = nullptr;
     const int64_t* blk_vptr = nullptr;
-    const double* blk_val = nullptr;
+    const T* blk_val = nullptr;
     // restriction to the next coarser level (levels >= 2)
     const int32_t* r_first = nullptr;   // [m_c]
-    const double* r_w = nullptr;        // [m_c][p+2]
+    const T* r_w = nullptr;             // [m_c][p+2]
     const int32_t* t_first = nullptr;   // [m]
-    const double* t_w = nullptr;        // [m][TW]
+    const T* t_w = nullptr;             // [m][TW]
     int TW = 0;
+    // Jacobi scaling of the mixed-precision V-cycle (nullptr on the FP64 path):
+    // s = 1/sqrt(A_ii), d = sqrt(A_ii) on active rows, 0 elsewhere
+    const T* s = nullptr;
+    const T* d = nullptr;
 };
+using DevLevel = DevLevelT<double>;
 
 // Scalars of the CG iteration, kept on the device.
 struct PcgState {
@@ -43,50 +51,102 @@ struct PcgState {
     double true_rr;     // ||b - A x||^2 at exit
     int iter, maxit, done, status;
     unsigned int ticket[4];   // last-block reduction counters
+    double rz_prev;     // r_{k+1}^T z_k (flexible CG)
+    int flexible;       // 1: Polak-Ribiere beta (mixed-precision V-cycle)
+    int pad;
 };
 
 enum ApplyMode { APPLY = 0, RESID = 1, RESID_SMOOTH = 2 };
 
 // y = A x (APPLY), out = rin - A x (RESID), or out = rin - A x followed by
 // xs += gamma * dinv .* out (RESID_SMOOTH).  `out` may alias `rin`.
-cudaError_t launch_apply(const DevLevel& L, int mode, const double* x, const double* rin, double* out, double* xs,
-                         double gamma, const int* done, cudaStream_t s);
-// q = A p and the partial sums of p^T q; the last block sets alpha = rz / (p^T q) in st.
+template <typename T>
+cudaError_t launch_apply(const DevLevelT<T>& L, int mode, const T* x, const T* rin, T* out, T* xs, double gamma,
+                         const int* done, cudaStream_t s);
+// x = gamma * dinv .* r
+template <typename T>
+cudaError_t launch_scale_diag(const DevLevelT<T>& L, const T* r, T* x, double gamma, const int* done, cudaStream_t s);
+// x[idx_j] += gamma * A_j^{-1} r[idx_j] for every stored Schwarz block (atomic adds)
+template <typename T>
+cudaError_t launch_blocks(const DevLevelT<T>& L, const T* r, T* x, double gamma, const int* done, cudaStream_t s);
+// rc = R rf on the coarse rows; if xc != nullptr also xc = gamma * dinv_c .* rc
+template <typename T>
+cudaError_t launch_restrict(const DevLevelT<T>& F, const DevLevelT<T>& C, const T* rf, T* rc, T* xc, double gamma,
+                            const int* done, cudaStream_t s);
+// e = R^T xc on the fine rows (0 on inactive rows); if x != nullptr also x += e
+template <typename T>
+cudaError_t launch_prolong(const DevLevelT<T>& F, const DevLevelT<T>& C, const T* xc, T* e, T* x, const int* done,
+                           cudaStream_t s);
+// x[rows] = Cinv r[rows] (dense coarsest-level inverse, row-major nc x nc)
+template <typename T>
+cudaError_t launch_coarse(const int32_t* rows, const T* Cinv, int nc, const T* r, T* x, const int* done,
+                          cudaStream_t s);
+// elementwise type conversion out = (TO) in
+template <typename TI, typename TO>
+cudaError_t launch_convert(int64_t N, const TI* in, TO* out, const int* done, cudaStream_t s);
+
+// V-cycle input from an FP64 residual: r_lo = (TZ)(rs .* r) (rs == nullptr: (TZ) r) and
+// xv = gamma * dinv .* r_lo (the diagonal part of the first smoothing step)
+template <typename TZ>
+cudaError_t launch_vcycle_in(int64_t N, const double* r, const TZ* rs, const TZ* dinv, double gamma, TZ* r_lo, TZ* xv,
+                             const int* done, cudaStream_t s);
+// V-cycle output in FP64: out = zs .* z (zs == nullptr: out = z)
+template <typename TZ>
+cudaError_t launch_vcycle_out(int64_t N, const TZ* z, const TZ* zs, double* out, cudaStream_t s);
+
+// q = A p (FP64) and the partial sums of p^T q; the last block sets alpha = rz / (p^T q).
 cudaError_t launch_apply_pq(const DevLevel& L, const double* p, double* q, double* partial, PcgState* st,
                             cudaStream_t s);
-// x = gamma * dinv .* r
-cudaError_t launch_scale_diag(const DevLevel& L, const double* r, double* x, double gamma, const int* done,
-                              cudaStream_t s);
-// x[idx_j] += gamma * A_j^{-1} r[idx_j] for every stored Schwarz block (atomic adds)
-cudaError_t launch_blocks(const DevLevel& L, const double* r, double* x, double gamma, const int* done,
-                          cudaStream_t s);
-// rc = R rf on the coarse rows; if xc != nullptr also xc = gamma * dinv_c .* rc
-cudaError_t launch_restrict(const DevLevel& F, const DevLevel& C, const double* rf, double* rc, double* xc,
-                            double gamma, const int* done, cudaStream_t s);
-// e = R^T xc on the fine rows (0 on inactive rows); if x != nullptr also x += e
-cudaError_t launch_prolong(const DevLevel& F, const DevLevel& C, const double* xc, double* e, double* x,
-                           const int* done, cudaStream_t s);
-// x[rows] = Cinv r[rows] (dense coarsest-level inverse, row-major nc x nc)
-cudaError_t launch_coarse(const int32_t* rows, const double* Cinv, int nc, const double* r, double* x,
-                          const int* done, cudaStream_t s);
 // CG: x += alpha p, r -= alpha q, rr = ||r||^2 (last block: iteration count, history,
-// convergence); then xv = gamma * dinv .* r for the V-cycle's first smoothing step
-cudaError_t launch_pcg_update(const DevLevel& L, double* x, double* r, const double* p, const double* q, double* xv,
-                              double gamma, double* partial, PcgState* st, double* hist, cudaStream_t s);
-// rz_new = r^T z; beta = rz_new / rz; rz = rz_new (last block)
-cudaError_t launch_pcg_rz(int64_t N, const double* r, const double* z, double* partial, PcgState* st, cudaStream_t s);
-// p = z + beta p
-cudaError_t launch_pcg_xpay(int64_t N, const double* z, double* p, PcgState* st, cudaStream_t s);
+// convergence); then xv = gamma * dinv .* r in the V-cycle's type (the first smoothing
+// step), and r_lo = (TZ) r when r_lo != nullptr (the V-cycle's copy of r)
+// (rs: the V-cycle's scale 1/sqrt(A_ii), nullptr on the FP64 path)
+template <typename TZ>
+cudaError_t launch_pcg_update(const DevLevel& L, const TZ* dinv_z, double* x, double* r, const double* p,
+                              const double* q, TZ* xv, TZ* r_lo, const TZ* rs, double gamma, double* partial,
+                              PcgState* st, double* hist, cudaStream_t s);
+// rz_new = r^T z (and r^T z_prev when zprev != nullptr: flexible CG); beta; rz = rz_new.
+// z = zs .* z^ when zs != nullptr (scaled V-cycle), z otherwise.
+template <typename TZ>
+cudaError_t launch_pcg_rz(int64_t N, const double* r, const TZ* z, const TZ* zs, const TZ* zprev, double* partial,
+                          PcgState* st, cudaStream_t s);
+// p = z + beta p (and zprev = z^ when zprev != nullptr)
+template <typename TZ>
+cudaError_t launch_pcg_xpay(int64_t N, const TZ* z, const TZ* zs, double* p, TZ* zprev, PcgState* st,
+                            cudaStream_t s);
 // CG start: rr = ||r||^2, bb = ||b||^2, convergence test of the initial guess (last block)
 cudaError_t launch_pcg_init_norms(int64_t N, const double* r, const double* b, double* partial, PcgState* st,
                                   double* hist, cudaStream_t s);
-// CG start after the first V-cycle: rz = r^T z, p = z
-cudaError_t launch_pcg_init_dir(int64_t N, const double* r, const double* z, double* p, double* partial,
-                                PcgState* st, cudaStream_t s);
+// CG start after the first V-cycle: rz = r^T z, p = z (and zprev = z when zprev != nullptr)
+template <typename TZ>
+cudaError_t launch_pcg_init_dir(int64_t N, const double* r, const TZ* z, const TZ* zs, double* p, TZ* zprev,
+                                double* partial, PcgState* st, cudaStream_t s);
 // true_rr = ||v||^2 (last block)
 cudaError_t launch_true_residual_norm(int64_t N, const double* v, double* partial, PcgState* st, cudaStream_t s);
 // sets the conditional of the solve loop to !done
 cudaError_t launch_set_continue(PcgState* st, unsigned long long handle, cudaStream_t s);
+
+// The coarse part of the FP32 V-cycle (levels top .. 1 and the level-1 solve) as one
+// thread-block-cluster launch.  V lives in device memory (a multiple of 4 bytes; the
+// kernel copies it to shared memory).
+constexpr int VCYCLE_MAX_LEVELS = 16;
+struct VcycleCoarse {
+    DevLevelT<float> lv[VCYCLE_MAX_LEVELS];
+    float* x[VCYCLE_MAX_LEVELS];
+    float* r[VCYCLE_MAX_LEVELS];
+    float* t[VCYCLE_MAX_LEVELS];
+    float* e[VCYCLE_MAX_LEVELS];
+    const int32_t* c_rows;
+    const float* c_inv;
+    int nc;
+    int top;            // highest level index handled (the finest level's restriction fills r[top], x[top])
+    int max_block;      // largest Schwarz block over levels 1..top
+    double gamma;
+};
+// cluster size the device supports for it (0: none)
+int vcycle_cluster_size();
+cudaError_t launch_vcycle_cluster(int dim, int p, const VcycleCoarse* V, int max_block, const int* done,
+                                  cudaStream_t s);
 
 int reduction_blocks();   // fixed number of blocks of every reducing kernel
 

@@ -1281,6 +1281,63 @@ struct Builder {
         return true;
     }
 
+    // FP32 copies of every level in Jacobi-scaled variables (mixed-precision V-cycle)
+    void build_fp32() {
+        for (int li = 0; li < L; ++li) {
+            LevelData& lv = H.lv[li];
+            const int64_t N = lv.N, m = lv.m, nb = (int64_t)lv.band_rows.size();
+            std::vector<double> dg(N, 0.0), row(ncoef);
+            for (int64_t r = 0; r < N; ++r) {
+                if (!lv.active[r]) continue;
+                row_coeffs(lv, r, row.data());
+                dg[r] = std::sqrt(row[ncoef / 2]);
+            }
+            lv.f_d.assign(N, 0.0f);
+            lv.f_s.assign(N, 0.0f);
+            for (int64_t r = 0; r < N; ++r)
+                if (dg[r] > 0.0) {
+                    lv.f_d[r] = (float)dg[r];
+                    lv.f_s[r] = (float)(1.0 / dg[r]);
+                }
+            lv.f_band_coef.assign(lv.band_coef.size(), 0.0f);
+            for (int64_t bi = 0; bi < nb; ++bi) {
+                const int64_t r = lv.band_rows[bi];
+                int i[3];
+                unflat(r, m, i);
+                for (int c = 0; c < ncoef; ++c) {
+                    const double v = lv.band_coef[(size_t)c * nb + bi];
+                    if (v == 0.0) continue;
+                    int o[3] = {c % W - p, (c / W) % W - p, dim == 3 ? c / (W * W) - p : 0};
+                    int j[3] = {i[0] + o[0], i[1] + o[1], i[2] + o[2]};
+                    const int64_t jf = flat(j, m);
+                    if (dg[r] > 0.0 && dg[jf] > 0.0) lv.f_band_coef[(size_t)c * nb + bi] = (float)(v / (dg[r] * dg[jf]));
+                }
+            }
+            lv.f_K1.assign(lv.K1.begin(), lv.K1.end());
+            lv.f_M1.assign(lv.M1.begin(), lv.M1.end());
+            lv.f_r_w.assign(lv.r_w.begin(), lv.r_w.end());
+            lv.f_t_w.assign(lv.t_w.begin(), lv.t_w.end());
+            lv.f_dinv.assign(N, 0.0f);
+            for (int64_t r = 0; r < (int64_t)lv.dinv.size(); ++r) lv.f_dinv[r] = (float)(lv.dinv[r] * dg[r] * dg[r]);
+            lv.f_blk_val.assign(lv.blk_val.size(), 0.0f);
+            const int64_t nblk = lv.blk_ptr.empty() ? 0 : (int64_t)lv.blk_ptr.size() - 1;
+            for (int64_t b = 0; b < nblk; ++b) {
+                const int64_t s0 = lv.blk_ptr[b], nj = lv.blk_ptr[b + 1] - s0, v0 = lv.blk_vptr[b];
+                for (int64_t c = 0; c < nj; ++c)
+                    for (int64_t a = 0; a < nj; ++a)
+                        lv.f_blk_val[v0 + c * nj + a] =
+                            (float)(lv.blk_val[v0 + c * nj + a] * dg[lv.blk_idx[s0 + a]] * dg[lv.blk_idx[s0 + c]]);
+            }
+            if (li == 0) {
+                const size_t nc = H.c_rows.size();
+                H.f_c_inv.assign(nc * nc, 0.0f);
+                for (size_t a = 0; a < nc; ++a)
+                    for (size_t c = 0; c < nc; ++c)
+                        H.f_c_inv[a * nc + c] = (float)(H.c_inv[a * nc + c] * dg[H.c_rows[a]] * dg[H.c_rows[c]]);
+            }
+        }
+    }
+
     bool run(std::string& err) {
         basis.resize(L);
         Ke.resize(L);
@@ -1304,6 +1361,7 @@ struct Builder {
         if (!build_coarse_solve(err)) return false;
         for (int li = L - 1; li >= 1; --li)
             if (!build_blocks(li, err)) return false;
+        if (pb.precision == 1) build_fp32();
         return true;
     }
 };
@@ -1322,6 +1380,7 @@ bool build_hierarchy(const Problem& pb, Hierarchy& H, std::string& err) {
     if (pb.depth < 0 || pb.depth > 6) { err = "depth must be in 0..6"; return false; }
     if (pb.bc != 0 && pb.bc != 1) { err = "bc must be 0 (penalty) or 1 (Nitsche)"; return false; }
     if (!(pb.hi > pb.lo)) { err = "hi must exceed lo"; return false; }
+    if (pb.precision != 0 && pb.precision != 1) { err = "precision must be 0 (FP64) or 1 (FP32 V-cycle)"; return false; }
     double Nd = std::pow((double)(pb.n + pb.p), pb.dim);
     if (Nd > 2.0e9) { err = "grid too large for 32-bit row indices"; return false; }
     H = Hierarchy();

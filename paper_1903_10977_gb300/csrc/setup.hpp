@@ -19,6 +19,7 @@ struct Problem {
     double lo = 0.0, hi = 1.0;
     int n = 32, basis = 0, p = 2, levels = 3, depth = 0, bc = 1;
     double gamma = 0.0;
+    int precision = 0;   // 0: FP64 V-cycle, 1: FP32 V-cycle (FP32 copies are built)
 };
 
 // Everything the kernels of one level need.  Row index = ix + m*(iy + m*iz).
@@ -48,6 +49,10 @@ struct LevelData {
     // element status (finest-descendant based)
     std::vector<uint8_t> elem_active;  // [n^d]
     std::vector<uint8_t> elem_full;    // [n^d]
+    // FP32 copies for the mixed-precision V-cycle, in Jacobi-scaled variables
+    // (D = diag(A)^{1/2}): stored rows A_ij/(d_i d_j), block inverses d_a A_j^{-1}_ab d_b,
+    // dinv d_i^2 / A_ii-sums, the scale s = 1/d and d itself; tables unscaled
+    std::vector<float> f_band_coef, f_K1, f_M1, f_dinv, f_blk_val, f_r_w, f_t_w, f_s, f_d;
 };
 
 struct Hierarchy {
@@ -57,6 +62,7 @@ struct Hierarchy {
     std::vector<double> b;             // finest right-hand side [N_L]
     std::vector<int32_t> c_rows;       // active rows of level 1 kept by the Remark 3.3 rule
     std::vector<double> c_inv;         // [nc x nc] row-major inverse on those rows
+    std::vector<float> f_c_inv;        // FP32 d_a C_ab d_b (scaled variables of level 1)
     int64_t coarse_pruned = 0;
     int64_t n_cut = 0;
     double setup_seconds = 0.0;

@@ -205,6 +205,46 @@ def test_pcg_converged(pair):
     assert mr < (1e-10 if res["iterations"] == it else 1e-6)
 
 
+# ------------------------------------------------- mixed-precision V-cycle
+@pytest.fixture(scope="module", params=CASES, ids=[f"{n}-{'-'.join(f'{k}{v}' for k, v in o.items())}" for n, o in CASES])
+def mixed(request):
+    name, ov = request.param
+    pr, lay, d, H = oracle_for(name, **ov)
+    S = lib.Solver(pr.dim, lay.centers, lay.radii, pr.n, pr.degree, pr.levels, pr.depth, pr.bc, basis=pr.basis,
+                   lo=lay.lo, hi=lay.hi, precision=1)
+    yield pr, d, H, S
+    S.close()
+
+
+def test_mixed_vcycle_close_to_oracle(mixed):
+    """The FP32 V-cycle (Jacobi-scaled data) equals the FP64 oracle's B r up to FP32
+    rounding: 1e-4 in the energy norm leaves the CG convergence unchanged (next test)."""
+    pr, d, H, S = mixed
+    r = random_grid_vector(d.n_active, 60)
+    z = host(S.apply_preconditioner(dev(d.to_full(r))))
+    ref = H.precondition(r)
+    er = energy_rel(z[d.active] - ref, ref, d.A)
+    record(energy_rel=er)
+    assert er < 1e-4
+    assert not np.any(np.delete(z, d.active))
+
+
+def test_mixed_pcg_reaches_the_same_residual(mixed):
+    """FP32 V-cycle inside the FP64 flexible CG: the same 1e-8 relative residual, the
+    true residual recomputed in FP64, a solution equal to the oracle's to the accuracy of
+    the stopping test, and no more than 10 % more iterations than the FP64 path."""
+    pr, d, H, S = mixed
+    x, res, _ = S.pcg_solve(dev(d.to_full(d.b)), rtol=1e-8, maxit=1000)
+    ref, it, _ = MG.pcg(d.A, d.b, H.precondition, rtol=1e-8, maxit=1000)
+    x = host(x)[d.active]
+    mr = mass_rel(x - ref, ref, d.M)
+    record(iterations=res["iterations"], oracle_iterations=it, mass_rel=mr, true_rel_residual=res["true_rel_residual"])
+    assert res["status"] == lib.IMGM_OK and res["rel_residual"] <= 1e-8
+    assert res["true_rel_residual"] <= 1e-7
+    assert res["iterations"] <= 1.1 * it + 2
+    assert mr < 1e-6
+
+
 # ---------------------------------------------------------------- edge cases
 @pytest.fixture(scope="module")
 def small():
