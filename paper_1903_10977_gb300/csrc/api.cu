@@ -10,6 +10,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <memory>
 #include <mutex>
@@ -78,6 +79,7 @@ struct imgm_handle {
     imgm::VcycleCoarse* vc = nullptr;  // device copy of the coarse levels for the cluster V-cycle (FP32)
     int vc_top = -1;                   // highest level index the cluster kernel handles (-1: not used)
     int vc_max_block = 1;
+    size_t vc_smem = 0;                // dynamic shared memory of the cluster launch
     double* b = nullptr;               // built-in right-hand side
     // CG state
     double *cx = nullptr, *cr = nullptr, *cp = nullptr, *cq = nullptr, *cz = nullptr, *cb = nullptr;
@@ -90,6 +92,7 @@ struct imgm_handle {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     bool graph_failed = false;
+    cudaStream_t capture = nullptr;    // the solve graph is captured here (the caller's stream may be the legacy one)
     std::string err;
 
     template <class T>
@@ -109,6 +112,7 @@ struct imgm_handle {
     }
     ~imgm_handle() {
         if (exec) cudaGraphExecDestroy(exec);
+        if (capture) cudaStreamDestroy(capture);
         if (graph) cudaGraphDestroy(graph);
         for (void* v : allocs) cudaFree(v);
     }
@@ -196,7 +200,7 @@ cudaError_t enqueue_vcycle(imgm_handle* h, const T* r, T* z, const int* done, cu
             if ((e = imgm::launch_restrict<T>(A::d(F), A::d(C), A::t(F), A::r(C), xc, g, done, s)) != cudaSuccess)
                 return e;
         }
-        if ((e = imgm::launch_vcycle_cluster(h->dim, h->p, h->vc, h->vc_max_block, done, s)) != cudaSuccess) return e;
+        if ((e = imgm::launch_vcycle_cluster(h->dim, h->p, h->vc, h->vc_smem, done, s)) != cudaSuccess) return e;
         for (int li = ct + 1; li <= L - 1; ++li) {
             LevelDev& F = h->lv[li];
             LevelDev& C = h->lv[li - 1];
@@ -299,10 +303,15 @@ cudaError_t enqueue_solve_finish(imgm_handle* h, cudaStream_t s) {
 }
 
 // Builds the solve graph: start -> while (!done) { iteration } -> finish.
-cudaError_t build_solve_graph(imgm_handle* h, cudaStream_t s) {
+// Captures start, conditional WHILE loop over one iteration, and finish into h->exec.
+// Capture runs on a stream of the handle (capturing the legacy default stream is not
+// allowed); the graph is then launched on the caller's stream.
+cudaError_t build_solve_graph(imgm_handle* h) {
+    cudaError_t e = cudaSuccess;
+    if (!h->capture && (e = cudaStreamCreateWithFlags(&h->capture, cudaStreamNonBlocking)) != cudaSuccess) return e;
+    cudaStream_t s = h->capture;
     cudaStream_t body_stream = nullptr;
-    cudaError_t e = cudaStreamCreateWithFlags(&body_stream, cudaStreamNonBlocking);
-    if (e != cudaSuccess) return e;
+    if ((e = cudaStreamCreateWithFlags(&body_stream, cudaStreamNonBlocking)) != cudaSuccess) return e;
     cudaGraph_t g = nullptr;
     do {
         if ((e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) break;
@@ -374,35 +383,38 @@ cudaError_t autotune_cluster(imgm_handle* h, imgm::VcycleCoarse& vc) {
         if (err == cudaSuccess) err = cudaEventElapsedTime(ms, e0, e1);
         return err;
     };
-    int best_top = -1;
-    float best = 0.0f;
-    h->vc_top = -1;
-    e = time_vcycles(&best);
-    for (int top = h->L - 2; top >= 0 && e == cudaSuccess; --top) {
+    // makes `top` the cluster launch's highest level (-1: separate launches only)
+    auto install = [&](int top) -> cudaError_t {
         int mb = 1;
         for (int li = 1; li <= top; ++li) mb = std::max(mb, (int)h->lv[li].fd.max_block);
-        vc.top = top;
-        vc.max_block = mb;
-        e = cudaMemcpy(h->vc, &vc, sizeof(vc), cudaMemcpyHostToDevice);
-        if (e != cudaSuccess) break;
         h->vc_top = top;
         h->vc_max_block = mb;
+        h->vc_smem = imgm::vcycle_cluster_smem(mb);
+        if (top < 0) return cudaSuccess;
+        vc.top = top;
+        vc.max_block = mb;
+        return cudaMemcpy(h->vc, &vc, sizeof(vc), cudaMemcpyHostToDevice);
+    };
+    const bool verbose = std::getenv("IMGM_VERBOSE") != nullptr;
+    int best_top = -1;
+    float best = 0.0f;
+    install(-1);
+    e = time_vcycles(&best);
+    if (verbose && e == cudaSuccess)
+        std::fprintf(stderr, "imgm: V-cycle, all levels as separate launches: %.2f us\n", best * 50.0f);
+    for (int top = h->L - 2; top >= 0 && e == cudaSuccess; --top) {
+        if ((e = install(top)) != cudaSuccess) break;
         float t = 0.0f;
         e = time_vcycles(&t);
+        if (verbose && e == cudaSuccess)
+            std::fprintf(stderr, "imgm: V-cycle, levels 1..%d in one cluster launch: %.2f us\n", top + 1, t * 50.0f);
         if (e == cudaSuccess && t < best) {
             best = t;
             best_top = top;
         }
     }
-    if (e == cudaSuccess && best_top >= 0) {
-        int mb = 1;
-        for (int li = 1; li <= best_top; ++li) mb = std::max(mb, (int)h->lv[li].fd.max_block);
-        vc.top = best_top;
-        vc.max_block = mb;
-        e = cudaMemcpy(h->vc, &vc, sizeof(vc), cudaMemcpyHostToDevice);
-        h->vc_max_block = mb;
-    }
-    h->vc_top = best_top;
+    const cudaError_t ei = install(e == cudaSuccess ? best_top : -1);
+    if (e == cudaSuccess) e = ei;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaStreamDestroy(s);
@@ -624,6 +636,7 @@ int imgm_setup(const imgm_geometry* geom, const imgm_config* cfg, imgm_handle** 
                 CK(cudaMemcpy(h->vc, &vc, sizeof(vc), cudaMemcpyHostToDevice), "upload cluster levels");
                 h->vc_top = vc.top;
                 h->vc_max_block = mb;
+                h->vc_smem = imgm::vcycle_cluster_smem(mb);
                 CK(autotune_cluster(h, vc), "cluster autotune");
             }
         }
@@ -767,9 +780,23 @@ int imgm_pcg_solve(imgm_handle* h, const double* dev_b, double* dev_x, double rt
     CK(cudaMemcpyAsync(h->cb, dev_b, N * sizeof(double), cudaMemcpyDeviceToDevice, s), "copy b");
     CK(cudaMemcpyAsync(h->cx, dev_x, N * sizeof(double), cudaMemcpyDeviceToDevice, s), "copy x0");
     if (!h->exec && !h->graph_failed) {
-        if (build_solve_graph(h, s) != cudaSuccess) {
+        cudaError_t ge = build_solve_graph(h);
+        if (ge != cudaSuccess) {
+            // capture without programmatic edges
+            cudaGetLastError();
+            if (std::getenv("IMGM_VERBOSE"))
+                std::fprintf(stderr, "imgm: solve graph with programmatic launches not built (%s)\n",
+                             cudaGetErrorString(ge));
+            imgm::set_programmatic_launch(false);
+            ge = build_solve_graph(h);
+            imgm::set_programmatic_launch(true);
+        }
+        if (ge == cudaSuccess && std::getenv("IMGM_VERBOSE")) std::fprintf(stderr, "imgm: solve graph built\n");
+        if (ge != cudaSuccess) {
             h->graph_failed = true;
             cudaGetLastError();
+            if (std::getenv("IMGM_VERBOSE"))
+                std::fprintf(stderr, "imgm: conditional solve graph not built (%s), host loop\n", cudaGetErrorString(ge));
         }
     }
     if (h->exec) {

@@ -26,6 +26,7 @@
 #include <cooperative_groups.h>
 
 #include <algorithm>
+#include <utility>
 
 namespace cg = cooperative_groups;
 
@@ -34,6 +35,28 @@ namespace {
 
 constexpr int TPB = 256;
 int g_red_blocks = 0;
+
+// Programmatic dependent launch: every kernel is launched with programmatic stream
+// serialisation allowed, so that the blocks of the next kernel in the stream (or graph)
+// are scheduled while this one drains instead of after a full launch round trip.  Each
+// kernel first waits until its predecessor has completed and its writes are visible
+// (griddepcontrol.wait returns at once when there is no programmatic predecessor), then
+// lets its own successor launch.
+__device__ __forceinline__ void pdl_begin() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// Read-only data (level tables, stored coefficients, block inverses, scales): never
+// written on the device after setup, so it may take the non-coherent cached path.
+// The row tables are read with plain loads.
+template <typename T>
+__device__ __forceinline__ T ro(const T* p) {
+    return __ldg(p);
+}
+__device__ __forceinline__ int64_t ro(const int64_t* p) {
+    return (int64_t)__ldg(reinterpret_cast<const long long*>(p));
+}
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -141,7 +164,7 @@ __device__ __forceinline__ T row_apply(const DevLevelT<T>& L, int64_t i, const T
                 for (int ox = -P; ox <= P; ++ox) {
                     if ((unsigned)(ix + ox) >= (unsigned)m) continue;
                     const int ci = (ox + P) + W * ((oy + P) + (DIM == 3 ? W * (oz + P) : 0));
-                    y = fmaT(c[(int64_t)ci * nb], x[i + ox + oy * sy + (DIM == 3 ? oz * sz : 0)], y);
+                    y = fmaT(ro(c + (int64_t)ci * nb), x[i + ox + oy * sy + (DIM == 3 ? oz * sz : 0)], y);
                 }
             }
         }
@@ -154,8 +177,8 @@ __device__ __forceinline__ T row_apply(const DevLevelT<T>& L, int64_t i, const T
     T kx[W], mx[W];
 #pragma unroll
     for (int ox = -P; ox <= P; ++ox) {
-        kx[ox + P] = Kx[ox];
-        mx[ox + P] = Mx[ox];
+        kx[ox + P] = ro(Kx + ox);
+        mx[ox + P] = ro(Mx + ox);
     }
     if (DIM == 2) {
 #pragma unroll
@@ -166,31 +189,31 @@ __device__ __forceinline__ T row_apply(const DevLevelT<T>& L, int64_t i, const T
 #pragma unroll
             for (int ox = -P; ox <= P; ++ox) {
                 if ((unsigned)(ix + ox) >= (unsigned)m) continue;
-                const T xv = sc ? x[rb + ox] * sc[rb + ox] : x[rb + ox];
+                const T xv = sc ? x[rb + ox] * ro(sc + rb + ox) : x[rb + ox];
                 a = fmaT(kx[ox + P], xv, a);
                 b = fmaT(mx[ox + P], xv, b);
             }
-            y = fmaT(My[oy], a, y);
-            y = fmaT(Ky[oy], b, y);
+            y = fmaT(ro(My + oy), a, y);
+            y = fmaT(ro(Ky + oy), b, y);
         }
-        return sc ? y * sc[i] : y;
+        return sc ? y * ro(sc + i) : y;
     }
     const T* __restrict__ Kz = L.K1 + (int64_t)iz * W + P;
     const T* __restrict__ Mz = L.M1 + (int64_t)iz * W + P;
 #pragma unroll
     for (int oz = -P; oz <= P; ++oz) {
         if ((unsigned)(iz + oz) >= (unsigned)m) continue;
-        const T mz = Mz[oz], kz = Kz[oz];
+        const T mz = ro(Mz + oz), kz = ro(Kz + oz);
 #pragma unroll
         for (int oy = -P; oy <= P; ++oy) {
             if ((unsigned)(iy + oy) >= (unsigned)m) continue;
-            const T my = My[oy], ky = Ky[oy];
+            const T my = ro(My + oy), ky = ro(Ky + oy);
             T a = T(0), b = T(0);
             const int64_t rb = i + oy * sy + oz * sz;
 #pragma unroll
             for (int ox = -P; ox <= P; ++ox) {
                 if ((unsigned)(ix + ox) >= (unsigned)m) continue;
-                const T xv = sc ? x[rb + ox] * sc[rb + ox] : x[rb + ox];
+                const T xv = sc ? x[rb + ox] * ro(sc + rb + ox) : x[rb + ox];
                 a = fmaT(kx[ox + P], xv, a);
                 b = fmaT(mx[ox + P], xv, b);
             }
@@ -199,7 +222,7 @@ __device__ __forceinline__ T row_apply(const DevLevelT<T>& L, int64_t i, const T
             y = fmaT(fmaT(ky, mz, my * kz), b, y);
         }
     }
-    return sc ? y * sc[i] : y;
+    return sc ? y * ro(sc + i) : y;
 }
 
 template <typename T, int DIM, int P>
@@ -212,7 +235,7 @@ __device__ __forceinline__ void apply_rows(const DevLevelT<T>& L, int mode, cons
         } else {
             const T v = (L.rowinfo[i] == -2) ? T(0) : rin[i] - ax;
             out[i] = v;
-            if (mode == RESID_SMOOTH) xs[i] = fmaT(gamma * L.dinv[i], v, xs[i]);
+            if (mode == RESID_SMOOTH) xs[i] = fmaT(gamma * ro(L.dinv + i), v, xs[i]);
         }
     }
 }
@@ -220,6 +243,7 @@ __device__ __forceinline__ void apply_rows(const DevLevelT<T>& L, int mode, cons
 template <typename T, int DIM, int P>
 __global__ void __launch_bounds__(TPB) k_apply(DevLevelT<T> L, int mode, const T* __restrict__ x, const T* rin,
                                                T* out, T* __restrict__ xs, T gamma, const int* done) {
+    pdl_begin();
     if (done && *done) return;
     apply_rows<T, DIM, P>(L, mode, x, rin, out, xs, gamma, (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
                           (int64_t)gridDim.x * blockDim.x);
@@ -240,6 +264,7 @@ template <typename T, int P, int MODE, bool DOT>
 __global__ void __launch_bounds__(TPB) k_apply_tile2d(DevLevelT<T> L, const T* __restrict__ x, const T* rin, T* out,
                                                       T* __restrict__ xs, T gamma, const int* done, double* partial,
                                                       PcgState* st) {
+    pdl_begin();
     constexpr int W = 2 * P + 1;
     constexpr int SX = TX + 2 * P, SY = TY + 2 * P;
     constexpr int OUT_PER_THREAD = (TX * TY) / TPB;
@@ -267,19 +292,19 @@ __global__ void __launch_bounds__(TPB) k_apply_tile2d(DevLevelT<T> L, const T* _
             const bool in = (unsigned)gx < (unsigned)m && (unsigned)gy < (unsigned)m;
             const int64_t g = (int64_t)gy * m + gx;
             sx[ly][lx] = in ? x[g] : T(0);
-            ss[ly][lx] = in ? (scaled ? L.s[g] : T(1)) : T(0);
+            ss[ly][lx] = in ? (scaled ? ro(L.s + g) : T(1)) : T(0);
         }
         for (int k = threadIdx.x; k < TY * W; k += TPB) {
             const int ly = k / W, o = k % W;
             const int gy = y0 + ly;
-            tMy[ly][o] = gy < m ? L.M1[(int64_t)gy * W + o] : T(0);
-            tKy[ly][o] = gy < m ? L.K1[(int64_t)gy * W + o] : T(0);
+            tMy[ly][o] = gy < m ? ro(L.M1 + (int64_t)gy * W + o) : T(0);
+            tKy[ly][o] = gy < m ? ro(L.K1 + (int64_t)gy * W + o) : T(0);
         }
         for (int k = threadIdx.x; k < TX * W; k += TPB) {
             const int lx = k / W, o = k % W;
             const int gx = x0 + lx;
-            tKx[lx][o] = gx < m ? L.K1[(int64_t)gx * W + o] : T(0);
-            tMx[lx][o] = gx < m ? L.M1[(int64_t)gx * W + o] : T(0);
+            tKx[lx][o] = gx < m ? ro(L.K1 + (int64_t)gx * W + o) : T(0);
+            tMx[lx][o] = gx < m ? ro(L.M1 + (int64_t)gx * W + o) : T(0);
         }
         int ri[OUT_PER_THREAD];
         T rv[OUT_PER_THREAD], dv[OUT_PER_THREAD], xv[OUT_PER_THREAD];
@@ -289,9 +314,9 @@ __global__ void __launch_bounds__(TPB) k_apply_tile2d(DevLevelT<T> L, const T* _
             const int gx = x0 + k % TX, gy = y0 + k / TX;
             const bool in = gx < m && gy < m;
             const int64_t i = (int64_t)gy * m + gx;
-            ri[q] = in ? L.rowinfo[i] : -3;
+            ri[q] = in ? ro(L.rowinfo + i) : -3;
             rv[q] = (MODE != APPLY && in) ? rin[i] : T(0);
-            dv[q] = (MODE == RESID_SMOOTH && in) ? L.dinv[i] : T(0);
+            dv[q] = (MODE == RESID_SMOOTH && in) ? ro(L.dinv + i) : T(0);
             xv[q] = (MODE == RESID_SMOOTH && in) ? xs[i] : T(0);
         }
         __syncthreads();
@@ -330,7 +355,7 @@ __global__ void __launch_bounds__(TPB) k_apply_tile2d(DevLevelT<T> L, const T* _
 #pragma unroll
                 for (int oy = 0; oy < W; ++oy)
 #pragma unroll
-                    for (int ox = 0; ox < W; ++ox) y = fmaT(c[(int64_t)(ox + W * oy) * nb], sx[ly + oy][lx + ox], y);
+                    for (int ox = 0; ox < W; ++ox) y = fmaT(ro(c + (int64_t)(ox + W * oy) * nb), sx[ly + oy][lx + ox], y);
             }
             if (MODE == APPLY) {
                 out[i] = y;
@@ -360,6 +385,7 @@ __global__ void __launch_bounds__(TPB) k_apply_tile2d(DevLevelT<T> L, const T* _
 template <int DIM, int P>
 __global__ void __launch_bounds__(TPB) k_apply_pq(DevLevel L, const double* __restrict__ p, double* __restrict__ q,
                                                   double* partial, PcgState* st) {
+    pdl_begin();
     if (st->done) return;
     double acc = 0.0;
     const int64_t stride = (int64_t)gridDim.x * TPB;
@@ -384,6 +410,7 @@ __global__ void __launch_bounds__(TPB) k_apply_pq(DevLevel L, const double* __re
 template <typename T>
 __global__ void __launch_bounds__(TPB) k_scale_diag(int64_t N, const T* __restrict__ dinv, const T* __restrict__ r,
                                                     T* __restrict__ x, T gamma, const int* done) {
+    pdl_begin();
     if (done && *done) return;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) x[i] = gamma * dinv[i] * r[i];
@@ -394,15 +421,15 @@ template <typename T>
 __device__ __forceinline__ void blocks_warps(const DevLevelT<T>& L, const T* __restrict__ r, T* x, T gamma,
                                              int64_t warp0, int64_t nwarps, int lane, T* rs) {
     for (int64_t b = warp0; b < L.nblk; b += nwarps) {
-        const int64_t s = L.blk_ptr[b];
-        const int nj = (int)(L.blk_ptr[b + 1] - s);
-        const T* __restrict__ A = L.blk_val + L.blk_vptr[b];
-        for (int a = lane; a < nj; a += 32) rs[a] = r[L.blk_idx[s + a]];
+        const int64_t s = ro(L.blk_ptr + b);
+        const int nj = (int)(ro(L.blk_ptr + b + 1) - s);
+        const T* __restrict__ A = L.blk_val + ro(L.blk_vptr + b);
+        for (int a = lane; a < nj; a += 32) rs[a] = r[ro(L.blk_idx + s + a)];
         __syncwarp();
         for (int a = lane; a < nj; a += 32) {
             T acc = T(0);
-            for (int c = 0; c < nj; ++c) acc = fmaT(A[(int64_t)c * nj + a], rs[c], acc);
-            atomicAdd(&x[L.blk_idx[s + a]], gamma * acc);
+            for (int c = 0; c < nj; ++c) acc = fmaT(ro(A + (int64_t)c * nj + a), rs[c], acc);
+            atomicAdd(&x[ro(L.blk_idx + s + a)], gamma * acc);
         }
         __syncwarp();
     }
@@ -411,6 +438,7 @@ __device__ __forceinline__ void blocks_warps(const DevLevelT<T>& L, const T* __r
 template <typename T>
 __global__ void __launch_bounds__(TPB) k_blocks(DevLevelT<T> L, const T* __restrict__ r, T* x, T gamma,
                                                 const int* done) {
+    pdl_begin();
     extern __shared__ __align__(16) unsigned char smraw[];
     T* sm = reinterpret_cast<T*>(smraw);
     if (done && *done) return;
@@ -433,33 +461,34 @@ __device__ __forceinline__ void restrict_rows(const DevLevelT<T>& F, const DevLe
             continue;
         }
         const int cx = (int)(i % mc), cy = (int)((i / mc) % mc), cz = (DIM == 3) ? (int)(i / ((int64_t)mc * mc)) : 0;
-        const int fx = F.r_first[cx], fy = F.r_first[cy], fz = (DIM == 3) ? F.r_first[cz] : 0;
+        const int fx = ro(F.r_first + cx), fy = ro(F.r_first + cy), fz = (DIM == 3) ? ro(F.r_first + cz) : 0;
         const T* wx = F.r_w + (int64_t)cx * P2;
         const T* wy = F.r_w + (int64_t)cy * P2;
         const T* wz = F.r_w + (int64_t)cz * P2;
         T s = T(0);
 #pragma unroll
         for (int kz = 0; kz < (DIM == 3 ? P2 : 1); ++kz) {
-            const T wzk = (DIM == 3) ? wz[kz] : T(1);
+            const T wzk = (DIM == 3) ? ro(wz + kz) : T(1);
 #pragma unroll
             for (int ky = 0; ky < P2; ++ky) {
-                const T wyz = wy[ky] * wzk;
+                const T wyz = ro(wy + ky) * wzk;
                 const int64_t rb = (int64_t)(fx) + (int64_t)mf * ((fy + ky) + (DIM == 3 ? (int64_t)mf * (fz + kz) : 0));
                 T t = T(0);
 #pragma unroll
-                for (int kx = 0; kx < P2; ++kx) t = fmaT(wx[kx], df ? rf[rb + kx] * df[rb + kx] : rf[rb + kx], t);
+                for (int kx = 0; kx < P2; ++kx) t = fmaT(ro(wx + kx), df ? rf[rb + kx] * ro(df + rb + kx) : rf[rb + kx], t);
                 s = fmaT(wyz, t, s);
             }
         }
-        if (C.s) s *= C.s[i];
+        if (C.s) s *= ro(C.s + i);
         rc[i] = s;
-        if (xc) xc[i] = gamma * C.dinv[i] * s;
+        if (xc) xc[i] = gamma * ro(C.dinv + i) * s;
     }
 }
 
 template <typename T, int DIM, int P>
 __global__ void __launch_bounds__(TPB) k_restrict(DevLevelT<T> F, DevLevelT<T> C, const T* __restrict__ rf,
                                                   T* __restrict__ rc, T* __restrict__ xc, T gamma, const int* done) {
+    pdl_begin();
     if (done && *done) return;
     restrict_rows<T, DIM, P>(F, C, rf, rc, xc, gamma, (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
                              (int64_t)gridDim.x * blockDim.x);
@@ -476,22 +505,22 @@ __device__ __forceinline__ void prolong_rows(const DevLevelT<T>& F, const DevLev
             continue;
         }
         const int ax = (int)(a % mf), ay = (int)((a / mf) % mf), az = (DIM == 3) ? (int)(a / ((int64_t)mf * mf)) : 0;
-        const int cx = F.t_first[ax], cy = F.t_first[ay], cz = (DIM == 3) ? F.t_first[az] : 0;
+        const int cx = ro(F.t_first + ax), cy = ro(F.t_first + ay), cz = (DIM == 3) ? ro(F.t_first + az) : 0;
         const T* wx = F.t_w + (int64_t)ax * TW;
         const T* wy = F.t_w + (int64_t)ay * TW;
         const T* wz = F.t_w + (int64_t)az * TW;
         T s = T(0);
         for (int tz = 0; tz < (DIM == 3 ? TW : 1); ++tz) {
-            const T wzk = (DIM == 3) ? wz[tz] : T(1);
+            const T wzk = (DIM == 3) ? ro(wz + tz) : T(1);
             for (int ty = 0; ty < TW; ++ty) {
-                const T wyz = wy[ty] * wzk;
+                const T wyz = ro(wy + ty) * wzk;
                 const int64_t rb = (int64_t)cx + (int64_t)mc * ((cy + ty) + (DIM == 3 ? (int64_t)mc * (cz + tz) : 0));
                 T t = T(0);
-                for (int tx = 0; tx < TW; ++tx) t = fmaT(wx[tx], sc ? xc[rb + tx] * sc[rb + tx] : xc[rb + tx], t);
+                for (int tx = 0; tx < TW; ++tx) t = fmaT(ro(wx + tx), sc ? xc[rb + tx] * ro(sc + rb + tx) : xc[rb + tx], t);
                 s = fmaT(wyz, t, s);
             }
         }
-        if (F.d) s *= F.d[a];
+        if (F.d) s *= ro(F.d + a);
         e[a] = s;
         if (x) x[a] += s;
     }
@@ -500,6 +529,7 @@ __device__ __forceinline__ void prolong_rows(const DevLevelT<T>& F, const DevLev
 template <typename T, int DIM, int P>
 __global__ void __launch_bounds__(TPB) k_prolong(DevLevelT<T> F, DevLevelT<T> C, const T* __restrict__ xc,
                                                  T* __restrict__ e, T* __restrict__ x, const int* done) {
+    pdl_begin();
     if (done && *done) return;
     prolong_rows<T, DIM, P>(F, C, xc, e, x, (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
                             (int64_t)gridDim.x * blockDim.x);
@@ -513,15 +543,16 @@ __device__ __forceinline__ void coarse_warps(const int32_t* __restrict__ rows, c
     for (int64_t a = warp0; a < nc; a += nwarps) {
         const T* row = Cinv + a * nc;
         double acc = 0.0;
-        for (int b = lane; b < nc; b += 32) acc = fma((double)row[b], (double)r[rows[b]], acc);
+        for (int b = lane; b < nc; b += 32) acc = fma((double)ro(row + b), (double)r[ro(rows + b)], acc);
         acc = warp_sum(acc);
-        if (lane == 0) x[rows[a]] = (T)acc;
+        if (lane == 0) x[ro(rows + a)] = (T)acc;
     }
 }
 
 template <typename T>
 __global__ void __launch_bounds__(TPB) k_coarse(const int32_t* __restrict__ rows, const T* __restrict__ Cinv, int nc,
                                                 const T* __restrict__ r, T* __restrict__ x, const int* done) {
+    pdl_begin();
     if (done && *done) return;
     coarse_warps<T>(rows, Cinv, nc, r, x, ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5,
                     ((int64_t)gridDim.x * blockDim.x) >> 5, threadIdx.x & 31);
@@ -537,6 +568,7 @@ constexpr int CLUSTER_TPB = 1024;
 
 template <int DIM, int P>
 __global__ void __launch_bounds__(CLUSTER_TPB) k_vcycle_cluster(const VcycleCoarse* __restrict__ Vg, const int* done) {
+    pdl_begin();
     extern __shared__ __align__(16) unsigned char smraw[];
     __shared__ VcycleCoarse Vs;  // the level table in shared memory: field reads stay on chip
     float* sm = reinterpret_cast<float*>(smraw);
@@ -578,6 +610,7 @@ __global__ void __launch_bounds__(CLUSTER_TPB) k_vcycle_cluster(const VcycleCoar
 template <typename TI, typename TO>
 __global__ void __launch_bounds__(TPB) k_convert(int64_t N, const TI* __restrict__ in, TO* __restrict__ out,
                                                  const int* done) {
+    pdl_begin();
     if (done && *done) return;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) out[i] = (TO)in[i];
@@ -588,6 +621,7 @@ template <typename TZ>
 __global__ void __launch_bounds__(TPB) k_vcycle_in(int64_t N, const double* __restrict__ r, const TZ* __restrict__ rs,
                                                    const TZ* __restrict__ dinv, TZ gamma, TZ* __restrict__ rlo,
                                                    TZ* __restrict__ xv, const int* done) {
+    pdl_begin();
     if (done && *done) return;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
@@ -601,6 +635,7 @@ __global__ void __launch_bounds__(TPB) k_vcycle_in(int64_t N, const double* __re
 template <typename TZ>
 __global__ void __launch_bounds__(TPB) k_vcycle_out(int64_t N, const TZ* __restrict__ z, const TZ* __restrict__ zs,
                                                     double* __restrict__ out) {
+    pdl_begin();
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride)
         out[i] = zs ? (double)z[i] * (double)zs[i] : (double)z[i];
@@ -618,6 +653,7 @@ __global__ void __launch_bounds__(TPB) k_pcg_update(int64_t N, const TZ* __restr
                                                     const double* __restrict__ p, const double* __restrict__ q,
                                                     TZ* __restrict__ xv, TZ* __restrict__ rlo, double gamma,
                                                     double* partial, PcgState* st, double* hist) {
+    pdl_begin();
     if (st->done) return;
     const double alpha = st->alpha;
     double acc = 0.0;
@@ -655,6 +691,7 @@ template <typename TZ>
 __global__ void __launch_bounds__(TPB) k_pcg_rz(int64_t N, const double* __restrict__ r, const TZ* __restrict__ z,
                                                 const TZ* __restrict__ zs, const TZ* __restrict__ zprev,
                                                 double* partial, PcgState* st) {
+    pdl_begin();
     if (st->done) return;
     double acc = 0.0, accp = 0.0;
     const int64_t stride = (int64_t)gridDim.x * TPB;
@@ -677,6 +714,7 @@ __global__ void __launch_bounds__(TPB) k_pcg_rz(int64_t N, const double* __restr
 template <typename TZ>
 __global__ void __launch_bounds__(TPB) k_pcg_xpay(int64_t N, const TZ* __restrict__ z, const TZ* __restrict__ zs,
                                                   double* __restrict__ p, TZ* __restrict__ zprev, PcgState* st) {
+    pdl_begin();
     if (st->done) return;
     const double beta = st->beta;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -688,6 +726,7 @@ __global__ void __launch_bounds__(TPB) k_pcg_xpay(int64_t N, const TZ* __restric
 
 __global__ void __launch_bounds__(TPB) k_init_norms(int64_t N, const double* __restrict__ r, const double* __restrict__ b,
                                                     double* partial, PcgState* st, double* hist) {
+    pdl_begin();
     double a = 0.0, c = 0.0;
     const int64_t stride = (int64_t)gridDim.x * TPB;
     for (int64_t i = (int64_t)blockIdx.x * TPB + threadIdx.x; i < N; i += stride) {
@@ -719,6 +758,7 @@ template <typename TZ>
 __global__ void __launch_bounds__(TPB) k_init_dir(int64_t N, const double* __restrict__ r, const TZ* __restrict__ z,
                                                   const TZ* __restrict__ zs, double* __restrict__ p,
                                                   TZ* __restrict__ zprev, double* partial, PcgState* st) {
+    pdl_begin();
     if (st->done) return;
     double acc = 0.0;
     const int64_t stride = (int64_t)gridDim.x * TPB;
@@ -739,6 +779,7 @@ __global__ void __launch_bounds__(TPB) k_init_dir(int64_t N, const double* __res
 }
 
 __global__ void __launch_bounds__(TPB) k_norm2(int64_t N, const double* __restrict__ v, double* partial, PcgState* st) {
+    pdl_begin();
     double acc = 0.0;
     const int64_t stride = (int64_t)gridDim.x * TPB;
     for (int64_t i = (int64_t)blockIdx.x * TPB + threadIdx.x; i < N; i += stride) acc = fma(v[i], v[i], acc);
@@ -747,7 +788,50 @@ __global__ void __launch_bounds__(TPB) k_norm2(int64_t N, const double* __restri
 }
 
 __global__ void k_set_continue(PcgState* st, cudaGraphConditionalHandle handle) {
+    pdl_begin();
     cudaGraphSetConditional(handle, st->done ? 0u : 1u);
+}
+
+thread_local bool t_pdl = true;
+
+// Whether the next launch on s may carry the programmatic-serialisation attribute: always
+// outside stream capture; under capture only when every node it will depend on is a
+// kernel node (a programmatic edge joins two kernels).
+bool pdl_allowed(cudaStream_t s) {
+    if (!t_pdl) return false;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t nd = 0;
+    if (cudaStreamGetCaptureInfo(s, &cs, nullptr, nullptr, &deps, nullptr, &nd) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    if (cs != cudaStreamCaptureStatusActive) return true;
+    for (size_t k = 0; k < nd; ++k) {
+        cudaGraphNodeType t;
+        if (cudaGraphNodeGetType(deps[k], &t) != cudaSuccess || t != cudaGraphNodeTypeKernel) {
+            cudaGetLastError();
+            return false;
+        }
+    }
+    return true;
+}
+
+// Every kernel goes through here: programmatic stream serialisation lets the kernel
+// launch while its predecessor drains (each kernel starts with pdl_begin()).
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl_allowed(s) ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
 }
 
 int num_sms() {
@@ -786,15 +870,17 @@ cudaError_t launch_tile2d(const DevLevelT<T>& L, int mode, const T* x, const T* 
                           const int* done, cudaStream_t s) {
     const int g = tiles_2d(L.m);
     if (mode == APPLY)
-        k_apply_tile2d<T, P, APPLY, false><<<g, TPB, 0, s>>>(L, x, rin, out, xs, gamma, done, nullptr, nullptr);
+        launch_pdl(k_apply_tile2d<T, P, APPLY, false>, g, TPB, 0, s, L, x, rin, out, xs, gamma, done, nullptr, nullptr);
     else if (mode == RESID)
-        k_apply_tile2d<T, P, RESID, false><<<g, TPB, 0, s>>>(L, x, rin, out, xs, gamma, done, nullptr, nullptr);
+        launch_pdl(k_apply_tile2d<T, P, RESID, false>, g, TPB, 0, s, L, x, rin, out, xs, gamma, done, nullptr, nullptr);
     else
-        k_apply_tile2d<T, P, RESID_SMOOTH, false><<<g, TPB, 0, s>>>(L, x, rin, out, xs, gamma, done, nullptr, nullptr);
+        launch_pdl(k_apply_tile2d<T, P, RESID_SMOOTH, false>, g, TPB, 0, s, L, x, rin, out, xs, gamma, done, nullptr, nullptr);
     return cudaGetLastError();
 }
 
 }  // namespace
+
+void set_programmatic_launch(bool on) { t_pdl = on; }
 
 int reduction_blocks() {
     if (g_red_blocks == 0) g_red_blocks = num_sms() * 4;
@@ -823,7 +909,7 @@ cudaError_t launch_apply(const DevLevelT<T>& L, int mode, const T* x, const T* r
     }
     const RowLaunch rl = row_launch(L.N);
     IMGM_DISPATCH(L.dim, L.p,
-                  (k_apply<T, D, Q><<<rl.grid, rl.block, 0, s>>>(L, mode, x, rin, out, xs, (T)gamma, done)));
+                  (launch_pdl(k_apply<T, D, Q>, rl.grid, rl.block, 0, s, L, mode, x, rin, out, xs, (T)gamma, done)));
     return cudaGetLastError();
 }
 
@@ -832,23 +918,23 @@ cudaError_t launch_apply_pq(const DevLevel& L, const double* p, double* q, doubl
     if (L.dim == 2) {
         const int g = std::min(tiles_2d(L.m), reduction_blocks());
         if (L.p == 1)
-            k_apply_tile2d<double, 1, APPLY, true><<<g, TPB, 0, s>>>(L, p, nullptr, q, nullptr, 0.0, &st->done, partial, st);
+            launch_pdl(k_apply_tile2d<double, 1, APPLY, true>, g, TPB, 0, s, L, p, nullptr, q, nullptr, 0.0, &st->done, partial, st);
         else if (L.p == 2)
-            k_apply_tile2d<double, 2, APPLY, true><<<g, TPB, 0, s>>>(L, p, nullptr, q, nullptr, 0.0, &st->done, partial, st);
+            launch_pdl(k_apply_tile2d<double, 2, APPLY, true>, g, TPB, 0, s, L, p, nullptr, q, nullptr, 0.0, &st->done, partial, st);
         else if (L.p == 3)
-            k_apply_tile2d<double, 3, APPLY, true><<<g, TPB, 0, s>>>(L, p, nullptr, q, nullptr, 0.0, &st->done, partial, st);
+            launch_pdl(k_apply_tile2d<double, 3, APPLY, true>, g, TPB, 0, s, L, p, nullptr, q, nullptr, 0.0, &st->done, partial, st);
         else
             return cudaErrorInvalidValue;
         return cudaGetLastError();
     }
-    IMGM_DISPATCH(L.dim, L.p, (k_apply_pq<D, Q><<<reduction_blocks(), TPB, 0, s>>>(L, p, q, partial, st)));
+    IMGM_DISPATCH(L.dim, L.p, (launch_pdl(k_apply_pq<D, Q>, reduction_blocks(), TPB, 0, s, L, p, q, partial, st)));
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_scale_diag(const DevLevelT<T>& L, const T* r, T* x, double gamma, const int* done, cudaStream_t s) {
     const RowLaunch rl = row_launch(L.N);
-    k_scale_diag<T><<<rl.grid, rl.block, 0, s>>>(L.N, L.dinv, r, x, (T)gamma, done);
+    launch_pdl(k_scale_diag<T>, rl.grid, rl.block, 0, s, L.N, L.dinv, r, x, (T)gamma, done);
     return cudaGetLastError();
 }
 
@@ -859,7 +945,7 @@ cudaError_t launch_blocks(const DevLevelT<T>& L, const T* r, T* x, double gamma,
     int64_t g = (L.nblk + warps - 1) / warps;
     if (g > 65535) g = 65535;
     size_t smem = (size_t)warps * L.max_block * sizeof(T);
-    k_blocks<T><<<(int)g, 32 * warps, smem, s>>>(L, r, x, (T)gamma, done);
+    launch_pdl(k_blocks<T>, (int)g, 32 * warps, smem, s, L, r, x, (T)gamma, done);
     return cudaGetLastError();
 }
 
@@ -867,7 +953,7 @@ template <typename T>
 cudaError_t launch_restrict(const DevLevelT<T>& F, const DevLevelT<T>& C, const T* rf, T* rc, T* xc, double gamma,
                             const int* done, cudaStream_t s) {
     const RowLaunch rl = row_launch(C.N);
-    IMGM_DISPATCH(F.dim, F.p, (k_restrict<T, D, Q><<<rl.grid, rl.block, 0, s>>>(F, C, rf, rc, xc, (T)gamma, done)));
+    IMGM_DISPATCH(F.dim, F.p, (launch_pdl(k_restrict<T, D, Q>, rl.grid, rl.block, 0, s, F, C, rf, rc, xc, (T)gamma, done)));
     return cudaGetLastError();
 }
 
@@ -875,7 +961,7 @@ template <typename T>
 cudaError_t launch_prolong(const DevLevelT<T>& F, const DevLevelT<T>& C, const T* xc, T* e, T* x, const int* done,
                            cudaStream_t s) {
     const RowLaunch rl = row_launch(F.N);
-    IMGM_DISPATCH(F.dim, F.p, (k_prolong<T, D, Q><<<rl.grid, rl.block, 0, s>>>(F, C, xc, e, x, done)));
+    IMGM_DISPATCH(F.dim, F.p, (launch_pdl(k_prolong<T, D, Q>, rl.grid, rl.block, 0, s, F, C, xc, e, x, done)));
     return cudaGetLastError();
 }
 
@@ -884,7 +970,7 @@ cudaError_t launch_coarse(const int32_t* rows, const T* Cinv, int nc, const T* r
                           cudaStream_t s) {
     if (nc == 0) return cudaSuccess;
     const int warps = 2;
-    k_coarse<T><<<(nc + warps - 1) / warps, 32 * warps, 0, s>>>(rows, Cinv, nc, r, x, done);
+    launch_pdl(k_coarse<T>, (nc + warps - 1) / warps, 32 * warps, 0, s, rows, Cinv, nc, r, x, done);
     return cudaGetLastError();
 }
 
@@ -892,12 +978,15 @@ int vcycle_cluster_size() {
     static int cs = -1;
     if (cs < 0) {
         cs = 0;
+        // cluster sizes above 8 are opt-in per kernel; set here, outside any stream capture
+        for (auto k : {k_vcycle_cluster<2, 1>, k_vcycle_cluster<2, 2>, k_vcycle_cluster<2, 3>, k_vcycle_cluster<3, 1>,
+                       k_vcycle_cluster<3, 2>, k_vcycle_cluster<3, 3>})
+            if (cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) cudaGetLastError();
         auto kern = k_vcycle_cluster<2, 2>;
-        if (cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) cudaGetLastError();
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(16, 1, 1);
         cfg.blockDim = dim3(CLUSTER_TPB, 1, 1);
-        cfg.dynamicSmemBytes = 32 * 64 * sizeof(float);
+        cfg.dynamicSmemBytes = VCYCLE_SMEM_MAX;
         cudaLaunchAttribute attr;
         attr.id = cudaLaunchAttributeClusterDimension;
         attr.val.clusterDim.x = 16;
@@ -912,27 +1001,30 @@ int vcycle_cluster_size() {
     return cs;
 }
 
-cudaError_t launch_vcycle_cluster(int dim, int p, const VcycleCoarse* V, int max_block, const int* done,
+size_t vcycle_cluster_smem(int max_block) { return (size_t)(CLUSTER_TPB / 32) * max_block * sizeof(float); }
+
+cudaError_t launch_vcycle_cluster(int dim, int p, const VcycleCoarse* V, size_t smem, const int* done,
                                   cudaStream_t s) {
     const int cs = vcycle_cluster_size();
     if (cs <= 0) return cudaErrorNotSupported;
+    if (smem > VCYCLE_SMEM_MAX) return cudaErrorInvalidValue;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(cs, 1, 1);
     cfg.blockDim = dim3(CLUSTER_TPB, 1, 1);
-    cfg.dynamicSmemBytes = (size_t)(CLUSTER_TPB / 32) * max_block * sizeof(float);
+    cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
-    cudaLaunchAttribute attr;
-    attr.id = cudaLaunchAttributeClusterDimension;
-    attr.val.clusterDim.x = cs;
-    attr.val.clusterDim.y = 1;
-    attr.val.clusterDim.z = 1;
-    cfg.attrs = &attr;
-    cfg.numAttrs = 1;
+    cudaLaunchAttribute attr[2];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cs;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[1].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl_allowed(s) ? 2 : 1;
 #define IMGM_CLUSTER_CASE(D_, P_)                                                                                 \
     if (dim == D_ && p == P_) {                                                                                   \
-        auto kern = k_vcycle_cluster<D_, P_>;                                                                     \
-        if (cs > 8) cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);                \
-        return cudaLaunchKernelEx(&cfg, kern, V, done);                                                           \
+        return cudaLaunchKernelEx(&cfg, k_vcycle_cluster<D_, P_>, V, done);                                      \
     }
     IMGM_CLUSTER_CASE(2, 1)
     IMGM_CLUSTER_CASE(2, 2)
@@ -947,7 +1039,7 @@ cudaError_t launch_vcycle_cluster(int dim, int p, const VcycleCoarse* V, int max
 template <typename TI, typename TO>
 cudaError_t launch_convert(int64_t N, const TI* in, TO* out, const int* done, cudaStream_t s) {
     const RowLaunch rl = row_launch(N);
-    k_convert<TI, TO><<<rl.grid, rl.block, 0, s>>>(N, in, out, done);
+    launch_pdl(k_convert<TI, TO>, rl.grid, rl.block, 0, s, N, in, out, done);
     return cudaGetLastError();
 }
 
@@ -955,14 +1047,14 @@ template <typename TZ>
 cudaError_t launch_vcycle_in(int64_t N, const double* r, const TZ* rs, const TZ* dinv, double gamma, TZ* r_lo, TZ* xv,
                              const int* done, cudaStream_t s) {
     const RowLaunch rl = row_launch(N);
-    k_vcycle_in<TZ><<<rl.grid, rl.block, 0, s>>>(N, r, rs, dinv, (TZ)gamma, r_lo, xv, done);
+    launch_pdl(k_vcycle_in<TZ>, rl.grid, rl.block, 0, s, N, r, rs, dinv, (TZ)gamma, r_lo, xv, done);
     return cudaGetLastError();
 }
 
 template <typename TZ>
 cudaError_t launch_vcycle_out(int64_t N, const TZ* z, const TZ* zs, double* out, cudaStream_t s) {
     const RowLaunch rl = row_launch(N);
-    k_vcycle_out<TZ><<<rl.grid, rl.block, 0, s>>>(N, z, zs, out);
+    launch_pdl(k_vcycle_out<TZ>, rl.grid, rl.block, 0, s, N, z, zs, out);
     return cudaGetLastError();
 }
 
@@ -970,14 +1062,14 @@ template <typename TZ>
 cudaError_t launch_pcg_update(const DevLevel& L, const TZ* dinv_z, double* x, double* r, const double* p,
                               const double* q, TZ* xv, TZ* r_lo, const TZ* rs, double gamma, double* partial,
                               PcgState* st, double* hist, cudaStream_t s) {
-    k_pcg_update<TZ><<<reduction_blocks(), TPB, 0, s>>>(L.N, dinv_z, rs, x, r, p, q, xv, r_lo, gamma, partial, st, hist);
+    launch_pdl(k_pcg_update<TZ>, reduction_blocks(), TPB, 0, s, L.N, dinv_z, rs, x, r, p, q, xv, r_lo, gamma, partial, st, hist);
     return cudaGetLastError();
 }
 
 template <typename TZ>
 cudaError_t launch_pcg_rz(int64_t N, const double* r, const TZ* z, const TZ* zs, const TZ* zprev, double* partial,
                           PcgState* st, cudaStream_t s) {
-    k_pcg_rz<TZ><<<reduction_blocks(), TPB, 0, s>>>(N, r, z, zs, zprev, partial, st);
+    launch_pdl(k_pcg_rz<TZ>, reduction_blocks(), TPB, 0, s, N, r, z, zs, zprev, partial, st);
     return cudaGetLastError();
 }
 
@@ -985,30 +1077,30 @@ template <typename TZ>
 cudaError_t launch_pcg_xpay(int64_t N, const TZ* z, const TZ* zs, double* p, TZ* zprev, PcgState* st,
                             cudaStream_t s) {
     const RowLaunch rl = row_launch(N);
-    k_pcg_xpay<TZ><<<rl.grid, rl.block, 0, s>>>(N, z, zs, p, zprev, st);
+    launch_pdl(k_pcg_xpay<TZ>, rl.grid, rl.block, 0, s, N, z, zs, p, zprev, st);
     return cudaGetLastError();
 }
 
 cudaError_t launch_pcg_init_norms(int64_t N, const double* r, const double* b, double* partial, PcgState* st,
                                   double* hist, cudaStream_t s) {
-    k_init_norms<<<reduction_blocks(), TPB, 0, s>>>(N, r, b, partial, st, hist);
+    launch_pdl(k_init_norms, reduction_blocks(), TPB, 0, s, N, r, b, partial, st, hist);
     return cudaGetLastError();
 }
 
 template <typename TZ>
 cudaError_t launch_pcg_init_dir(int64_t N, const double* r, const TZ* z, const TZ* zs, double* p, TZ* zprev,
                                 double* partial, PcgState* st, cudaStream_t s) {
-    k_init_dir<TZ><<<reduction_blocks(), TPB, 0, s>>>(N, r, z, zs, p, zprev, partial, st);
+    launch_pdl(k_init_dir<TZ>, reduction_blocks(), TPB, 0, s, N, r, z, zs, p, zprev, partial, st);
     return cudaGetLastError();
 }
 
 cudaError_t launch_true_residual_norm(int64_t N, const double* v, double* partial, PcgState* st, cudaStream_t s) {
-    k_norm2<<<reduction_blocks(), TPB, 0, s>>>(N, v, partial, st);
+    launch_pdl(k_norm2, reduction_blocks(), TPB, 0, s, N, v, partial, st);
     return cudaGetLastError();
 }
 
 cudaError_t launch_set_continue(PcgState* st, unsigned long long handle, cudaStream_t s) {
-    k_set_continue<<<1, 1, 0, s>>>(st, (cudaGraphConditionalHandle)handle);
+    launch_pdl(k_set_continue, 1, 1, 0, s, st, (cudaGraphConditionalHandle)handle);
     return cudaGetLastError();
 }
 

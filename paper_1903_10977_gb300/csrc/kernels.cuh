@@ -130,6 +130,7 @@ cudaError_t launch_set_continue(PcgState* st, unsigned long long handle, cudaStr
 // thread-block-cluster launch.  V lives in device memory (a multiple of 4 bytes; the
 // kernel copies it to shared memory).
 constexpr int VCYCLE_MAX_LEVELS = 16;
+constexpr size_t VCYCLE_SMEM_MAX = 48 * 1024;       // dynamic shared memory per block, at most
 struct VcycleCoarse {
     DevLevelT<float> lv[VCYCLE_MAX_LEVELS];
     float* x[VCYCLE_MAX_LEVELS];
@@ -145,9 +146,13 @@ struct VcycleCoarse {
 };
 // cluster size the device supports for it (0: none)
 int vcycle_cluster_size();
-cudaError_t launch_vcycle_cluster(int dim, int p, const VcycleCoarse* V, int max_block, const int* done,
+// dynamic shared memory of the launch (the block-inverse scratch of its warps)
+size_t vcycle_cluster_smem(int max_block);
+cudaError_t launch_vcycle_cluster(int dim, int p, const VcycleCoarse* V, size_t smem, const int* done,
                                   cudaStream_t s);
 
 int reduction_blocks();   // fixed number of blocks of every reducing kernel
+// programmatic dependent launch of the kernels issued by this host thread (default on)
+void set_programmatic_launch(bool on);
 
 }  // namespace imgm
