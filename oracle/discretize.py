@@ -263,29 +263,33 @@ class Discretization:
         self.b = bfull[act]
 
     def assemble_rows(self, rows_full: np.ndarray):
-        """Rows of A (in full-grid column indexing) assembled from the elements in their supports.
+        """Rows of A (in full-grid column indexing) and entries of b, assembled from the
+        elements in their supports.
 
         Used where the whole matrix is too large for this oracle: returns a dict
-        row -> (cols, vals) for the requested full-grid rows.
+        row -> (cols, vals, b_row) for the requested full-grid rows.
         """
         out = {}
         cache = {}
         for I in rows_full:
             I = int(I)
             acc: dict[int, float] = {}
+            bI = 0.0
             if self.func_active_full[I]:
                 for E in self.tb.support_elems(I):
                     if not self.elem_active[E]:
                         continue
                     if E not in cache:
-                        cache[E] = self.element_system(E)[0]
+                        cache[E] = self.element_system(E)[:2]
+                    AK, bK = cache[E]
                     dofs = self.tb.elem_dofs(E)
                     a = int(np.flatnonzero(dofs == I)[0])
+                    bI += bK[a]
                     for bi, J in enumerate(dofs):
                         if self.func_active_full[J]:
-                            acc[int(J)] = acc.get(int(J), 0.0) + cache[E][a, bi]
+                            acc[int(J)] = acc.get(int(J), 0.0) + AK[a, bi]
             cols = np.array(sorted(acc), dtype=np.int64)
-            out[I] = (cols, np.array([acc[j] for j in cols]))
+            out[I] = (cols, np.array([acc[j] for j in cols]), bI)
         return out
 
     # ------------------------------------------------------------------ helpers

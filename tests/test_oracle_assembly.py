@@ -154,3 +154,27 @@ def test_nitsche_beta_closed_form_1d_like():
     B = np.array([[1.0, -1.0], [-1.0, 1.0]]) * 5.0
     assert nitsche_beta(S, B, 1.0) == 4.0          # lambda = 5/3 -> 2 lambda = 3.33 -> 4
     assert nitsche_beta(S, B, 1e-3) == 2048.0      # floor 1/h = 1000 -> 2000 -> 2048
+
+
+def test_row_assembly_matches_global_assembly():
+    """Rows of A and entries of b assembled one by one from the element systems of the
+    support elements (the path the full-size parity tests take) equal the globally
+    assembled system (batched tensor rule on full elements)."""
+    from parity_utils import oracle_for
+    pr, lay, d, H = oracle_for("disc1_32_p2")
+    rng = np.random.default_rng(3)
+    rows = np.unique(np.concatenate([rng.choice(d.active, 60, replace=False),
+                                     [int(J) for E in d.cut_elems[:20] for J in d.tb.elem_dofs(int(E))
+                                      if d.func_active_full[J]]]))
+    got = d.assemble_rows(rows)
+    pos = -np.ones(d.tb.n_funcs, dtype=np.int64)
+    pos[d.active] = np.arange(d.n_active)
+    Ad = d.A.tocsr()
+    for I in rows:
+        cols, vals, bI = got[int(I)]
+        ref = Ad[pos[I]].toarray().ravel()
+        row = np.zeros(d.n_active)
+        row[pos[cols]] = vals
+        scale = np.abs(ref).max()
+        assert np.abs(row - ref).max() <= 1e-13 * scale
+        assert abs(bI - d.b[pos[I]]) <= 1e-13 * np.abs(d.b).max()
