@@ -46,7 +46,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         jobs.append(common_nv + ["-c", os.path.join(CSRC, f), "-o", o])
     o = os.path.join(tmp, "setup.o")
     objs.append(o)
-    jobs.append([cxx, "-O2", "-std=c++17", "-fPIC", "-fopenmp", "-I", INCLUDE, "-c",
+    jobs.append([cxx, "-O3", "-std=c++17", "-fPIC", "-fopenmp", "-I", INCLUDE, "-c",
                  os.path.join(CSRC, "setup.cpp"), "-o", o])
     procs = [subprocess.Popen(j, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True) for j in jobs]
     errors = []

@@ -10,6 +10,8 @@
 #include <algorithm>
 #include <array>
 #include <chrono>
+#include <cstdio>
+#include <cstdlib>
 #include <cmath>
 #include <cstring>
 #include <numeric>
@@ -682,6 +684,33 @@ struct CutElem {
     std::vector<double> b;   // nloc
 };
 
+// S (upper triangle) += w sum_j g_j g_j^T for the nloc-vectors g_j = grad + j nloc;
+// NL > 0 fixes nloc at compile time so that the inner loop is unrolled and vectorised
+template <int NL>
+void add_grad_outer(double* S, const double* grad, int dim, int nloc_rt, double w) {
+    const int nloc = NL > 0 ? NL : nloc_rt;
+    for (int j = 0; j < dim; ++j) {
+        const double* gj = grad + (size_t)j * nloc;
+        for (int a = 0; a < nloc; ++a) {
+            const double t = w * gj[a];
+            double* Sa = S + (size_t)a * nloc;
+            for (int c = a; c < nloc; ++c) Sa[c] += t * gj[c];
+        }
+    }
+}
+
+void add_grad_outer_any(double* S, const double* grad, int dim, int nloc, double w) {
+    switch (nloc) {
+        case 4: add_grad_outer<4>(S, grad, dim, nloc, w); break;
+        case 8: add_grad_outer<8>(S, grad, dim, nloc, w); break;
+        case 9: add_grad_outer<9>(S, grad, dim, nloc, w); break;
+        case 16: add_grad_outer<16>(S, grad, dim, nloc, w); break;
+        case 27: add_grad_outer<27>(S, grad, dim, nloc, w); break;
+        case 64: add_grad_outer<64>(S, grad, dim, nloc, w); break;
+        default: add_grad_outer<0>(S, grad, dim, nloc, w); break;
+    }
+}
+
 void cut_element_system(const Geometry& G, const Basis1D& B, int dim, int p, int depth, int bc, const int* e,
                         const double* lo, const double* hi, CutElem& out) {
     const int nloc = (dim == 2) ? (p + 1) * (p + 1) : (p + 1) * (p + 1) * (p + 1);
@@ -691,21 +720,19 @@ void cut_element_system(const Geometry& G, const Basis1D& B, int dim, int p, int
     std::vector<double> val(nloc), grad((size_t)dim * nloc);
     double vol = 0.0;
     const size_t nv = R.vw.size();
+    // S = sum_q w_q sum_j grad_j(q) grad_j(q)^T, upper triangle accumulated with the
+    // contiguous index innermost, then mirrored
     for (size_t q = 0; q < nv; ++q) {
         const double* x = &R.vp[q * dim];
         double w = R.vw[q];
         vol += w;
         te(e, x, val.data(), grad.data());
         double fw = w * f_rhs(x, dim);
-        for (int a = 0; a < nloc; ++a) {
-            rhs[a] += val[a] * fw;
-            for (int c = 0; c < nloc; ++c) {
-                double s = 0.0;
-                for (int j = 0; j < dim; ++j) s += grad[j * nloc + a] * grad[j * nloc + c];
-                S[(size_t)a * nloc + c] += w * s;
-            }
-        }
+        for (int a = 0; a < nloc; ++a) rhs[a] += val[a] * fw;
+        add_grad_outer_any(S.data(), grad.data(), dim, nloc, w);
     }
+    for (int a = 0; a < nloc; ++a)
+        for (int c = 0; c < a; ++c) S[(size_t)a * nloc + c] = S[(size_t)c * nloc + a];
     std::vector<double> A = S;
     const size_t nb = R.bw.size();
     if (nb > 0) {
@@ -723,14 +750,26 @@ void cut_element_system(const Geometry& G, const Basis1D& B, int dim, int p, int
             gq[q] = g_bc(x, dim);
         }
         for (size_t q = 0; q < nb; ++q) {
-            double w = R.bw[q];
-            for (int a = 0; a < nloc; ++a)
-                for (int c = 0; c < nloc; ++c) {
-                    Mb[(size_t)a * nloc + c] += w * bv[q * nloc + a] * bv[q * nloc + c];
-                    Bn[(size_t)a * nloc + c] += w * dn[q * nloc + a] * dn[q * nloc + c];
-                    C[(size_t)a * nloc + c] += w * dn[q * nloc + a] * bv[q * nloc + c];
+            const double w = R.bw[q];
+            const double* bq = &bv[q * nloc];
+            const double* dq = &dn[q * nloc];
+            for (int a = 0; a < nloc; ++a) {
+                const double wb = w * bq[a], wd = w * dq[a];
+                double* Ma = &Mb[(size_t)a * nloc];
+                double* Ba = &Bn[(size_t)a * nloc];
+                double* Ca = &C[(size_t)a * nloc];
+                for (int c = a; c < nloc; ++c) {
+                    Ma[c] += wb * bq[c];
+                    Ba[c] += wd * dq[c];
                 }
+                for (int c = 0; c < nloc; ++c) Ca[c] += wd * bq[c];
+            }
         }
+        for (int a = 0; a < nloc; ++a)
+            for (int c = 0; c < a; ++c) {
+                Mb[(size_t)a * nloc + c] = Mb[(size_t)c * nloc + a];
+                Bn[(size_t)a * nloc + c] = Bn[(size_t)c * nloc + a];
+            }
         double beta;
         if (bc == 0) {
             beta = 2.0 / B.h;                    // the paper's penalty parameter 2/h
@@ -923,6 +962,13 @@ struct Builder {
             }
         }
         H.n_cut = (int64_t)cut.size();
+        const bool verbose = std::getenv("IMGM_VERBOSE") != nullptr;
+        auto t = std::chrono::steady_clock::now();
+        auto phase = [&](const char* name) {
+            const auto now = std::chrono::steady_clock::now();
+            if (verbose) std::fprintf(stderr, "imgm: setup   %-20s %8.3f s\n", name, std::chrono::duration<double>(now - t).count());
+            t = now;
+        };
         std::vector<CutElem> ce(cut.size());
 #pragma omp parallel for schedule(dynamic, 4)
         for (int64_t c = 0; c < (int64_t)cut.size(); ++c) {
@@ -936,6 +982,7 @@ struct Builder {
             ce[c].E = cut[c];
             cut_element_system(G, B, dim, p, pb.depth, pb.bc, e, lo, hi, ce[c]);
         }
+        phase("cut elements");
         std::vector<int32_t> cut_id(NE, -1);
         for (size_t c = 0; c < ce.size(); ++c) {
             cut_id[ce[c].E] = (int32_t)c;
@@ -989,42 +1036,61 @@ struct Builder {
                     }
             for (int c = 0; c < ncoef; ++c) lv.band_coef[(size_t)c * nb + bi] = row[c];
         }
-        // right-hand side
+        phase("stored rows");
+        // right-hand side, element by element; elements are taken in (p+1)^d colour
+        // classes (e_k mod (p+1) per direction) whose members share no function, so each
+        // class scatters into b in parallel without races
         H.b.assign(lv.N, 0.0);
         std::vector<double> g1, w1;
         gauss01(q, g1, w1);
-        TensorEval te{dim, p, nloc, &B};
-        std::vector<double> val(nloc), grad((size_t)dim * nloc);
-        for (int64_t E = 0; E < NE; ++E) {
-            if (!lv.elem_active[E]) continue;
-            int e[3];
-            unflat(E, n, e);
-            std::vector<double> bl;
-            if (lv.elem_full[E]) {
-                double lo[3], hi[3];
-                for (int k = 0; k < dim; ++k) {
-                    lo[k] = pb.lo + e[k] * B.h;
-                    hi[k] = lo[k] + B.h;
-                }
+        const int ncol = (dim == 2) ? q * q : q * q * q;
+        for (int col = 0; col < ncol; ++col) {
+            const int c0 = col % q, c1 = (col / q) % q, c2 = col / (q * q);
+            const int64_t n0 = (n - c0 + q - 1) / q, n1 = (n - c1 + q - 1) / q;
+            const int64_t n2 = (dim == 3) ? (n - c2 + q - 1) / q : 1;
+            const int64_t cnt = n0 * n1 * n2;
+#pragma omp parallel
+            {
+                TensorEval te{dim, p, nloc, &B};
+                std::vector<double> val(nloc), grad((size_t)dim * nloc), bl(nloc);
                 Rule R;
-                box_rule(lo, hi, dim, q, g1, w1, R);
-                bl.assign(nloc, 0.0);
-                for (size_t t = 0; t < R.vw.size(); ++t) {
-                    te(e, &R.vp[t * dim], val.data(), grad.data());
-                    double fw = R.vw[t] * f_rhs(&R.vp[t * dim], dim);
-                    for (int a = 0; a < nloc; ++a) bl[a] += val[a] * fw;
+#pragma omp for schedule(static)
+                for (int64_t k = 0; k < cnt; ++k) {
+                    int e[3] = {c0 + q * (int)(k % n0), c1 + q * (int)((k / n0) % n1),
+                                dim == 3 ? c2 + q * (int)(k / (n0 * n1)) : 0};
+                    const int64_t E = flat(e, n);
+                    if (!lv.elem_active[E]) continue;
+                    const double* src;
+                    if (lv.elem_full[E]) {
+                        double lo[3], hi[3];
+                        for (int kk = 0; kk < dim; ++kk) {
+                            lo[kk] = pb.lo + e[kk] * B.h;
+                            hi[kk] = lo[kk] + B.h;
+                        }
+                        R.vp.clear();
+                        R.vw.clear();
+                        box_rule(lo, hi, dim, q, g1, w1, R);
+                        std::fill(bl.begin(), bl.end(), 0.0);
+                        for (size_t t = 0; t < R.vw.size(); ++t) {
+                            te(e, &R.vp[t * dim], val.data(), grad.data());
+                            const double fw = R.vw[t] * f_rhs(&R.vp[t * dim], dim);
+                            for (int a = 0; a < nloc; ++a) bl[a] += val[a] * fw;
+                        }
+                        src = bl.data();
+                    } else {
+                        src = ce[cut_id[E]].b.data();
+                    }
+                    for (int a = 0; a < nloc; ++a) {
+                        int c[3] = {a % q, (a / q) % q, a / (q * q)};
+                        int j[3] = {e[0] + c[0], e[1] + c[1], dim == 3 ? e[2] + c[2] : 0};
+                        H.b[flat(j, lv.m)] += src[a];
+                    }
                 }
-            } else {
-                bl = ce[cut_id[E]].b;
-            }
-            for (int a = 0; a < nloc; ++a) {
-                int c[3] = {a % q, (a / q) % q, a / (q * q)};
-                int j[3] = {e[0] + c[0], e[1] + c[1], dim == 3 ? e[2] + c[2] : 0};
-                H.b[flat(j, lv.m)] += bl[a];
             }
         }
         for (int64_t r = 0; r < lv.N; ++r)
             if (!lv.active[r]) H.b[r] = 0.0;
+        phase("right-hand side");
         (void)err;
         return true;
     }
@@ -1353,15 +1419,27 @@ struct Builder {
             lv.h = basis[li].h;
             lv.N = pw(lv.m, dim);
         }
+        const bool verbose = std::getenv("IMGM_VERBOSE") != nullptr;
+        auto t = std::chrono::steady_clock::now();
+        auto phase = [&](const char* name) {
+            const auto now = std::chrono::steady_clock::now();
+            if (verbose) std::fprintf(stderr, "imgm: setup %-22s %8.3f s\n", name, std::chrono::duration<double>(now - t).count());
+            t = now;
+        };
         if (!build_finest(err)) return false;
+        phase("finest level");
         for (int li = L - 1; li >= 1; --li) {
             build_transfer(li);
             build_coarse(li - 1);
         }
+        phase("Galerkin levels");
         if (!build_coarse_solve(err)) return false;
+        phase("coarsest solve");
         for (int li = L - 1; li >= 1; --li)
             if (!build_blocks(li, err)) return false;
+        phase("Schwarz blocks");
         if (pb.precision == 1) build_fp32();
+        phase("FP32 copies");
         return true;
     }
 };
