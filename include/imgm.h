@@ -73,6 +73,8 @@ typedef struct {
     int status;              /* IMGM_OK, IMGM_MAX_ITER or IMGM_ERR_BREAKDOWN */
     double rel_residual;     /* ||r_k|| / ||b|| of the recursively updated residual */
     double true_rel_residual;/* ||b - A x|| / ||b||, recomputed at exit */
+    int64_t kernel_launches; /* kernels of this library the solve ran on the device (measurement aid;
+                                the paper has no counterpart) */
 } imgm_result;
 
 typedef struct {

@@ -9,6 +9,12 @@
   domain lies inside its own (the encapsulating-support rule; for Lagrange bases only
   the nodal functions own blocks), the tiny-eigenvalue rule of Remark 3.3, and the
   relaxation gamma = 1 / max_K N_K (N_K = (p+1)^d for B-splines, 2^d for Lagrange);
+* coloured multiplicative Schwarz (Sec. 3.4, the smoother of the paper's experiments):
+  the blocks fall into classes of equal colour whose owners' supports are disjoint
+  ((p+1)^d colours for B-splines, 2^d for Lagrange), the blocks of one colour act
+  together on the current residual, and the residual is updated after each colour; the
+  post-smoothing sweep takes the colours in reverse order, which makes it the adjoint of
+  the pre-smoothing sweep, and no relaxation parameter is used;
 * the V-cycle of Algorithm 1 with a direct solve on level 1, one pre- and one
   post-smoothing step, and the symmetric V-cycle as a CG preconditioner (Sec. 3.2).
 
@@ -30,7 +36,13 @@ Readings of the silent or ambiguous points:
 * the encapsulating-support test compares the sets of active support elements
   (B-splines and Lagrange functions are non-zero inside every element of their
   support, so this is the set inclusion of the supports within Omega_h);
-* a Lagrange function that no nodal block contains gets a block of its own;
+* a Lagrange function that no nodal block contains gets a block of its own (additive
+  smoother only: the paper's colouring covers the nodal blocks, so the multiplicative
+  smoother rejects such levels);
+* the colour of a block is that of its owner: the owner's index modulo p+1 in every
+  direction for B-splines, its vertex index modulo 2 for Lagrange functions; colours are
+  taken in increasing order of sum_k c_k (p+1)^k (2^k for Lagrange) in the
+  pre-smoothing sweep;
 * tiny-eigenvalue rule: while lambda_min(A_j) < 1e-16 max_i (A_j)_ii, the function
   with the largest |entry| of the eigenvector of lambda_min (lowest index on ties) leaves
   the block; lambda_min is taken as 1 / lambda_max(A_j^{-1}) with A_j^{-1} formed through
@@ -103,12 +115,15 @@ def coarse_activity(tb_c: TensorBasis, fine_elem_active: np.ndarray, n_fine: int
     return elem_active, np.flatnonzero(func)
 
 
-def schwarz_blocks(tb: TensorBasis, elem_active: np.ndarray, active: np.ndarray):
-    """Index blocks by encapsulating supports (Sec. 3.4), in active numbering."""
+def schwarz_blocks(tb: TensorBasis, elem_active: np.ndarray, active: np.ndarray, with_owners: bool = False):
+    """Index blocks by encapsulating supports (Sec. 3.4), in active numbering.
+
+    with_owners: also return the owner of every block (full-grid index of the function
+    whose support bounds it; -1 for the block of a function that no nodal block holds)."""
     pos = -np.ones(tb.n_funcs, dtype=np.int64)
     pos[active] = np.arange(active.size)
     act_el = {int(I): frozenset(E for E in tb.support_elems(int(I)) if elem_active[E]) for I in active}
-    blocks = []
+    blocks, owners = [], []
     covered = np.zeros(active.size, dtype=bool)
     for I in active:
         I = int(I)
@@ -120,10 +135,24 @@ def schwarz_blocks(tb: TensorBasis, elem_active: np.ndarray, active: np.ndarray)
             cand.update(int(J) for J in tb.elem_dofs(E) if pos[J] >= 0)
         blk = sorted(pos[J] for J in cand if act_el[J] <= act_el[I])
         blocks.append(np.array(blk, dtype=np.int64))
+        owners.append(I)
         covered[blk] = True
     for k in np.flatnonzero(~covered):
         blocks.append(np.array([k], dtype=np.int64))
-    return blocks
+        owners.append(-1)
+    return (blocks, owners) if with_owners else blocks
+
+
+def block_colour(tb: TensorBasis, owner: int) -> int:
+    """Colour of the block of `owner`: functions of equal colour have disjoint supports
+    (Sec. 3.4): index mod (p+1) per direction for B-splines, vertex index mod 2 for
+    Lagrange functions (vertex = node / p)."""
+    multi = tb.func_multi(int(owner))
+    if isinstance(tb.b, Lagrange1D):
+        digits, base = [(int(i) // tb.b.p) % 2 for i in multi], 2
+    else:
+        digits, base = [int(i) % (tb.b.p + 1) for i in multi], tb.b.p + 1
+    return int(sum(c * base ** k for k, c in enumerate(digits)))
 
 
 def block_inverse(Aj: np.ndarray) -> np.ndarray:
@@ -166,23 +195,29 @@ def prune_block(Aj: np.ndarray, idx: np.ndarray):
     return Aj, idx, removed
 
 
-def schwarz_operator(A: sp.csr_matrix, blocks):
-    """sum_j P_j A_j^{-1} P_j^T as a sparse matrix, after the Remark 3.3 rule."""
-    rows, cols, vals = [], [], []
-    kept, pruned = [], 0
+def block_sum(n: int, blocks, inverses) -> sp.csr_matrix:
+    """sum_j P_j A_j^{-1} P_j^T over the given blocks as a sparse n x n matrix."""
+    if not blocks:
+        return sp.csr_matrix((n, n))
+    rows = [np.repeat(idx, idx.size) for idx in blocks]
+    cols = [np.tile(idx, idx.size) for idx in blocks]
+    vals = [inv.ravel() for inv in inverses]
+    return sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(n, n))
+
+
+def schwarz_operator(A: sp.csr_matrix, blocks, with_inverses: bool = False):
+    """sum_j P_j A_j^{-1} P_j^T as a sparse matrix, after the Remark 3.3 rule
+    (with_inverses: also the kept blocks' inverses, in block order)."""
+    kept, inverses, pruned = [], [], 0
     Ad = A.tocsr()
     for idx in blocks:
         Aj = Ad[idx][:, idx].toarray()
         Aj, idx, removed = prune_block(Aj, idx)
         pruned += removed
-        Ainv = block_inverse(Aj)
-        rows.append(np.repeat(idx, idx.size))
-        cols.append(np.tile(idx, idx.size))
-        vals.append(Ainv.ravel())
+        inverses.append(block_inverse(Aj))
         kept.append(idx)
-    n = A.shape[0]
-    Minv = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(n, n))
-    return Minv, kept, pruned
+    Minv = block_sum(A.shape[0], kept, inverses)
+    return (Minv, kept, pruned, inverses) if with_inverses else (Minv, kept, pruned)
 
 
 def default_gamma(kind: int, p: int, dim: int) -> float:
@@ -195,8 +230,13 @@ class Hierarchy:
 
     def __init__(self, disc, levels: int, gamma: float | None = None, smoother: str = "additive"):
         self.disc, self.L = disc, int(levels)
-        self.gamma = default_gamma(disc.kind, disc.p, disc.dim) if gamma is None else float(gamma)
+        if smoother not in ("additive", "multiplicative"):
+            raise ValueError("smoother must be 'additive' or 'multiplicative'")
         self.smoother = smoother
+        if smoother == "multiplicative":
+            self.gamma = 1.0                              # no relaxation (Sec. 3.4)
+        else:
+            self.gamma = default_gamma(disc.kind, disc.p, disc.dim) if gamma is None else float(gamma)
         d, p, n = disc.dim, disc.p, disc.n
         if n % (2 ** (levels - 1)):
             raise ValueError("n must be divisible by 2^(levels-1)")
@@ -216,17 +256,38 @@ class Hierarchy:
             self.lv[l - 1] = Level(tbc, ea, Ac, act)
         for l in range(levels, 1, -1):
             lev = self.lv[l]
-            blocks = schwarz_blocks(lev.tb, lev.elem_active, lev.active)
-            lev.Minv, lev.blocks, lev.pruned = schwarz_operator(lev.A, blocks)
+            blocks, owners = schwarz_blocks(lev.tb, lev.elem_active, lev.active, with_owners=True)
+            lev.Minv, lev.blocks, lev.pruned, inverses = schwarz_operator(lev.A, blocks, with_inverses=True)
+            lev.owners = owners
+            if smoother == "multiplicative":
+                if min(owners) < 0:
+                    raise ValueError("multiplicative Schwarz: a function lies in no nodal block")
+                colours = np.array([block_colour(lev.tb, o) for o in owners])
+                n_col = (2 if isinstance(lev.tb.b, Lagrange1D) else p + 1) ** d
+                lev.colour_ops = [block_sum(lev.A.shape[0], [lev.blocks[j] for j in np.flatnonzero(colours == c)],
+                                            [inverses[j] for j in np.flatnonzero(colours == c)])
+                                  for c in range(n_col)]
         A1 = self.lv[1].A.toarray()
         _, self.coarse_idx, self.coarse_pruned = prune_block(A1, np.arange(A1.shape[0]))
         self.coarse_inv = block_inverse(A1[np.ix_(self.coarse_idx, self.coarse_idx)])
 
     # -------------------------------------------------------------- Algorithm 1
     def smooth(self, l: int, r: np.ndarray, adjoint: bool = False) -> np.ndarray:
-        """gamma M^{-1} r (adjoint: gamma M^{-T} r; M^{-1} is symmetric for additive Schwarz)."""
-        Minv = self.lv[l].Minv
-        return self.gamma * ((Minv.T if adjoint else Minv) @ r)
+        """gamma M^{-1} r (adjoint: gamma M^{-T} r; M^{-1} is symmetric for additive Schwarz).
+
+        Multiplicative: one coloured sweep from zero, colours in increasing order
+        (adjoint: decreasing), the residual updated after every colour."""
+        lev = self.lv[l]
+        if self.smoother == "additive":
+            return self.gamma * ((lev.Minv.T if adjoint else lev.Minv) @ r)
+        order = range(len(lev.colour_ops))
+        y = np.zeros_like(r)
+        rt = r.copy()
+        for c in (reversed(order) if adjoint else order):
+            dy = lev.colour_ops[c] @ rt
+            y = y + dy
+            rt = rt - lev.A @ dy
+        return y
 
     def vcycle(self, l: int, r: np.ndarray) -> np.ndarray:
         if l == 1:                                                      # line 14

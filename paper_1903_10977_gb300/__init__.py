@@ -38,7 +38,7 @@ class Config(ctypes.Structure):
 
 class Result(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("status", ctypes.c_int), ("rel_residual", ctypes.c_double),
-                ("true_rel_residual", ctypes.c_double)]
+                ("true_rel_residual", ctypes.c_double), ("kernel_launches", ctypes.c_int64)]
 
 
 class LevelInfo(ctypes.Structure):
@@ -217,7 +217,7 @@ class Solver:
                                  _ptr(hbuf) if hist else None, _stream(stream))
         self._check(rc)
         out = {"iterations": res.iterations, "status": res.status, "rel_residual": res.rel_residual,
-               "true_rel_residual": res.true_rel_residual}
+               "true_rel_residual": res.true_rel_residual, "kernel_launches": res.kernel_launches}
         if hist:
             hbuf = hbuf[: res.iterations + 1]
         return x, out, hbuf

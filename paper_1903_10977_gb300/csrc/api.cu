@@ -93,6 +93,7 @@ struct imgm_handle {
     cudaGraphExec_t exec = nullptr;
     bool graph_failed = false;
     cudaStream_t capture = nullptr;    // the solve graph is captured here (the caller's stream may be the legacy one)
+    int64_t graph_kernels[3] = {0, 0, 0};   // kernel nodes of the solve graph: start, loop body, finish
     std::string err;
 
     template <class T>
@@ -315,6 +316,7 @@ cudaError_t build_solve_graph(imgm_handle* h) {
     cudaGraph_t g = nullptr;
     do {
         if ((e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) break;
+        int64_t c0 = imgm::launch_count();
         cudaError_t ce = enqueue_solve_start(h, s);
         cudaGraph_t cg = nullptr;
         const cudaGraphNode_t* deps = nullptr;
@@ -341,14 +343,19 @@ cudaError_t build_solve_graph(imgm_handle* h) {
             cudaGraph_t body = cp.conditional.phGraph_out[0];
             ce = cudaStreamBeginCaptureToGraph(body_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
             if (ce == cudaSuccess) {
+                h->graph_kernels[0] = imgm::launch_count() - c0;
+                c0 = imgm::launch_count();
                 cudaError_t be = enqueue_iteration(h, body_stream);
                 if (be == cudaSuccess) be = imgm::launch_set_continue(h->st, (unsigned long long)handle, body_stream);
+                h->graph_kernels[1] = imgm::launch_count() - c0;
+                c0 = imgm::launch_count();
                 cudaGraph_t outb = nullptr;
                 cudaError_t ee = cudaStreamEndCapture(body_stream, &outb);
                 ce = (be != cudaSuccess) ? be : ee;
             }
         }
         if (ce == cudaSuccess) ce = enqueue_solve_finish(h, s);
+        h->graph_kernels[2] = imgm::launch_count() - c0;
         e = cudaStreamEndCapture(s, &g);
         if (ce != cudaSuccess) e = ce;
         if (e != cudaSuccess) break;
@@ -779,6 +786,13 @@ int imgm_pcg_solve(imgm_handle* h, const double* dev_b, double* dev_x, double rt
     CK(cudaMemcpyAsync(h->st, &init, sizeof(init), cudaMemcpyHostToDevice, s), "state");
     CK(cudaMemcpyAsync(h->cb, dev_b, N * sizeof(double), cudaMemcpyDeviceToDevice, s), "copy b");
     CK(cudaMemcpyAsync(h->cx, dev_x, N * sizeof(double), cudaMemcpyDeviceToDevice, s), "copy x0");
+    // IMGM_SOLVE_GRAPH=0: the same kernels from a host loop instead of the conditional graph
+    // (profilers cannot look inside graphs that hold conditional nodes)
+    static const bool no_graph = [] {
+        const char* v = std::getenv("IMGM_SOLVE_GRAPH");
+        return v && v[0] == '0';
+    }();
+    if (no_graph) h->graph_failed = true;
     if (!h->exec && !h->graph_failed) {
         cudaError_t ge = build_solve_graph(h);
         if (ge != cudaSuccess) {
@@ -799,6 +813,7 @@ int imgm_pcg_solve(imgm_handle* h, const double* dev_b, double* dev_x, double rt
                 std::fprintf(stderr, "imgm: conditional solve graph not built (%s), host loop\n", cudaGetErrorString(ge));
         }
     }
+    const int64_t launches0 = imgm::launch_count();
     if (h->exec) {
         CK(cudaGraphLaunch(h->exec, s), "graph launch");
     } else {
@@ -822,6 +837,9 @@ int imgm_pcg_solve(imgm_handle* h, const double* dev_b, double* dev_x, double rt
     CK(cudaStreamSynchronize(s), "solve sync");
     out->iterations = fin.iter;
     out->status = fin.status;
+    // graph: the start part, one loop body per iteration, the finish part
+    out->kernel_launches = h->exec ? h->graph_kernels[0] + (int64_t)fin.iter * h->graph_kernels[1] + h->graph_kernels[2]
+                                   : imgm::launch_count() - launches0;
     out->rel_residual = fin.bb > 0 ? std::sqrt(fin.rr / fin.bb) : 0.0;
     out->true_rel_residual = fin.bb > 0 ? std::sqrt(fin.true_rr / fin.bb) : 0.0;
     return fin.status == -5 ? IMGM_ERR_BREAKDOWN : (fin.status == 1 ? IMGM_MAX_ITER : IMGM_OK);

@@ -793,6 +793,7 @@ __global__ void k_set_continue(PcgState* st, cudaGraphConditionalHandle handle) 
 }
 
 thread_local bool t_pdl = true;
+thread_local int64_t t_launches = 0;   // kernels issued by this host thread
 
 // Whether the next launch on s may carry the programmatic-serialisation attribute: always
 // outside stream capture; under capture only when every node it will depend on is a
@@ -831,6 +832,7 @@ cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t sme
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = pdl_allowed(s) ? 1 : 0;
+    ++t_launches;
     return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
 }
 
@@ -881,6 +883,7 @@ cudaError_t launch_tile2d(const DevLevelT<T>& L, int mode, const T* x, const T* 
 }  // namespace
 
 void set_programmatic_launch(bool on) { t_pdl = on; }
+int64_t launch_count() { return t_launches; }
 
 int reduction_blocks() {
     if (g_red_blocks == 0) g_red_blocks = num_sms() * 4;
@@ -1022,6 +1025,7 @@ cudaError_t launch_vcycle_cluster(int dim, int p, const VcycleCoarse* V, size_t 
     attr[1].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = pdl_allowed(s) ? 2 : 1;
+    ++t_launches;
 #define IMGM_CLUSTER_CASE(D_, P_)                                                                                 \
     if (dim == D_ && p == P_) {                                                                                   \
         return cudaLaunchKernelEx(&cfg, k_vcycle_cluster<D_, P_>, V, done);                                      \

@@ -154,5 +154,7 @@ cudaError_t launch_vcycle_cluster(int dim, int p, const VcycleCoarse* V, size_t 
 int reduction_blocks();   // fixed number of blocks of every reducing kernel
 // programmatic dependent launch of the kernels issued by this host thread (default on)
 void set_programmatic_launch(bool on);
+// kernels launched (or captured) so far by this host thread
+int64_t launch_count();
 
 }  // namespace imgm

@@ -201,6 +201,7 @@ def test_pcg_converged(pair):
     record(iterations=res["iterations"], oracle_iterations=it, mass_rel=mr,
            true_rel_residual=res["true_rel_residual"])
     assert res["status"] == lib.IMGM_OK and abs(res["iterations"] - it) <= max(1, 0.05 * it)
+    assert res["kernel_launches"] > 5 * res["iterations"]
     assert res["rel_residual"] <= 1e-8 and res["true_rel_residual"] <= 1e-7
     assert mr < (1e-10 if res["iterations"] == it else 1e-6)
 

@@ -194,3 +194,135 @@ def test_iterations_independent_of_mesh_size():
         _, it, _ = pcg(d.A, d.b, H.precondition, 1e-8, 400)
         its.append(it)
     assert max(its) - min(its) <= 0.25 * max(its), its
+
+
+# ------------------------------------------------ coloured multiplicative Schwarz
+@pytest.fixture(scope="module")
+def mult_hier():
+    geom = G.Balls([[0.52, 0.47]], [0.3])
+    d = Discretization(geom, 0, 2, 16, 2, NITSCHE)
+    return d, Hierarchy(d, 2, smoother="multiplicative")
+
+
+def test_colour_classes_are_decoupled(mult_hier):
+    """Blocks of one colour share no function and no matrix entry (Sec. 3.4: functions of
+    blocks with equal colour have disjoint supports), so they do not see each other's
+    residual updates; (p+1)^d = 9 colours for quadratic B-splines in 2-D."""
+    d, H = mult_hier
+    lev = H.lv[2]
+    assert len(lev.colour_ops) == 9
+    A = lev.A.tocsr()
+    from oracle.multigrid import block_colour
+    for col, C in enumerate(lev.colour_ops):
+        # two different blocks of this colour: no common member, no coupling in A
+        seen = np.zeros(C.shape[0], dtype=int)
+        blocks_c = [b for b, o in zip(lev.blocks, lev.owners) if block_colour(lev.tb, o) == col]
+        for k, b in enumerate(blocks_c):
+            assert not seen[b].any()
+            seen[b] = k + 1
+        for k, b in enumerate(blocks_c):
+            coupled = np.unique(A[b].indices)
+            others = seen[coupled]
+            assert np.all((others == 0) | (others == k + 1))
+
+
+def sequential_multiplicative(A, blocks, inverses, r):
+    """Eq. multiplicativeSchwarz1 taken literally: one block at a time, the residual
+    updated after every block."""
+    y = np.zeros_like(r)
+    rt = r.copy()
+    for idx, Ainv in zip(blocks, inverses):
+        dy = np.zeros_like(r)
+        dy[idx] = Ainv @ rt[idx]
+        y += dy
+        rt -= A @ dy
+    return y
+
+
+def test_coloured_sweep_equals_block_by_block_sweep(mult_hier):
+    """The coloured sweep (residual updated once per colour) equals the block-by-block
+    multiplicative Schwarz of Eq. multiplicativeSchwarz1 with the blocks in colour order,
+    forward and reversed."""
+    from oracle.multigrid import block_colour, block_inverse
+    d, H = mult_hier
+    lev = H.lv[2]
+    A = lev.A.tocsr()
+    colours = [block_colour(lev.tb, o) for o in lev.owners]
+    order = sorted(range(len(lev.blocks)), key=lambda j: (colours[j], j))
+    blocks = [lev.blocks[j] for j in order]
+    invs = [block_inverse(A[b][:, b].toarray()) for b in blocks]
+    r = np.random.default_rng(7).standard_normal(A.shape[0])
+    fwd = sequential_multiplicative(A, blocks, invs, r)
+    bwd = sequential_multiplicative(A, blocks[::-1], invs[::-1], r)
+    got_f, got_b = H.smooth(2, r), H.smooth(2, r, adjoint=True)
+    Ad = A.toarray()
+    en = lambda v: math.sqrt(v @ Ad @ v)
+    assert en(got_f - fwd) <= 1e-12 * en(fwd)
+    assert en(got_b - bwd) <= 1e-12 * en(bwd)
+
+
+def test_multiplicative_lagrange_p1_box_is_coloured_gauss_seidel():
+    """Lagrange p = 1 without holes: every block is one function, so a forward sweep is
+    point Gauss-Seidel with the unknowns ordered by colour, (D + L)^{-1} r, solved here
+    by a library triangular solve."""
+    geom = G.Balls(np.zeros((0, 2)), np.zeros(0))
+    d = Discretization(geom, 1, 1, 8, 0, NITSCHE)
+    H = Hierarchy(d, 2, smoother="multiplicative")
+    lev = H.lv[2]
+    assert all(b.size == 1 for b in lev.blocks) and len(lev.colour_ops) == 4
+    from oracle.multigrid import block_colour
+    col = np.empty(len(lev.blocks), dtype=int)
+    for b, o in zip(lev.blocks, lev.owners):
+        col[b[0]] = block_colour(lev.tb, o)
+    perm = np.argsort(col, kind="stable")
+    A = lev.A.tocsr()
+    Ap = A[perm][:, perm]
+    r = np.random.default_rng(3).standard_normal(A.shape[0])
+    y = np.empty_like(r)
+    y[perm] = spla.spsolve_triangular(sp_tril(Ap), r[perm], lower=True)
+    np.testing.assert_allclose(H.smooth(2, r), y, rtol=1e-12, atol=1e-12 * np.abs(y).max())
+
+
+def sp_tril(M):
+    import scipy.sparse as sp
+    return sp.tril(M, format="csr")
+
+
+def test_multiplicative_vcycle_symmetric_error_propagation_and_spectrum(mult_hier):
+    """With the reversed post-smoothing sweep the V-cycle is symmetric; its error
+    propagation is E_post (I - R^T A_c^-1 R A) E_pre with E_pre = prod_c (I - B_c A) in
+    colour order and E_post the reversed product (Eq. eigenMulti with M^-1 the
+    multiplicative sweep); the spectrum of B A lies in (0, 1]."""
+    d, H = mult_hier
+    B = dense_vcycle(H)
+    assert np.abs(B - B.T).max() <= 1e-9 * np.abs(B).max()
+    lev = H.lv[2]
+    A = lev.A.toarray()
+    I = np.eye(A.shape[0])
+    Epre, Epost = I.copy(), I.copy()
+    for C in lev.colour_ops:
+        Epre = (I - C.toarray() @ A) @ Epre
+        Epost = Epost @ (I - C.toarray() @ A)
+    R = lev.R.toarray()
+    Ac = H.lv[1].A.toarray()
+    E = Epost @ (I - R.T @ np.linalg.solve(Ac, R @ A)) @ Epre
+    Ah = sla.sqrtm(A).real
+    lhs = Ah @ (I - B @ A) @ np.linalg.pinv(Ah)
+    rhs = Ah @ E @ np.linalg.pinv(Ah)
+    assert np.abs(lhs - rhs).max() < 1e-6
+    L = np.linalg.cholesky(0.5 * (B + B.T))
+    ev = np.linalg.eigvalsh(L.T @ A @ L)
+    assert ev.min() > 0.0 and ev.max() <= 1.0 + 1e-8
+
+
+def test_multiplicative_better_conditioned_than_additive(small_hier, mult_hier):
+    """Sec. 3.4: without the small relaxation parameter additive Schwarz needs, the
+    multiplicative V-cycle gives a much smaller condition number of B A."""
+    kappa = []
+    for d, H in (small_hier, mult_hier):
+        B = dense_vcycle(H)
+        A = H.lv[2].A.toarray()
+        L = np.linalg.cholesky(0.5 * (B + B.T))
+        ev = np.linalg.eigvalsh(L.T @ A @ L)
+        kappa.append(ev.max() / ev.min())
+    assert kappa[1] < 0.5 * kappa[0], kappa
