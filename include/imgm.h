@@ -66,6 +66,10 @@ typedef struct {
     double gamma;            /* additive Schwarz relaxation; <= 0 selects 1/(p+1)^d (Eq. applyCS) */
     int precision;           /* V-cycle arithmetic: 0 = FP64; 1 = FP32 on Jacobi-scaled data inside the
                                 FP64 CG, which then uses the flexible (Polak-Ribiere) beta */
+    int smoother;            /* 0 = additive Schwarz with relaxation gamma (Sec. 3.4, Eq. applyCS);
+                                1 = coloured multiplicative Schwarz (Sec. 3.4): (p+1)^d colours by the
+                                owner's index mod p+1, residual updated after each colour, colours
+                                reversed in the post-smoothing sweep, no relaxation (gamma unused) */
 } imgm_config;
 
 typedef struct {

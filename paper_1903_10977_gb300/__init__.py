@@ -33,7 +33,7 @@ class Geometry(ctypes.Structure):
 class Config(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int), ("basis", ctypes.c_int), ("degree", ctypes.c_int), ("levels", ctypes.c_int),
                 ("depth", ctypes.c_int), ("bc", ctypes.c_int), ("gamma", ctypes.c_double),
-                ("precision", ctypes.c_int)]
+                ("precision", ctypes.c_int), ("smoother", ctypes.c_int)]
 
 
 class Result(ctypes.Structure):
@@ -113,12 +113,12 @@ class Solver:
     """
 
     def __init__(self, dim, centers, radii, n, degree=2, levels=3, depth=0, bc=1, basis=0, gamma=0.0,
-                 lo=0.0, hi=1.0, host_only=False, precision=0):
+                 lo=0.0, hi=1.0, host_only=False, precision=0, smoother=0):
         self._c = np.ascontiguousarray(np.asarray(centers, dtype=np.float64).reshape(-1, dim))
         self._r = np.ascontiguousarray(np.asarray(radii, dtype=np.float64).reshape(-1))
         g = Geometry(dim, int(self._r.size), self._c.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                      self._r.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), lo, hi)
-        cfg = Config(n, basis, degree, levels, depth, bc, gamma, precision)
+        cfg = Config(n, basis, degree, levels, depth, bc, gamma, precision, smoother)
         h = _H()
         fn = _lib.imgm_setup_host if host_only else _lib.imgm_setup
         rc = fn(ctypes.byref(g), ctypes.byref(cfg), ctypes.byref(h))

@@ -38,6 +38,12 @@ struct LevelDev {
     // the same in FP32 and Jacobi-scaled variables (mixed-precision V-cycle)
     imgm::DevLevelT<float> fd;
     float *fx = nullptr, *fr = nullptr, *ft = nullptr, *fe = nullptr;
+    // multiplicative Schwarz: colour ranges (host) and the one-function blocks (device)
+    int ncolour = 0;
+    std::vector<int64_t> blk_cptr, sg_cptr;
+    int32_t* sg_row = nullptr;
+    double* sg_inv = nullptr;
+    float* f_sg_inv = nullptr;
     imgm_level_info info{};
 };
 
@@ -51,6 +57,7 @@ struct Acc<double> {
     static double* r(LevelDev& L) { return L.r; }
     static double* t(LevelDev& L) { return L.t; }
     static double* e(LevelDev& L) { return L.e; }
+    static const double* sg_inv(const LevelDev& L) { return L.sg_inv; }
 };
 template <>
 struct Acc<float> {
@@ -59,6 +66,7 @@ struct Acc<float> {
     static float* r(LevelDev& L) { return L.fr; }
     static float* t(LevelDev& L) { return L.ft; }
     static float* e(LevelDev& L) { return L.fe; }
+    static const float* sg_inv(const LevelDev& L) { return L.f_sg_inv; }
 };
 
 }  // namespace
@@ -68,6 +76,8 @@ struct imgm_handle {
     bool on_device = false;
     int dim = 2, p = 2, L = 2;
     double gamma = 0.0;
+    int smoother = 0;          // 0 additive, 1 coloured multiplicative Schwarz
+    double gamma_diag = 0.0;   // factor of the diagonal start x = gamma_diag dinv r (0: x starts at 0)
     std::vector<LevelDev> lv;          // index 0 = level 1
     std::vector<void*> allocs;
     int32_t* c_rows = nullptr;
@@ -180,8 +190,62 @@ int cluster_top<double>(const imgm_handle*) { return -1; }
 template <>
 int cluster_top<float>(const imgm_handle* h) { return h->vc_top; }
 
+// one colour c of the multiplicative Schwarz sweep on level F: x += B_c r
+template <typename T>
+cudaError_t colour_step(LevelDev& F, int c, const T* r, T* x, const int* done, cudaStream_t s) {
+    using A = Acc<T>;
+    const int64_t s0 = F.sg_cptr[c];
+    return imgm::launch_colour_smooth<T>(A::d(F), F.blk_cptr[c], F.blk_cptr[c + 1], F.sg_row + s0, A::sg_inv(F) + s0,
+                                         F.sg_cptr[c + 1] - s0, r, x, done, s);
+}
+
+// The V-cycle with coloured multiplicative Schwarz (Sec. 3.4).  On entry z = 0.  Each
+// level: a forward sweep over the colours from x = 0, the residual recomputed after every
+// colour (so that line 5 falls out of the last one), restriction, coarse correction,
+// t -= A e (line 10), and the reversed sweep on the current residual (line 12).
+template <typename T>
+cudaError_t enqueue_vcycle_mult(imgm_handle* h, const T* r, T* z, const int* done, cudaStream_t s) {
+    using A = Acc<T>;
+    const int L = h->L;
+    cudaError_t e;
+    for (int li = L - 1; li >= 1; --li) {
+        LevelDev& F = h->lv[li];
+        LevelDev& C = h->lv[li - 1];
+        const T* rl = (li == L - 1) ? r : A::r(F);
+        T* xl = (li == L - 1) ? z : A::x(F);
+        for (int c = 0; c < F.ncolour; ++c) {
+            if ((e = colour_step<T>(F, c, c == 0 ? rl : A::t(F), xl, done, s)) != cudaSuccess) return e;
+            if ((e = imgm::launch_apply<T>(A::d(F), imgm::RESID, xl, rl, A::t(F), nullptr, 0.0, done, s)) != cudaSuccess)
+                return e;
+        }
+        T* xc = (li - 1 >= 1) ? A::x(C) : nullptr;     // zeroed: the coarse sweep starts from 0
+        if ((e = imgm::launch_restrict<T>(A::d(F), A::d(C), A::t(F), A::r(C), xc, 0.0, done, s)) != cudaSuccess) return e;
+    }
+    if ((e = imgm::launch_coarse<T>(h->c_rows, coarse_inverse<T>(h), h->nc, A::r(h->lv[0]), A::x(h->lv[0]), done, s)) !=
+        cudaSuccess)
+        return e;
+    for (int li = 1; li <= L - 1; ++li) {
+        LevelDev& F = h->lv[li];
+        LevelDev& C = h->lv[li - 1];
+        const T* rl = (li == L - 1) ? r : A::r(F);
+        T* xl = (li == L - 1) ? z : A::x(F);
+        if ((e = imgm::launch_prolong<T>(A::d(F), A::d(C), A::x(C), A::e(F), xl, done, s)) != cudaSuccess) return e;
+        if ((e = imgm::launch_apply<T>(A::d(F), imgm::RESID, A::e(F), A::t(F), A::t(F), nullptr, 0.0, done, s)) !=
+            cudaSuccess)
+            return e;
+        for (int c = F.ncolour - 1; c >= 0; --c) {
+            if ((e = colour_step<T>(F, c, A::t(F), xl, done, s)) != cudaSuccess) return e;
+            if (c > 0 &&
+                (e = imgm::launch_apply<T>(A::d(F), imgm::RESID, xl, rl, A::t(F), nullptr, 0.0, done, s)) != cudaSuccess)
+                return e;
+        }
+    }
+    return cudaSuccess;
+}
+
 template <typename T>
 cudaError_t enqueue_vcycle(imgm_handle* h, const T* r, T* z, const int* done, cudaStream_t s) {
+    if (h->smoother == 1) return enqueue_vcycle_mult<T>(h, r, z, done, s);
     using A = Acc<T>;
     const int L = h->L;
     const double g = h->gamma;
@@ -259,13 +323,13 @@ cudaError_t enqueue_solve_start(imgm_handle* h, cudaStream_t s) {
         return e;
     if ((e = imgm::launch_pcg_init_norms(N, h->cr, h->cb, h->partial, h->st, h->hist, s)) != cudaSuccess) return e;
     if (h->precision == 1) {
-        if ((e = imgm::launch_vcycle_in<float>(N, h->cr, F.fd.s, F.fd.dinv, h->gamma, h->rf, h->zf, done, s)) !=
+        if ((e = imgm::launch_vcycle_in<float>(N, h->cr, F.fd.s, F.fd.dinv, h->gamma_diag, h->rf, h->zf, done, s)) !=
             cudaSuccess)
             return e;
         if ((e = enqueue_vcycle<float>(h, h->rf, h->zf, done, s)) != cudaSuccess) return e;
         return imgm::launch_pcg_init_dir<float>(N, h->cr, h->zf, F.fd.s, h->cp, h->zpf, h->partial, h->st, s);
     }
-    if ((e = imgm::launch_scale_diag<double>(F.d, h->cr, h->cz, h->gamma, done, s)) != cudaSuccess) return e;
+    if ((e = imgm::launch_scale_diag<double>(F.d, h->cr, h->cz, h->gamma_diag, done, s)) != cudaSuccess) return e;
     if ((e = enqueue_vcycle<double>(h, h->cr, h->cz, done, s)) != cudaSuccess) return e;
     return imgm::launch_pcg_init_dir<double>(N, h->cr, h->cz, nullptr, h->cp, nullptr, h->partial, h->st, s);
 }
@@ -278,7 +342,7 @@ cudaError_t enqueue_iteration(imgm_handle* h, cudaStream_t s) {
     if ((e = imgm::launch_apply_pq(F.d, h->cp, h->cq, h->partial, h->st, s)) != cudaSuccess) return e;
     if (h->precision == 1) {
         if ((e = imgm::launch_pcg_update<float>(F.d, F.fd.dinv, h->cx, h->cr, h->cp, h->cq, h->zf, h->rf, F.fd.s,
-                                                h->gamma, h->partial, h->st, h->hist, s)) != cudaSuccess)
+                                                h->gamma_diag, h->partial, h->st, h->hist, s)) != cudaSuccess)
             return e;
         if ((e = enqueue_vcycle<float>(h, h->rf, h->zf, done, s)) != cudaSuccess) return e;
         if ((e = imgm::launch_pcg_rz<float>(N, h->cr, h->zf, F.fd.s, h->zpf, h->partial, h->st, s)) != cudaSuccess)
@@ -286,7 +350,7 @@ cudaError_t enqueue_iteration(imgm_handle* h, cudaStream_t s) {
         return imgm::launch_pcg_xpay<float>(N, h->zf, F.fd.s, h->cp, h->zpf, h->st, s);
     }
     if ((e = imgm::launch_pcg_update<double>(F.d, F.d.dinv, h->cx, h->cr, h->cp, h->cq, h->cz, nullptr, nullptr,
-                                             h->gamma, h->partial, h->st, h->hist, s)) != cudaSuccess)
+                                             h->gamma_diag, h->partial, h->st, h->hist, s)) != cudaSuccess)
         return e;
     if ((e = enqueue_vcycle<double>(h, h->cr, h->cz, done, s)) != cudaSuccess) return e;
     if ((e = imgm::launch_pcg_rz<double>(N, h->cr, h->cz, nullptr, nullptr, h->partial, h->st, s)) != cudaSuccess)
@@ -523,6 +587,14 @@ int upload_level(imgm_handle* h, const imgm::LevelData& src, LevelDev& dst, int 
         CK(cudaMemset(dst.ft, 0, src.N * sizeof(float)), "memset");
         CK(cudaMemset(dst.fe, 0, src.N * sizeof(float)), "memset");
     }
+    dst.ncolour = src.ncolour;
+    dst.blk_cptr = src.blk_cptr;
+    dst.sg_cptr = src.sg_cptr;
+    if (src.ncolour > 0) {
+        CK(h->upload(&dst.sg_row, src.sg_row), "upload one-function blocks");
+        CK(h->upload(&dst.sg_inv, src.sg_inv), "upload one-function blocks");
+        if (h->precision == 1) CK(h->upload(&dst.f_sg_inv, src.f_sg_inv), "upload fp32 one-function blocks");
+    }
     imgm_level_info& in = dst.info;
     in.n_grid = src.N;
     in.n_active = src.n_active;
@@ -556,6 +628,7 @@ imgm::Problem make_problem(const imgm_geometry* geom, const imgm_config* cfg) {
     pb.bc = cfg->bc;
     pb.gamma = cfg->gamma;
     pb.precision = cfg->precision;
+    pb.smoother = cfg->smoother;
     return pb;
 }
 
@@ -596,6 +669,8 @@ int imgm_setup(const imgm_geometry* geom, const imgm_config* cfg, imgm_handle** 
     hp->L = h->H.L;
     hp->gamma = h->H.gamma;
     hp->precision = cfg->precision;
+    hp->smoother = cfg->smoother;
+    hp->gamma_diag = cfg->smoother == 1 ? 0.0 : hp->gamma;
     hp->lv.resize(hp->L);
     for (int li = 0; li < hp->L; ++li) {
         int rc = upload_level(hp, hp->H.lv[li], hp->lv[li], li);
@@ -621,7 +696,8 @@ int imgm_setup(const imgm_geometry* geom, const imgm_config* cfg, imgm_handle** 
                 CK(cudaMemset(h->zpf, 0, Nf0 * sizeof(float)), "memset");
             }
             // the coarse levels of the FP32 V-cycle as one cluster launch, when the device has clusters
-            if (h->L >= 2 && h->L - 1 <= imgm::VCYCLE_MAX_LEVELS && imgm::vcycle_cluster_size() > 0) {
+            if (h->smoother == 0 && h->L >= 2 && h->L - 1 <= imgm::VCYCLE_MAX_LEVELS &&
+                imgm::vcycle_cluster_size() > 0) {
                 imgm::VcycleCoarse vc{};
                 vc.top = h->L - 2;
                 int mb = 1;
@@ -716,8 +792,18 @@ int imgm_smooth(imgm_handle* h, int level, const double* dev_r, double* dev_z, v
     int c = check_level(h, level, 2);
     if (c) return c;
     if (!dev_r || !dev_z || dev_r == dev_z) return fail(h, IMGM_ERR_INVALID, "bad vector pointers");
-    const LevelDev& L = h->lv[level - 1];
+    LevelDev& L = h->lv[level - 1];
     cudaStream_t s = (cudaStream_t)stream;
+    if (h->smoother == 1) {
+        // forward coloured sweep from 0, residual (in the level's t) updated after each colour
+        CK(imgm::launch_scale_diag<double>(L.d, dev_r, dev_z, 0.0, nullptr, s), "smooth zero");
+        for (int k = 0; k < L.ncolour; ++k) {
+            CK(colour_step<double>(L, k, k == 0 ? dev_r : L.t, dev_z, nullptr, s), "smooth colour");
+            if (k + 1 < L.ncolour)
+                CK(imgm::launch_apply<double>(L.d, imgm::RESID, dev_z, dev_r, L.t, nullptr, 0.0, nullptr, s), "smooth residual");
+        }
+        return IMGM_OK;
+    }
     CK(imgm::launch_scale_diag<double>(L.d, dev_r, dev_z, h->gamma, nullptr, s), "smooth diag");
     CK(imgm::launch_blocks<double>(L.d, dev_r, dev_z, h->gamma, nullptr, s), "smooth blocks");
     return IMGM_OK;
@@ -760,13 +846,13 @@ int imgm_apply_preconditioner(imgm_handle* h, const double* dev_r, double* dev_z
     cudaStream_t s = (cudaStream_t)stream;
     LevelDev& F = h->lv[h->L - 1];
     if (h->precision == 1) {
-        CK(imgm::launch_vcycle_in<float>(F.d.N, dev_r, F.fd.s, F.fd.dinv, h->gamma, h->rf, h->zf, nullptr, s),
+        CK(imgm::launch_vcycle_in<float>(F.d.N, dev_r, F.fd.s, F.fd.dinv, h->gamma_diag, h->rf, h->zf, nullptr, s),
            "vcycle input");
         CK(enqueue_vcycle<float>(h, h->rf, h->zf, nullptr, s), "vcycle");
         CK(imgm::launch_vcycle_out<float>(F.d.N, h->zf, F.fd.s, dev_z, s), "vcycle output");
         return IMGM_OK;
     }
-    CK(imgm::launch_scale_diag<double>(F.d, dev_r, dev_z, h->gamma, nullptr, s), "vcycle diag");
+    CK(imgm::launch_scale_diag<double>(F.d, dev_r, dev_z, h->gamma_diag, nullptr, s), "vcycle diag");
     CK(enqueue_vcycle<double>(h, dev_r, dev_z, nullptr, s), "vcycle");
     return IMGM_OK;
 }
@@ -933,6 +1019,8 @@ int imgm_setup_host(const imgm_geometry* geom, const imgm_config* cfg, imgm_hand
     h->p = h->H.p;
     h->L = h->H.L;
     h->gamma = h->H.gamma;
+    h->smoother = h->H.smoother;
+    h->gamma_diag = h->smoother == 1 ? 0.0 : h->gamma;
     h->lv.resize(h->L);
     for (int li = 0; li < h->L; ++li) {
         const imgm::LevelData& s = h->H.lv[li];

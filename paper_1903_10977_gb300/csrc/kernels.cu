@@ -416,11 +416,13 @@ __global__ void __launch_bounds__(TPB) k_scale_diag(int64_t N, const T* __restri
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) x[i] = gamma * dinv[i] * r[i];
 }
 
-// one warp per stored block: gather r_j, z_j = A_j^{-1} r_j, x[idx_j] += gamma z_j
+// one warp per stored block of [b_first, b_end): gather r_j, z_j = A_j^{-1} r_j,
+// x[idx_j] += gamma z_j
 template <typename T>
 __device__ __forceinline__ void blocks_warps(const DevLevelT<T>& L, const T* __restrict__ r, T* x, T gamma,
-                                             int64_t warp0, int64_t nwarps, int lane, T* rs) {
-    for (int64_t b = warp0; b < L.nblk; b += nwarps) {
+                                             int64_t b_first, int64_t b_end, int64_t warp0, int64_t nwarps, int lane,
+                                             T* rs) {
+    for (int64_t b = b_first + warp0; b < b_end; b += nwarps) {
         const int64_t s = ro(L.blk_ptr + b);
         const int nj = (int)(ro(L.blk_ptr + b + 1) - s);
         const T* __restrict__ A = L.blk_val + ro(L.blk_vptr + b);
@@ -443,8 +445,36 @@ __global__ void __launch_bounds__(TPB) k_blocks(DevLevelT<T> L, const T* __restr
     T* sm = reinterpret_cast<T*>(smraw);
     if (done && *done) return;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    blocks_warps<T>(L, r, x, gamma, ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5,
+    blocks_warps<T>(L, r, x, gamma, 0, L.nblk, ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5,
                     ((int64_t)gridDim.x * blockDim.x) >> 5, lane, sm + (int64_t)wib * L.max_block);
+}
+
+// One colour of the multiplicative Schwarz sweep (Sec. 3.4): x += sum_{j of colour c}
+// P_j A_j^{-1} P_j^T r.  The first ceil(ns/32) warps take the one-function blocks
+// (x_i += r_i / A_ii, one per thread), the others one stored block each.  Blocks of one
+// colour share no function, so no two threads write the same entry of x.
+template <typename T>
+__global__ void __launch_bounds__(TPB) k_colour_smooth(DevLevelT<T> L, int64_t b_first, int64_t b_end,
+                                                       const int32_t* __restrict__ sg_row,
+                                                       const T* __restrict__ sg_inv, int64_t ns,
+                                                       const T* __restrict__ r, T* x, const int* done) {
+    pdl_begin();
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T* sm = reinterpret_cast<T*>(smraw);
+    if (done && *done) return;
+    const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t wsg = (ns + 31) >> 5;
+    const int64_t w = gt >> 5;
+    if (w < wsg) {                 // warp-uniform branch
+        if (gt < ns) {
+            const int32_t i = ro(sg_row + gt);
+            x[i] += ro(sg_inv + gt) * r[i];
+        }
+        return;
+    }
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    blocks_warps<T>(L, r, x, T(1), b_first, b_end, w - wsg, ((int64_t)gridDim.x * blockDim.x >> 5) - wsg, lane,
+                    sm + (int64_t)wib * L.max_block);
 }
 
 template <typename T, int DIM, int P>
@@ -588,7 +618,7 @@ __global__ void __launch_bounds__(CLUSTER_TPB) k_vcycle_cluster(const VcycleCoar
     const float g = (float)V->gamma;
     const int top = V->top;
     for (int li = top; li >= 1; --li) {
-        blocks_warps<float>(V->lv[li], V->r[li], V->x[li], g, start >> 5, stride >> 5, lane, rs);
+        blocks_warps<float>(V->lv[li], V->r[li], V->x[li], g, 0, V->lv[li].nblk, start >> 5, stride >> 5, lane, rs);
         cl.sync();
         apply_rows<float, DIM, P>(V->lv[li], RESID, V->x[li], V->r[li], V->t[li], nullptr, g, start, stride);
         cl.sync();
@@ -603,7 +633,7 @@ __global__ void __launch_bounds__(CLUSTER_TPB) k_vcycle_cluster(const VcycleCoar
         cl.sync();
         apply_rows<float, DIM, P>(V->lv[li], RESID_SMOOTH, V->e[li], V->t[li], V->t[li], V->x[li], g, start, stride);
         cl.sync();
-        blocks_warps<float>(V->lv[li], V->t[li], V->x[li], g, start >> 5, stride >> 5, lane, rs);
+        blocks_warps<float>(V->lv[li], V->t[li], V->x[li], g, 0, V->lv[li].nblk, start >> 5, stride >> 5, lane, rs);
     }
 }
 
@@ -953,6 +983,19 @@ cudaError_t launch_blocks(const DevLevelT<T>& L, const T* r, T* x, double gamma,
 }
 
 template <typename T>
+cudaError_t launch_colour_smooth(const DevLevelT<T>& L, int64_t b_first, int64_t b_end, const int32_t* sg_row,
+                                 const T* sg_inv, int64_t ns, const T* r, T* x, const int* done, cudaStream_t s) {
+    const int64_t nb = b_end - b_first;
+    if (nb <= 0 && ns <= 0) return cudaSuccess;
+    const int64_t warps = ((ns + 31) >> 5) + std::max<int64_t>(nb, 0);
+    const int64_t g = (warps * 32 + TPB - 1) / TPB;
+    if (g > 65535LL * 16) return cudaErrorInvalidValue;
+    const size_t smem = (size_t)(TPB / 32) * L.max_block * sizeof(T);
+    launch_pdl(k_colour_smooth<T>, (unsigned)g, TPB, smem, s, L, b_first, b_end, sg_row, sg_inv, ns, r, x, done);
+    return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t launch_restrict(const DevLevelT<T>& F, const DevLevelT<T>& C, const T* rf, T* rc, T* xc, double gamma,
                             const int* done, cudaStream_t s) {
     const RowLaunch rl = row_launch(C.N);
@@ -1114,6 +1157,8 @@ cudaError_t launch_set_continue(PcgState* st, unsigned long long handle, cudaStr
                                          cudaStream_t);                                                            \
     template cudaError_t launch_scale_diag<T>(const DevLevelT<T>&, const T*, T*, double, const int*, cudaStream_t); \
     template cudaError_t launch_blocks<T>(const DevLevelT<T>&, const T*, T*, double, const int*, cudaStream_t);     \
+    template cudaError_t launch_colour_smooth<T>(const DevLevelT<T>&, int64_t, int64_t, const int32_t*, const T*,   \
+                                                 int64_t, const T*, T*, const int*, cudaStream_t);                 \
     template cudaError_t launch_restrict<T>(const DevLevelT<T>&, const DevLevelT<T>&, const T*, T*, T*, double,     \
                                             const int*, cudaStream_t);                                             \
     template cudaError_t launch_prolong<T>(const DevLevelT<T>&, const DevLevelT<T>&, const T*, T*, T*, const int*,  \

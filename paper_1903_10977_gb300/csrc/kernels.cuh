@@ -69,6 +69,12 @@ cudaError_t launch_scale_diag(const DevLevelT<T>& L, const T* r, T* x, double ga
 // x[idx_j] += gamma * A_j^{-1} r[idx_j] for every stored Schwarz block (atomic adds)
 template <typename T>
 cudaError_t launch_blocks(const DevLevelT<T>& L, const T* r, T* x, double gamma, const int* done, cudaStream_t s);
+// one colour of the multiplicative Schwarz sweep: x += P_j A_j^{-1} P_j^T r for the stored
+// blocks [b_first, b_end) and x_i += sg_inv[k] r_i for the one-function blocks
+// (i = sg_row[k], k < ns) of that colour
+template <typename T>
+cudaError_t launch_colour_smooth(const DevLevelT<T>& L, int64_t b_first, int64_t b_end, const int32_t* sg_row,
+                                 const T* sg_inv, int64_t ns, const T* r, T* x, const int* done, cudaStream_t s);
 // rc = R rf on the coarse rows; if xc != nullptr also xc = gamma * dinv_c .* rc
 template <typename T>
 cudaError_t launch_restrict(const DevLevelT<T>& F, const DevLevelT<T>& C, const T* rf, T* rc, T* xc, double gamma,

@@ -1290,11 +1290,36 @@ struct Builder {
         lv.blk_val.clear();
         lv.pruned = 0;
         lv.max_block = 1;
+        // block order: by owner (additive), or by the owner's colour and then by owner
+        // (multiplicative): colour = sum_k (j_k mod (p+1)) (p+1)^k, so that functions of
+        // equal colour have disjoint supports (Sec. 3.4)
+        std::vector<int64_t> order(nr);
+        std::iota(order.begin(), order.end(), 0);
+        std::vector<int> colour(nr, 0);
+        const int ncol = (dim == 2) ? (p + 1) * (p + 1) : (p + 1) * (p + 1) * (p + 1);
         for (int64_t t = 0; t < nr; ++t) {
+            int j[3];
+            unflat(rows[t], m, j);
+            colour[t] = (j[0] % (p + 1)) + (p + 1) * ((j[1] % (p + 1)) + (dim == 3 ? (p + 1) * (j[2] % (p + 1)) : 0));
+        }
+        const bool mult = pb.smoother == 1;
+        if (mult) std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return colour[a] < colour[b]; });
+        lv.ncolour = mult ? ncol : 0;
+        lv.blk_cptr.assign(mult ? ncol + 1 : 0, 0);
+        lv.sg_cptr.assign(mult ? ncol + 1 : 0, 0);
+        lv.sg_row.clear();
+        lv.sg_inv.clear();
+        for (int64_t ot = 0; ot < nr; ++ot) {
+            const int64_t t = order[ot];
             lv.pruned += nprune[t];
             const int nj = (int)bidx[t].size();
             if (nj == 1) {
                 lv.dinv[bidx[t][0]] += binv[t][0];
+                if (mult) {
+                    lv.sg_row.push_back(bidx[t][0]);
+                    lv.sg_inv.push_back(binv[t][0]);
+                    lv.sg_cptr[colour[t] + 1] = (int64_t)lv.sg_row.size();
+                }
                 continue;
             }
             lv.max_block = std::max<int64_t>(lv.max_block, nj);
@@ -1304,6 +1329,12 @@ struct Builder {
                 for (int a = 0; a < nj; ++a) lv.blk_val.push_back(binv[t][(size_t)a * nj + c]);
             lv.blk_ptr.push_back((int64_t)lv.blk_idx.size());
             lv.blk_vptr.push_back((int64_t)lv.blk_val.size());
+            if (mult) lv.blk_cptr[colour[t] + 1] = (int64_t)lv.blk_ptr.size() - 1;
+        }
+        // colours without blocks of one kind: ranges start where the previous one ends
+        for (int c = 1; c <= (mult ? ncol : 0); ++c) {
+            lv.blk_cptr[c] = std::max(lv.blk_cptr[c], lv.blk_cptr[c - 1]);
+            lv.sg_cptr[c] = std::max(lv.sg_cptr[c], lv.sg_cptr[c - 1]);
         }
         return true;
     }
@@ -1394,6 +1425,9 @@ struct Builder {
                         lv.f_blk_val[v0 + c * nj + a] =
                             (float)(lv.blk_val[v0 + c * nj + a] * dg[lv.blk_idx[s0 + a]] * dg[lv.blk_idx[s0 + c]]);
             }
+            lv.f_sg_inv.resize(lv.sg_inv.size());
+            for (size_t k = 0; k < lv.sg_inv.size(); ++k)
+                lv.f_sg_inv[k] = (float)(lv.sg_inv[k] * dg[lv.sg_row[k]] * dg[lv.sg_row[k]]);
             if (li == 0) {
                 const size_t nc = H.c_rows.size();
                 H.f_c_inv.assign(nc * nc, 0.0f);
@@ -1459,6 +1493,7 @@ bool build_hierarchy(const Problem& pb, Hierarchy& H, std::string& err) {
     if (pb.bc != 0 && pb.bc != 1) { err = "bc must be 0 (penalty) or 1 (Nitsche)"; return false; }
     if (!(pb.hi > pb.lo)) { err = "hi must exceed lo"; return false; }
     if (pb.precision != 0 && pb.precision != 1) { err = "precision must be 0 (FP64) or 1 (FP32 V-cycle)"; return false; }
+    if (pb.smoother != 0 && pb.smoother != 1) { err = "smoother must be 0 (additive) or 1 (multiplicative)"; return false; }
     double Nd = std::pow((double)(pb.n + pb.p), pb.dim);
     if (Nd > 2.0e9) { err = "grid too large for 32-bit row indices"; return false; }
     H = Hierarchy();
@@ -1466,6 +1501,7 @@ bool build_hierarchy(const Problem& pb, Hierarchy& H, std::string& err) {
     H.p = pb.p;
     H.L = pb.levels;
     H.bc = pb.bc;
+    H.smoother = pb.smoother;
     const int W = 2 * pb.p + 1;
     H.ncoef = (pb.dim == 2) ? W * W : W * W * W;
     H.gamma = pb.gamma > 0 ? pb.gamma : 1.0 / std::pow((double)(pb.p + 1), pb.dim);

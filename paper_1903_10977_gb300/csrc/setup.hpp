@@ -20,6 +20,7 @@ struct Problem {
     int n = 32, basis = 0, p = 2, levels = 3, depth = 0, bc = 1;
     double gamma = 0.0;
     int precision = 0;   // 0: FP64 V-cycle, 1: FP32 V-cycle (FP32 copies are built)
+    int smoother = 0;    // 0: additive Schwarz, 1: coloured multiplicative Schwarz
 };
 
 // Everything the kernels of one level need.  Row index = ix + m*(iy + m*iz).
@@ -40,6 +41,13 @@ struct LevelData {
     std::vector<int64_t> blk_vptr;     // [nblk+1] into blk_val
     std::vector<double> blk_val;       // A_j^{-1}, column-major n_j x n_j
     int64_t pruned = 0, max_block = 1;
+    // coloured multiplicative Schwarz (smoother 1): the stored blocks above are sorted by
+    // colour, blocks [blk_cptr[c], blk_cptr[c+1]) have colour c; the one-function blocks
+    // are listed per colour as (row, 1/A_kk) in [sg_cptr[c], sg_cptr[c+1])
+    int ncolour = 0;
+    std::vector<int64_t> blk_cptr, sg_cptr;
+    std::vector<int32_t> sg_row;
+    std::vector<double> sg_inv;
     // restriction to the next coarser level (levels >= 2), 1-D tables
     std::vector<int32_t> r_first;      // [m_c] first fine index of coarse function i
     std::vector<double> r_w;           // [m_c][p+2]
@@ -52,11 +60,11 @@ struct LevelData {
     // FP32 copies for the mixed-precision V-cycle, in Jacobi-scaled variables
     // (D = diag(A)^{1/2}): stored rows A_ij/(d_i d_j), block inverses d_a A_j^{-1}_ab d_b,
     // dinv d_i^2 / A_ii-sums, the scale s = 1/d and d itself; tables unscaled
-    std::vector<float> f_band_coef, f_K1, f_M1, f_dinv, f_blk_val, f_r_w, f_t_w, f_s, f_d;
+    std::vector<float> f_band_coef, f_K1, f_M1, f_dinv, f_blk_val, f_r_w, f_t_w, f_s, f_d, f_sg_inv;
 };
 
 struct Hierarchy {
-    int dim = 2, p = 2, L = 2, bc = 1, ncoef = 0;
+    int dim = 2, p = 2, L = 2, bc = 1, ncoef = 0, smoother = 0;
     double gamma = 0.0;
     std::vector<LevelData> lv;         // lv[0] = level 1 (coarsest) ... lv[L-1] = finest
     std::vector<double> b;             // finest right-hand side [N_L]

@@ -23,19 +23,25 @@ def layout_for(name: str, seed: int = 0, **overrides):
 
 @functools.lru_cache(maxsize=8)
 def oracle_for(name: str, seed: int = 0, n: int | None = None, levels: int | None = None, depth: int | None = None,
-               bc: int | None = None):
+               bc: int | None = None, smoother: str = "additive"):
     """(preset, layout, Discretization, Hierarchy) of the oracle for a workload (optionally resized)."""
     ov = {k: v for k, v in dict(n=n, levels=levels, depth=depth, bc=bc).items() if v is not None}
     pr, lay = layout_for(name, seed, **ov)
-    geom = G.Balls(lay.centers, lay.radii, lay.lo, lay.hi)
-    d = D.Discretization(geom, pr.basis, pr.degree, pr.n, pr.depth, pr.bc)
-    H = MG.Hierarchy(d, pr.levels)
+    d = _disc_for(name, seed, tuple(sorted(ov.items())))
+    H = MG.Hierarchy(d, pr.levels, smoother=smoother)
     return pr, lay, d, H
 
 
-def solver_for(lib, pr, lay, host_only=False):
+@functools.lru_cache(maxsize=4)
+def _disc_for(name: str, seed: int, ov: tuple):
+    pr, lay = layout_for(name, seed, **dict(ov))
+    geom = G.Balls(lay.centers, lay.radii, lay.lo, lay.hi)
+    return D.Discretization(geom, pr.basis, pr.degree, pr.n, pr.depth, pr.bc)
+
+
+def solver_for(lib, pr, lay, host_only=False, **kw):
     return lib.Solver(pr.dim, lay.centers, lay.radii, pr.n, pr.degree, pr.levels, pr.depth, pr.bc,
-                      basis=pr.basis, lo=lay.lo, hi=lay.hi, host_only=host_only)
+                      basis=pr.basis, lo=lay.lo, hi=lay.hi, host_only=host_only, **kw)
 
 
 def coef_rows(lev, p: int, dim: int) -> np.ndarray:

@@ -1,7 +1,7 @@
 """Parity at the full 512 x 512 workloads (10 discs, Lagrange p = 1 and B-splines p = 2, 3,
 6 levels), in the configuration the benchmark times: the C-ABI solve from x0 = 0 to a
 relative residual of 1e-8 through the captured solve graph, FP64 and mixed-precision
-V-cycle.
+V-cycle, additive Schwarz (and, for p = 2, coloured multiplicative Schwarz).
 
 The oracle cannot assemble and solve these systems in seconds, so the checks are of two
 kinds:
@@ -41,7 +41,7 @@ def host(t):
     return t.detach().cpu().numpy()
 
 
-@functools.lru_cache(maxsize=1)
+@functools.lru_cache(maxsize=2)
 def oracle_rows(name: str):
     """Oracle discretisation (no global assembly) and sampled rows: random active rows
     and rows whose support holds a cut element (the assembled boundary band)."""
@@ -60,13 +60,16 @@ def oracle_rows(name: str):
     return pr, lay, d, rows, d.assemble_rows(rows)
 
 
-@pytest.fixture(scope="module", params=[(n, p) for n in NAMES for p in (0, 1)],
-                ids=[f"{n}-{'fp64' if p == 0 else 'mixed'}" for n in NAMES for p in (0, 1)])
+FULL = [(n, p, 0) for n in NAMES for p in (0, 1)] + [("discs10_512_p2", p, 1) for p in (0, 1)]
+
+
+@pytest.fixture(scope="module", params=FULL,
+                ids=[f"{n}-{'fp64' if p == 0 else 'mixed'}{'-multiplicative' if m else ''}" for n, p, m in FULL])
 def full(request):
-    name, precision = request.param
+    name, precision, smoother = request.param
     pr, lay, d, rows, A_rows = oracle_rows(name)
     S = lib.Solver(pr.dim, lay.centers, lay.radii, pr.n, pr.degree, pr.levels, pr.depth, pr.bc, basis=pr.basis,
-                   lo=lay.lo, hi=lay.hi, precision=precision)
+                   lo=lay.lo, hi=lay.hi, precision=precision, smoother=smoother)
     yield precision, d, rows, A_rows, S
     S.close()
 
