@@ -30,6 +30,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "DOF/s to rel. residual 1e-8 (PCG+MG) vs plain FP64 GPU; HBM GB/s of roofline"
+# DRAM bytes of one finest-level FP64 apply launch on this workload, from one ncu capture
+# (dram__bytes_read.sum 4.907 MB + dram__bytes_write.sum 0); null it when the kernel changes
+APPLY_TRAFFIC_BYTES = 4.907008e6
 WORKLOAD = "poisson2d-512x512-10discs-bspline-p2-6levels-nitsche"
 PRESET = "discs10_512_p2"
 RTOL = 1e-8
@@ -208,6 +211,11 @@ def run_ours(args, rank, world, local_rank):
         t_dev, results = timed_solves(S, args.steps, args.warmup, "solve_mixed" if mixed else "solve_fp64")
     clocks = clk.summary()
     t64, res64 = (t_dev, results) if not mixed else timed_solves(S64, args.steps, args.warmup, "solve_fp64")
+    # the same solve with coloured multiplicative Schwarz (Sec. 3.4), beside the headline
+    SM = lib.Solver(pr.dim, lay.centers, lay.radii, pr.n, pr.degree, pr.levels, pr.depth, pr.bc, basis=pr.basis,
+                    precision=1 if mixed else 0, smoother=1)
+    t_mult, res_mult = timed_solves(SM, args.steps, args.warmup, "solve_multiplicative")
+    SM.close()
 
     # end to end: host (pinned) b in, host x out, through the C-ABI
     bh = torch.empty(n_grid, dtype=torch.float64, pin_memory=True)
@@ -269,11 +277,19 @@ def run_ours(args, rank, world, local_rank):
         "fp64": {"value": value64, "unit": "DOF/s", "ms_per_step": 1e3 * t64 / args.steps,
                  "iterations": res64[0]["iterations"], "true_rel_residual": res64[-1]["true_rel_residual"]},
         "speedup_vs_fp64": value / value64,
+        "multiplicative": {"value": total_units / t_mult, "unit": "DOF/s", "ms_per_step": 1e3 * t_mult / args.steps,
+                           "iterations": res_mult[0]["iterations"],
+                           "true_rel_residual": res_mult[-1]["true_rel_residual"],
+                           "gpu_launches_per_solve": int(res_mult[0]["kernel_launches"]),
+                           "smoother": "coloured multiplicative Schwarz, same precision as the headline"},
         "e2e": {"value": total_units / t_e2e, "unit": "DOF/s", "h2d_bytes_per_step": 8 * n_grid,
                 "d2h_bytes_per_step": 8 * n_grid},
         "gpu_launches": sum(int(r["kernel_launches"]) for r in results),
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                     "traffic": None, "kernel": "k_apply_tile2d<double> (finest-level operator apply, FP64)",
+                     "traffic": APPLY_TRAFFIC_BYTES,
+                     "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of this kernel on this "
+                                       "workload (profiles/k_apply_fp64_poisson2d_512_p2.md)",
+                     "kernel": "k_apply_tile2d<double> (finest-level operator apply, FP64)",
                      "peak_source": "derived: " + FP64_PEAK_NOTE, "flops_per_launch": flops,
                      "launch_ms": apply_ms},
         "clocks": clocks,
