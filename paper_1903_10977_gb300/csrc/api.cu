@@ -204,8 +204,9 @@ cudaError_t colour_step(LevelDev& F, int c, const T* r, T* x, const int* done, c
 // colour (so that line 5 falls out of the last one), restriction, coarse correction,
 // t -= A e (line 10), and the reversed sweep on the current residual (line 12).
 template <typename T>
-cudaError_t enqueue_vcycle_mult(imgm_handle* h, const T* r, T* z, const int* done, cudaStream_t s) {
+cudaError_t enqueue_vcycle_mult(imgm_handle* h, const T* r, T* z, const int*, cudaStream_t s) {
     using A = Acc<T>;
+    const int* done = nullptr;   // see enqueue_vcycle
     const int L = h->L;
     cudaError_t e;
     for (int li = L - 1; li >= 1; --li) {
@@ -244,7 +245,11 @@ cudaError_t enqueue_vcycle_mult(imgm_handle* h, const T* r, T* z, const int* don
 }
 
 template <typename T>
-cudaError_t enqueue_vcycle(imgm_handle* h, const T* r, T* z, const int* done, cudaStream_t s) {
+cudaError_t enqueue_vcycle(imgm_handle* h, const T* r, T* z, const int*, cudaStream_t s) {
+    // The V-cycle kernels are not told the convergence flag: they touch only the V-cycle's
+    // own vectors, so the one V-cycle after convergence is harmless, while reading the flag
+    // would put a dependent memory round trip in front of every one of them.
+    const int* done = nullptr;
     if (h->smoother == 1) return enqueue_vcycle_mult<T>(h, r, z, done, s);
     using A = Acc<T>;
     const int L = h->L;
@@ -270,7 +275,8 @@ cudaError_t enqueue_vcycle(imgm_handle* h, const T* r, T* z, const int* done, cu
             LevelDev& F = h->lv[li];
             LevelDev& C = h->lv[li - 1];
             T* xl = (li == L - 1) ? z : A::x(F);
-            if ((e = imgm::launch_prolong<T>(A::d(F), A::d(C), A::x(C), A::e(F), xl, done, s)) != cudaSuccess) return e;
+            if ((e = imgm::launch_prolong<T>(A::d(F), A::d(C), A::x(C), A::e(F), xl, done, s)) != cudaSuccess)
+                return e;
             if ((e = imgm::launch_apply<T>(A::d(F), imgm::RESID_SMOOTH, A::e(F), A::t(F), A::t(F), xl, g, done, s)) !=
                 cudaSuccess)
                 return e;

@@ -485,11 +485,8 @@ __device__ __forceinline__ void restrict_rows(const DevLevelT<T>& F, const DevLe
     const int mc = C.m, mf = F.m;
     const T* __restrict__ df = F.d;      // fine scale d (FP32 path) or nullptr
     for (int64_t i = start; i < C.N; i += stride) {
-        if (C.rowinfo[i] == -2) {
-            rc[i] = T(0);
-            if (xc) xc[i] = T(0);
-            continue;
-        }
+        // the row's activity is applied at the end, so that its load overlaps the others
+        const bool inactive = C.rowinfo[i] == -2;
         const int cx = (int)(i % mc), cy = (int)((i / mc) % mc), cz = (DIM == 3) ? (int)(i / ((int64_t)mc * mc)) : 0;
         const int fx = ro(F.r_first + cx), fy = ro(F.r_first + cy), fz = (DIM == 3) ? ro(F.r_first + cz) : 0;
         const T* wx = F.r_w + (int64_t)cx * P2;
@@ -510,6 +507,7 @@ __device__ __forceinline__ void restrict_rows(const DevLevelT<T>& F, const DevLe
             }
         }
         if (C.s) s *= ro(C.s + i);
+        if (inactive) s = T(0);
         rc[i] = s;
         if (xc) xc[i] = gamma * ro(C.dinv + i) * s;
     }
@@ -530,10 +528,7 @@ __device__ __forceinline__ void prolong_rows(const DevLevelT<T>& F, const DevLev
     const int mc = C.m, mf = F.m, TW = F.TW;
     const T* __restrict__ sc = C.s;      // coarse scale 1/d (FP32 path) or nullptr
     for (int64_t a = start; a < F.N; a += stride) {
-        if (F.rowinfo[a] == -2) {
-            e[a] = T(0);
-            continue;
-        }
+        const bool inactive = F.rowinfo[a] == -2;    // applied at the end (overlapping loads)
         const int ax = (int)(a % mf), ay = (int)((a / mf) % mf), az = (DIM == 3) ? (int)(a / ((int64_t)mf * mf)) : 0;
         const int cx = ro(F.t_first + ax), cy = ro(F.t_first + ay), cz = (DIM == 3) ? ro(F.t_first + az) : 0;
         const T* wx = F.t_w + (int64_t)ax * TW;
@@ -551,8 +546,9 @@ __device__ __forceinline__ void prolong_rows(const DevLevelT<T>& F, const DevLev
             }
         }
         if (F.d) s *= ro(F.d + a);
+        if (inactive) s = T(0);
         e[a] = s;
-        if (x) x[a] += s;
+        if (x && !inactive) x[a] += s;
     }
 }
 
