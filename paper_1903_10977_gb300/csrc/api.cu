@@ -540,6 +540,12 @@ int upload_level(imgm_handle* h, const imgm::LevelData& src, LevelDev& dst, int 
     d.r_w = rw;
     d.t_first = tf;
     d.t_w = tw;
+    {
+        unsigned int* ctr = nullptr;
+        CK(h->alloc(&ctr, 2), "alloc tile counter");
+        CK(cudaMemset(ctr, 0, 2 * sizeof(unsigned int)), "memset tile counter");
+        d.tile_ctr = ctr;
+    }
     CK(h->alloc(&dst.x, src.N), "alloc x");
     CK(h->alloc(&dst.r, src.N), "alloc r");
     CK(h->alloc(&dst.t, src.N), "alloc t");
@@ -560,6 +566,7 @@ int upload_level(imgm_handle* h, const imgm::LevelData& src, LevelDev& dst, int 
         f.max_block = d.max_block;
         f.TW = d.TW;
         f.rowinfo = d.rowinfo;
+        f.tile_ctr = d.tile_ctr;
         f.blk_ptr = d.blk_ptr;
         f.blk_idx = d.blk_idx;
         f.blk_vptr = d.blk_vptr;

@@ -275,15 +275,26 @@ __global__ void __launch_bounds__(TPB) k_apply_tile2d(DevLevelT<T> L, const T* _
     __shared__ T sv[TY][SX];
     __shared__ T tMy[TY][W], tKy[TY][W];   // 1-D rows of the tile's y indices
     __shared__ T tKx[TX][W], tMx[TX][W];   // 1-D rows of the tile's x indices
+    __shared__ int s_tile;
     if (done && *done) return;
     const int m = L.m;
     const bool scaled = L.s != nullptr;
     const int tiles_x = (m + TX - 1) / TX, tiles_y = (m + TY - 1) / TY;
     const int ntiles = tiles_x * tiles_y;
+    // FP64: a grid smaller than the tile count takes tiles from a counter, so that SMs that
+    // finish early take more (tiles along a cut cost more, and FP64 issue is per SM);
+    // FP32: one tile per block, no counter round trip
+    const bool dyn = sizeof(T) == 8 && MODE == APPLY && (int)gridDim.x < ntiles;
     double acc = 0.0;
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    for (int tb = blockIdx.x;; tb += gridDim.x) {
+        __syncthreads();   // the previous tile's smem reads (and s_tile) are done
+        if (dyn) {
+            if (threadIdx.x == 0) s_tile = (int)atomicAdd(&L.tile_ctr[0], 1u);
+            __syncthreads();
+        }
+        const int tile = dyn ? s_tile : tb;
+        if (tile >= ntiles) break;
         const int x0 = (tile % tiles_x) * TX, y0 = (tile / tiles_x) * TY;
-        __syncthreads();   // the previous tile's smem reads are done
         // one round of independent global loads: the x tile with its halo, the 1-D table
         // rows, and everything the outputs of this thread need that does not depend on x
         for (int k = threadIdx.x; k < SX * SY; k += TPB) {
@@ -365,6 +376,14 @@ __global__ void __launch_bounds__(TPB) k_apply_tile2d(DevLevelT<T> L, const T* _
                 if (MODE == RESID_SMOOTH) xs[i] = fmaT(gamma * dv[q], r, xv[q]);
             }
             if (DOT) acc = fma((double)sx[ly + P][lx + P], (double)y, acc);
+        }
+    }
+    if (dyn && threadIdx.x == 0) {
+        // every block has drawn past the end once; the last one re-arms the counter for the
+        // next launch (which starts only after this grid has completed)
+        if (atomicAdd(&L.tile_ctr[1], 1u) == gridDim.x - 1) {
+            L.tile_ctr[0] = 0u;
+            L.tile_ctr[1] = 0u;
         }
     }
     if (DOT) {
@@ -893,10 +912,20 @@ inline RowLaunch row_launch(int64_t n) {
 
 inline int tiles_2d(int m) { return ((m + TX - 1) / TX) * ((m + TY - 1) / TY); }
 
+// blocks of a tile launch: one per tile, except the FP64 operator apply (the CG's A p, and
+// the standalone apply), whose two blocks per SM draw tiles from the level's counter.  In
+// the residual modes of the V-cycle the extra loads per row favour more resident blocks.
+template <typename T>
+inline int tile_grid(int m, int mode) {
+    const int n = tiles_2d(m);
+    return (sizeof(T) == 8 && mode == APPLY) ? std::min(n, 2 * num_sms()) : n;
+}
+
 template <typename T, int P>
 cudaError_t launch_tile2d(const DevLevelT<T>& L, int mode, const T* x, const T* rin, T* out, T* xs, T gamma,
                           const int* done, cudaStream_t s) {
-    const int g = tiles_2d(L.m);
+    if (sizeof(T) == 8 && L.tile_ctr == nullptr) return cudaErrorInvalidValue;
+    const int g = tile_grid<T>(L.m, mode);
     if (mode == APPLY)
         launch_pdl(k_apply_tile2d<T, P, APPLY, false>, g, TPB, 0, s, L, x, rin, out, xs, gamma, done, nullptr, nullptr);
     else if (mode == RESID)
@@ -945,7 +974,8 @@ cudaError_t launch_apply(const DevLevelT<T>& L, int mode, const T* x, const T* r
 cudaError_t launch_apply_pq(const DevLevel& L, const double* p, double* q, double* partial, PcgState* st,
                             cudaStream_t s) {
     if (L.dim == 2) {
-        const int g = std::min(tiles_2d(L.m), reduction_blocks());
+        if (L.tile_ctr == nullptr) return cudaErrorInvalidValue;
+        const int g = std::min(tile_grid<double>(L.m, APPLY), reduction_blocks());
         if (L.p == 1)
             launch_pdl(k_apply_tile2d<double, 1, APPLY, true>, g, TPB, 0, s, L, p, nullptr, q, nullptr, 0.0, &st->done, partial, st);
         else if (L.p == 2)

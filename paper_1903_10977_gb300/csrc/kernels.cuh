@@ -37,6 +37,8 @@ struct DevLevelT {
     // s = 1/sqrt(A_ii), d = sqrt(A_ii) on active rows, 0 elsewhere
     const T* s = nullptr;
     const T* d = nullptr;
+    // work counter of the FP64 tile kernels ([0] next tile, [1] blocks done); zero between launches
+    unsigned int* tile_ctr = nullptr;
 };
 using DevLevel = DevLevelT<double>;
 
