@@ -173,6 +173,39 @@ int imgm_residual_norm2(imgm_handle* h, const double* dev_b, const double* dev_x
 int imgm_residual_norm2_noalloc(imgm_handle* h, const double* dev_b, const double* dev_x, double* dev_out,
                                 void* stream);
 
+/* ---- Solve contexts and batches -------------------------------------------------
+ * Several solves at once: the per-solve work of Sec. 3.2 (CG with the V-cycle of
+ * Algorithm 1) is unchanged; what is new is only how many run together.  The paper has
+ * no counterpart. */
+
+/* A second solve context for the problem of h: it shares h's host hierarchy and device
+ * tables (read-only; freed when the last of h and its clones is destroyed) and owns its
+ * own vectors, reduction scratch and solve graph, so that it can solve at the same time as
+ * h (another right-hand side of the same geometry).  Returns IMGM_ERR_INVALID for a
+ * host-only handle, IMGM_ERR_CUDA if device memory runs out. */
+int imgm_clone(const imgm_handle* h, imgm_handle** out);
+
+typedef struct imgm_batch imgm_batch;
+
+/* One CUDA graph that runs the CG solves of the n contexts hs[0..n) concurrently, each on
+ * its own branch with its own device-side convergence loop (conditional WHILE node), so
+ * that one graph launch solves them all.  The contexts must be distinct (clone a context
+ * for more right-hand sides of one problem), may belong to different problems of any
+ * size, and must outlive the batch.  Errors: IMGM_ERR_INVALID (empty list, repeated or
+ * host-only context), IMGM_ERR_CUDA (stream capture or instantiation failed; the message
+ * is in imgm_last_error(NULL)). */
+int imgm_batch_create(imgm_handle* const* hs, int n, imgm_batch** out);
+
+/* Solves hs[k] x_k = b_k for every k with one graph launch on `stream` (cudaStream_t, NULL
+ * for the default stream): dev_b[k] and dev_x[k] are device vectors of n_grid doubles of
+ * context k (x_k in: initial guess, out: solution), rtol and maxit as in imgm_pcg_solve.
+ * out[k] receives each solve's result.  Waits for the device.  Returns IMGM_OK when every
+ * solve converged, else the status of the first solve that did not. */
+int imgm_batch_solve(imgm_batch* b, const double* const* dev_b, double* const* dev_x, double rtol, int maxit,
+                     imgm_result* out, void* stream);
+
+void imgm_batch_destroy(imgm_batch* b);
+
 /* ---- Setup inspection (host only; no GPU needed) --------------------------------
  * imgm_setup_host builds the same hierarchy as imgm_setup without touching the GPU;
  * such a handle serves only the imgm_host_* calls below, imgm_levels,

@@ -78,6 +78,10 @@ _SIGS = {
     "imgm_host_restriction": (_I, [_H, _I, _P, _P]),
     "imgm_host_coarse_size": (_I, [_H, ctypes.POINTER(_I64)]),
     "imgm_host_coarse": (_I, [_H, _P, _P]),
+    "imgm_clone": (_I, [_H, ctypes.POINTER(_H)]),
+    "imgm_batch_create": (_I, [ctypes.POINTER(_H), _I, ctypes.POINTER(_P)]),
+    "imgm_batch_solve": (_I, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), _D, _I, ctypes.POINTER(Result), _P]),
+    "imgm_batch_destroy": (None, [_P]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -138,6 +142,18 @@ class Solver:
         if getattr(self, "_h", None):
             _lib.imgm_destroy(self._h)
             self._h = None
+
+    def clone(self) -> "Solver":
+        """Another solve context of the same problem (shared hierarchy, own vectors)."""
+        h = _H()
+        rc = _lib.imgm_clone(self._h, ctypes.byref(h))
+        if rc != IMGM_OK:
+            raise ImgmError(f"clone failed ({ERRORS.get(rc, rc)}): {_lib.imgm_last_error(None).decode()}")
+        c = object.__new__(Solver)
+        c.__dict__.update({k: v for k, v in self.__dict__.items() if k != "_h"})
+        c._h = h
+        c._parent = self              # keeps the Python object of the source alive as well
+        return c
 
     def __del__(self):
         try:
@@ -301,3 +317,47 @@ class Solver:
         self._check(_lib.imgm_host_coarse(self._h, rows.ctypes.data_as(ctypes.c_void_p),
                                           inv.ctypes.data_as(ctypes.c_void_p)))
         return rows, inv
+
+
+def _result_dict(res) -> dict:
+    return {"iterations": res.iterations, "status": res.status, "rel_residual": res.rel_residual,
+            "true_rel_residual": res.true_rel_residual, "kernel_launches": res.kernel_launches}
+
+
+class Batch:
+    """CG solves of several contexts (Solver objects, distinct; clones for more right-hand
+    sides of one problem) run concurrently by one CUDA graph launch."""
+
+    def __init__(self, solvers):
+        self.solvers = list(solvers)
+        arr = (_H * len(self.solvers))(*[s._h for s in self.solvers])
+        b = _P()
+        rc = _lib.imgm_batch_create(arr, len(self.solvers), ctypes.byref(b))
+        if rc != IMGM_OK:
+            raise ImgmError(f"batch failed ({ERRORS.get(rc, rc)}): {_lib.imgm_last_error(None).decode()}")
+        self._b = b
+
+    def solve(self, bs, xs=None, rtol=1e-8, maxit=1000, stream=None):
+        """Solves solver[k] x_k = bs[k] for all k (xs: initial guesses, zeros when None);
+        returns (xs, list of result dicts)."""
+        import torch
+        n = len(self.solvers)
+        xs = [torch.zeros_like(b) for b in bs] if xs is None else xs
+        pb = (_P * n)(*[_ptr(b).value for b in bs])
+        px = (_P * n)(*[_ptr(x).value for x in xs])
+        res = (Result * n)()
+        rc = _lib.imgm_batch_solve(self._b, pb, px, rtol, maxit, res, _stream(stream))
+        if rc < 0:
+            raise ImgmError(f"{ERRORS.get(rc, rc)}: {_lib.imgm_last_error(None).decode()}")
+        return xs, [_result_dict(r) for r in res]
+
+    def close(self):
+        if getattr(self, "_b", None):
+            _lib.imgm_batch_destroy(self._b)
+            self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

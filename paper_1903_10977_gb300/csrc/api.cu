@@ -71,15 +71,28 @@ struct Acc<float> {
 
 }  // namespace
 
-struct imgm_handle {
+// What every solve context of one problem shares: the host hierarchy and the device
+// tables (operator rows, blocks, transfers, coarse inverse, right-hand side).  Freed with
+// the last handle that refers to it.
+struct SharedData {
     imgm::Hierarchy H;
+    std::vector<void*> allocs;
+    ~SharedData() {
+        for (void* v : allocs) cudaFree(v);
+    }
+};
+
+struct imgm_handle {
+    std::shared_ptr<SharedData> sh;
+    imgm::Hierarchy& H;
+    explicit imgm_handle(std::shared_ptr<SharedData> s) : sh(std::move(s)), H(sh->H) {}
     bool on_device = false;
     int dim = 2, p = 2, L = 2;
     double gamma = 0.0;
     int smoother = 0;          // 0 additive, 1 coloured multiplicative Schwarz
     double gamma_diag = 0.0;   // factor of the diagonal start x = gamma_diag dinv r (0: x starts at 0)
     std::vector<LevelDev> lv;          // index 0 = level 1
-    std::vector<void*> allocs;
+    std::vector<void*> allocs;         // this context's vectors and scratch
     int32_t* c_rows = nullptr;
     double* c_inv = nullptr;
     float* f_c_inv = nullptr;
@@ -115,10 +128,15 @@ struct imgm_handle {
         *p = (T*)v;
         return cudaSuccess;
     }
+    // read-only tables: shared by every context of the problem
     template <class T>
     cudaError_t upload(T** p, const std::vector<T>& h) {
-        cudaError_t e = alloc(p, h.size());
-        if (e != cudaSuccess || h.empty()) return e;
+        void* v = nullptr;
+        cudaError_t e = cudaMalloc(&v, h.size() * sizeof(T) > 0 ? h.size() * sizeof(T) : 16);
+        if (e != cudaSuccess) return e;
+        sh->allocs.push_back(v);
+        *p = (T*)v;
+        if (h.empty()) return cudaSuccess;
         return cudaMemcpy(*p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice);
     }
     ~imgm_handle() {
@@ -374,6 +392,57 @@ cudaError_t enqueue_solve_finish(imgm_handle* h, cudaStream_t s) {
 }
 
 // Builds the solve graph: start -> while (!done) { iteration } -> finish.
+// Enqueues the whole solve of h on the capturing stream s: the start, a conditional WHILE
+// node whose body is one CG iteration (captured into the node's graph on a side stream),
+// and the finish.  Records the kernel counts of the three parts in h->graph_kernels.
+cudaError_t capture_solve(imgm_handle* h, cudaStream_t s) {
+    cudaStream_t body_stream = nullptr;
+    cudaError_t ce = cudaStreamCreateWithFlags(&body_stream, cudaStreamNonBlocking);
+    if (ce != cudaSuccess) return ce;
+    int64_t c0 = imgm::launch_count();
+    ce = enqueue_solve_start(h, s);
+    cudaGraph_t cg = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t ndeps = 0;
+    cudaStreamCaptureStatus cs;
+    cudaGraphConditionalHandle handle = 0;
+    cudaGraphNode_t cnode = nullptr;
+    alignas(cudaGraphNodeParams) unsigned char cp_storage[sizeof(cudaGraphNodeParams)];
+    std::memset(cp_storage, 0, sizeof(cp_storage));
+    cudaGraphNodeParams& cp = *reinterpret_cast<cudaGraphNodeParams*>(cp_storage);
+    if (ce == cudaSuccess) ce = cudaStreamGetCaptureInfo(s, &cs, nullptr, &cg, &deps, nullptr, &ndeps);
+    if (ce == cudaSuccess) ce = cudaGraphConditionalHandleCreate(&handle, cg, 0, cudaGraphCondAssignDefault);
+    if (ce == cudaSuccess) ce = imgm::launch_set_continue(h->st, (unsigned long long)handle, s);
+    if (ce == cudaSuccess) ce = cudaStreamGetCaptureInfo(s, &cs, nullptr, &cg, &deps, nullptr, &ndeps);
+    if (ce == cudaSuccess) {
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = handle;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        ce = cudaGraphAddNode(&cnode, cg, deps, nullptr, ndeps, &cp);
+    }
+    if (ce == cudaSuccess) ce = cudaStreamUpdateCaptureDependencies(s, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies);
+    if (ce == cudaSuccess) {
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        ce = cudaStreamBeginCaptureToGraph(body_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+        if (ce == cudaSuccess) {
+            h->graph_kernels[0] = imgm::launch_count() - c0;
+            c0 = imgm::launch_count();
+            cudaError_t be = enqueue_iteration(h, body_stream);
+            if (be == cudaSuccess) be = imgm::launch_set_continue(h->st, (unsigned long long)handle, body_stream);
+            h->graph_kernels[1] = imgm::launch_count() - c0;
+            c0 = imgm::launch_count();
+            cudaGraph_t outb = nullptr;
+            cudaError_t ee = cudaStreamEndCapture(body_stream, &outb);
+            ce = (be != cudaSuccess) ? be : ee;
+        }
+    }
+    if (ce == cudaSuccess) ce = enqueue_solve_finish(h, s);
+    h->graph_kernels[2] = imgm::launch_count() - c0;
+    cudaStreamDestroy(body_stream);
+    return ce;
+}
+
 // Captures start, conditional WHILE loop over one iteration, and finish into h->exec.
 // Capture runs on a stream of the handle (capturing the legacy default stream is not
 // allowed); the graph is then launched on the caller's stream.
@@ -381,51 +450,10 @@ cudaError_t build_solve_graph(imgm_handle* h) {
     cudaError_t e = cudaSuccess;
     if (!h->capture && (e = cudaStreamCreateWithFlags(&h->capture, cudaStreamNonBlocking)) != cudaSuccess) return e;
     cudaStream_t s = h->capture;
-    cudaStream_t body_stream = nullptr;
-    if ((e = cudaStreamCreateWithFlags(&body_stream, cudaStreamNonBlocking)) != cudaSuccess) return e;
     cudaGraph_t g = nullptr;
     do {
         if ((e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) break;
-        int64_t c0 = imgm::launch_count();
-        cudaError_t ce = enqueue_solve_start(h, s);
-        cudaGraph_t cg = nullptr;
-        const cudaGraphNode_t* deps = nullptr;
-        size_t ndeps = 0;
-        cudaStreamCaptureStatus cs;
-        cudaGraphConditionalHandle handle = 0;
-        cudaGraphNode_t cnode = nullptr;
-        alignas(cudaGraphNodeParams) unsigned char cp_storage[sizeof(cudaGraphNodeParams)];
-        std::memset(cp_storage, 0, sizeof(cp_storage));
-        cudaGraphNodeParams& cp = *reinterpret_cast<cudaGraphNodeParams*>(cp_storage);
-        if (ce == cudaSuccess) ce = cudaStreamGetCaptureInfo(s, &cs, nullptr, &cg, &deps, nullptr, &ndeps);
-        if (ce == cudaSuccess) ce = cudaGraphConditionalHandleCreate(&handle, cg, 0, cudaGraphCondAssignDefault);
-        if (ce == cudaSuccess) ce = imgm::launch_set_continue(h->st, (unsigned long long)handle, s);
-        if (ce == cudaSuccess) ce = cudaStreamGetCaptureInfo(s, &cs, nullptr, &cg, &deps, nullptr, &ndeps);
-        if (ce == cudaSuccess) {
-            cp.type = cudaGraphNodeTypeConditional;
-            cp.conditional.handle = handle;
-            cp.conditional.type = cudaGraphCondTypeWhile;
-            cp.conditional.size = 1;
-            ce = cudaGraphAddNode(&cnode, cg, deps, nullptr, ndeps, &cp);
-        }
-        if (ce == cudaSuccess) ce = cudaStreamUpdateCaptureDependencies(s, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies);
-        if (ce == cudaSuccess) {
-            cudaGraph_t body = cp.conditional.phGraph_out[0];
-            ce = cudaStreamBeginCaptureToGraph(body_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
-            if (ce == cudaSuccess) {
-                h->graph_kernels[0] = imgm::launch_count() - c0;
-                c0 = imgm::launch_count();
-                cudaError_t be = enqueue_iteration(h, body_stream);
-                if (be == cudaSuccess) be = imgm::launch_set_continue(h->st, (unsigned long long)handle, body_stream);
-                h->graph_kernels[1] = imgm::launch_count() - c0;
-                c0 = imgm::launch_count();
-                cudaGraph_t outb = nullptr;
-                cudaError_t ee = cudaStreamEndCapture(body_stream, &outb);
-                ce = (be != cudaSuccess) ? be : ee;
-            }
-        }
-        if (ce == cudaSuccess) ce = enqueue_solve_finish(h, s);
-        h->graph_kernels[2] = imgm::launch_count() - c0;
+        const cudaError_t ce = capture_solve(h, s);
         e = cudaStreamEndCapture(s, &g);
         if (ce != cudaSuccess) e = ce;
         if (e != cudaSuccess) break;
@@ -437,7 +465,6 @@ cudaError_t build_solve_graph(imgm_handle* h) {
         cudaGetLastError();
     }
     h->graph = g;
-    cudaStreamDestroy(body_stream);
     return e;
 }
 
@@ -498,6 +525,93 @@ cudaError_t autotune_cluster(imgm_handle* h, imgm::VcycleCoarse& vc) {
     return e;
 }
 
+// one level's vectors and tile counter: per solve context
+int alloc_level_vectors(imgm_handle* h, LevelDev& dst) {
+    const int64_t N = dst.d.N;
+    unsigned int* ctr = nullptr;
+    CK(h->alloc(&ctr, 2), "alloc tile counter");
+    CK(cudaMemset(ctr, 0, 2 * sizeof(unsigned int)), "memset tile counter");
+    dst.d.tile_ctr = ctr;
+    dst.fd.tile_ctr = ctr;
+    CK(h->alloc(&dst.x, N), "alloc x");
+    CK(h->alloc(&dst.r, N), "alloc r");
+    CK(h->alloc(&dst.t, N), "alloc t");
+    CK(h->alloc(&dst.e, N), "alloc e");
+    CK(cudaMemset(dst.x, 0, N * sizeof(double)), "memset");
+    CK(cudaMemset(dst.r, 0, N * sizeof(double)), "memset");
+    CK(cudaMemset(dst.t, 0, N * sizeof(double)), "memset");
+    CK(cudaMemset(dst.e, 0, N * sizeof(double)), "memset");
+    if (h->precision == 1) {
+        CK(h->alloc(&dst.fx, N), "alloc x32");
+        CK(h->alloc(&dst.fr, N), "alloc r32");
+        CK(h->alloc(&dst.ft, N), "alloc t32");
+        CK(h->alloc(&dst.fe, N), "alloc e32");
+        CK(cudaMemset(dst.fx, 0, N * sizeof(float)), "memset");
+        CK(cudaMemset(dst.fr, 0, N * sizeof(float)), "memset");
+        CK(cudaMemset(dst.ft, 0, N * sizeof(float)), "memset");
+        CK(cudaMemset(dst.fe, 0, N * sizeof(float)), "memset");
+    }
+    return IMGM_OK;
+}
+
+// The FP32 V-cycle's coarse levels as one cluster launch: the level table of this
+// context (its vectors) in device memory.
+int alloc_cluster_table(imgm_handle* h, int top) {
+    imgm::VcycleCoarse vc{};
+    vc.top = top;
+    int mb = 1;
+    for (int li = 0; li <= h->L - 2 && li < imgm::VCYCLE_MAX_LEVELS; ++li) {
+        LevelDev& Ld = h->lv[li];
+        vc.lv[li] = Ld.fd;
+        vc.x[li] = Ld.fx;
+        vc.r[li] = Ld.fr;
+        vc.t[li] = Ld.ft;
+        vc.e[li] = Ld.fe;
+        if (li >= 1 && li <= top) mb = std::max(mb, (int)Ld.fd.max_block);
+    }
+    vc.c_rows = h->c_rows;
+    vc.c_inv = h->f_c_inv;
+    vc.nc = h->nc;
+    vc.max_block = mb;
+    vc.gamma = h->gamma;
+    if (!h->vc) CK(h->alloc(&h->vc, 1), "alloc cluster levels");
+    CK(cudaMemcpy(h->vc, &vc, sizeof(vc), cudaMemcpyHostToDevice), "upload cluster levels");
+    h->vc_top = top;
+    h->vc_max_block = mb;
+    h->vc_smem = imgm::vcycle_cluster_smem(mb);
+    return IMGM_OK;
+}
+
+// Everything a solve context owns besides the level vectors: FP32 finest vectors, CG
+// vectors, reduction scratch, state and history.
+int alloc_context(imgm_handle* h) {
+    const int64_t N = h->lv[h->L - 1].d.N;
+    if (h->precision == 1) {
+        CK(h->alloc(&h->zf, N), "alloc");
+        CK(h->alloc(&h->rf, N), "alloc");
+        CK(h->alloc(&h->zpf, N), "alloc");
+        CK(cudaMemset(h->zf, 0, N * sizeof(float)), "memset");
+        CK(cudaMemset(h->rf, 0, N * sizeof(float)), "memset");
+        CK(cudaMemset(h->zpf, 0, N * sizeof(float)), "memset");
+    }
+    CK(h->alloc(&h->cx, N), "alloc");
+    CK(h->alloc(&h->cr, N), "alloc");
+    CK(h->alloc(&h->cp, N), "alloc");
+    CK(h->alloc(&h->cq, N), "alloc");
+    CK(h->alloc(&h->cz, N), "alloc");
+    CK(h->alloc(&h->cb, N), "alloc");
+    CK(h->alloc(&h->partial, 2 * (size_t)imgm::reduction_blocks()), "alloc");
+    CK(h->alloc(&h->st, 1), "alloc");
+    CK(cudaMemset(h->st, 0, sizeof(PcgState)), "memset");
+    CK(h->alloc(&h->partial_aux, 2 * (size_t)imgm::reduction_blocks()), "alloc");
+    CK(h->alloc(&h->st_aux, 1), "alloc");
+    CK(cudaMemset(h->st_aux, 0, sizeof(PcgState)), "memset");
+    CK(cudaMemset(h->cz, 0, N * sizeof(double)), "memset");
+    h->hist_cap = 100001;
+    CK(h->alloc(&h->hist, (size_t)h->hist_cap), "alloc");
+    return IMGM_OK;
+}
+
 int upload_level(imgm_handle* h, const imgm::LevelData& src, LevelDev& dst, int level_index) {
     const imgm::Hierarchy& H = h->H;
     DevLevel& d = dst.d;
@@ -540,20 +654,6 @@ int upload_level(imgm_handle* h, const imgm::LevelData& src, LevelDev& dst, int 
     d.r_w = rw;
     d.t_first = tf;
     d.t_w = tw;
-    {
-        unsigned int* ctr = nullptr;
-        CK(h->alloc(&ctr, 2), "alloc tile counter");
-        CK(cudaMemset(ctr, 0, 2 * sizeof(unsigned int)), "memset tile counter");
-        d.tile_ctr = ctr;
-    }
-    CK(h->alloc(&dst.x, src.N), "alloc x");
-    CK(h->alloc(&dst.r, src.N), "alloc r");
-    CK(h->alloc(&dst.t, src.N), "alloc t");
-    CK(h->alloc(&dst.e, src.N), "alloc e");
-    CK(cudaMemset(dst.x, 0, src.N * sizeof(double)), "memset");
-    CK(cudaMemset(dst.r, 0, src.N * sizeof(double)), "memset");
-    CK(cudaMemset(dst.t, 0, src.N * sizeof(double)), "memset");
-    CK(cudaMemset(dst.e, 0, src.N * sizeof(double)), "memset");
     if (h->precision == 1) {
         imgm::DevLevelT<float>& f = dst.fd;
         f.dim = d.dim;
@@ -566,7 +666,6 @@ int upload_level(imgm_handle* h, const imgm::LevelData& src, LevelDev& dst, int 
         f.max_block = d.max_block;
         f.TW = d.TW;
         f.rowinfo = d.rowinfo;
-        f.tile_ctr = d.tile_ctr;
         f.blk_ptr = d.blk_ptr;
         f.blk_idx = d.blk_idx;
         f.blk_vptr = d.blk_vptr;
@@ -591,14 +690,6 @@ int upload_level(imgm_handle* h, const imgm::LevelData& src, LevelDev& dst, int 
         f.t_w = twf;
         f.s = sf;
         f.d = df;
-        CK(h->alloc(&dst.fx, src.N), "alloc x32");
-        CK(h->alloc(&dst.fr, src.N), "alloc r32");
-        CK(h->alloc(&dst.ft, src.N), "alloc t32");
-        CK(h->alloc(&dst.fe, src.N), "alloc e32");
-        CK(cudaMemset(dst.fx, 0, src.N * sizeof(float)), "memset");
-        CK(cudaMemset(dst.fr, 0, src.N * sizeof(float)), "memset");
-        CK(cudaMemset(dst.ft, 0, src.N * sizeof(float)), "memset");
-        CK(cudaMemset(dst.fe, 0, src.N * sizeof(float)), "memset");
     }
     dst.ncolour = src.ncolour;
     dst.blk_cptr = src.blk_cptr;
@@ -666,7 +757,7 @@ int imgm_setup(const imgm_geometry* geom, const imgm_config* cfg, imgm_handle** 
     *out = nullptr;
     int v = validate_inputs(geom, cfg);
     if (v != IMGM_OK) return v;
-    std::unique_ptr<imgm_handle> h(new (std::nothrow) imgm_handle());
+    std::unique_ptr<imgm_handle> h(new (std::nothrow) imgm_handle(std::make_shared<SharedData>()));
     if (!h) return fail(nullptr, IMGM_ERR_INVALID, "out of host memory");
     imgm::Problem pb = make_problem(geom, cfg);
     std::string err;
@@ -687,6 +778,7 @@ int imgm_setup(const imgm_geometry* geom, const imgm_config* cfg, imgm_handle** 
     hp->lv.resize(hp->L);
     for (int li = 0; li < hp->L; ++li) {
         int rc = upload_level(hp, hp->H.lv[li], hp->lv[li], li);
+        if (rc == IMGM_OK) rc = alloc_level_vectors(hp, hp->lv[li]);
         if (rc != IMGM_OK) {
             g_setup_error = hp->err;
             return rc;
@@ -697,63 +789,26 @@ int imgm_setup(const imgm_geometry* geom, const imgm_config* cfg, imgm_handle** 
         CK(h->upload(&h->c_rows, h->H.c_rows), "upload coarse rows");
         CK(h->upload(&h->c_inv, h->H.c_inv), "upload coarse inverse");
         h->nc = (int)h->H.c_rows.size();
-        if (h->precision == 1) {
-            CK(h->upload(&h->f_c_inv, h->H.f_c_inv), "upload fp32 coarse inverse");
-            {
-                const int64_t Nf0 = h->lv[h->L - 1].d.N;
-                CK(h->alloc(&h->zf, Nf0), "alloc");
-                CK(h->alloc(&h->rf, Nf0), "alloc");
-                CK(h->alloc(&h->zpf, Nf0), "alloc");
-                CK(cudaMemset(h->zf, 0, Nf0 * sizeof(float)), "memset");
-                CK(cudaMemset(h->rf, 0, Nf0 * sizeof(float)), "memset");
-                CK(cudaMemset(h->zpf, 0, Nf0 * sizeof(float)), "memset");
-            }
-            // the coarse levels of the FP32 V-cycle as one cluster launch, when the device has clusters
-            if (h->smoother == 0 && h->L >= 2 && h->L - 1 <= imgm::VCYCLE_MAX_LEVELS &&
-                imgm::vcycle_cluster_size() > 0) {
-                imgm::VcycleCoarse vc{};
-                vc.top = h->L - 2;
-                int mb = 1;
-                for (int li = 0; li <= vc.top; ++li) {
-                    LevelDev& Ld = h->lv[li];
-                    vc.lv[li] = Ld.fd;
-                    vc.x[li] = Ld.fx;
-                    vc.r[li] = Ld.fr;
-                    vc.t[li] = Ld.ft;
-                    vc.e[li] = Ld.fe;
-                    if (li >= 1) mb = std::max(mb, (int)Ld.fd.max_block);
-                }
-                vc.c_rows = h->c_rows;
-                vc.c_inv = h->f_c_inv;
-                vc.nc = h->nc;
-                vc.max_block = mb;
-                vc.gamma = h->gamma;
-                CK(h->alloc(&h->vc, 1), "alloc cluster levels");
-                CK(cudaMemcpy(h->vc, &vc, sizeof(vc), cudaMemcpyHostToDevice), "upload cluster levels");
-                h->vc_top = vc.top;
-                h->vc_max_block = mb;
-                h->vc_smem = imgm::vcycle_cluster_smem(mb);
-                CK(autotune_cluster(h, vc), "cluster autotune");
-            }
-        }
-        h->nc = (int)h->H.c_rows.size();
+        if (h->precision == 1) CK(h->upload(&h->f_c_inv, h->H.f_c_inv), "upload fp32 coarse inverse");
         CK(h->upload(&h->b, h->H.b), "upload rhs");
-        const int64_t N = h->lv[h->L - 1].d.N;
-        CK(h->alloc(&h->cx, N), "alloc");
-        CK(h->alloc(&h->cr, N), "alloc");
-        CK(h->alloc(&h->cp, N), "alloc");
-        CK(h->alloc(&h->cq, N), "alloc");
-        CK(h->alloc(&h->cz, N), "alloc");
-        CK(h->alloc(&h->cb, N), "alloc");
-        CK(h->alloc(&h->partial, 2 * (size_t)imgm::reduction_blocks()), "alloc");
-        CK(h->alloc(&h->st, 1), "alloc");
-        CK(cudaMemset(h->st, 0, sizeof(PcgState)), "memset");
-        CK(h->alloc(&h->partial_aux, 2 * (size_t)imgm::reduction_blocks()), "alloc");
-        CK(h->alloc(&h->st_aux, 1), "alloc");
-        CK(cudaMemset(h->st_aux, 0, sizeof(PcgState)), "memset");
-        CK(cudaMemset(h->cz, 0, N * sizeof(double)), "memset");
-        h->hist_cap = 100001;
-        CK(h->alloc(&h->hist, (size_t)h->hist_cap), "alloc");
+        int rc = alloc_context(h);
+        if (rc != IMGM_OK) {
+            g_setup_error = h->err;
+            return rc;
+        }
+        // the coarse levels of the FP32 V-cycle as one cluster launch, when the device has
+        // clusters and the autotuner finds it faster
+        if (h->precision == 1 && h->smoother == 0 && h->L >= 2 && h->L - 1 <= imgm::VCYCLE_MAX_LEVELS &&
+            imgm::vcycle_cluster_size() > 0) {
+            rc = alloc_cluster_table(h, h->L - 2);
+            if (rc != IMGM_OK) {
+                g_setup_error = h->err;
+                return rc;
+            }
+            imgm::VcycleCoarse vc{};
+            CK(cudaMemcpy(&vc, h->vc, sizeof(vc), cudaMemcpyDeviceToHost), "read cluster levels");
+            CK(autotune_cluster(h, vc), "cluster autotune");
+        }
         CK(cudaDeviceSynchronize(), "setup sync");
     }
     hp->on_device = true;
@@ -1019,7 +1074,7 @@ int imgm_setup_host(const imgm_geometry* geom, const imgm_config* cfg, imgm_hand
     *out = nullptr;
     int v = validate_inputs(geom, cfg);
     if (v != IMGM_OK) return v;
-    std::unique_ptr<imgm_handle> h(new (std::nothrow) imgm_handle());
+    std::unique_ptr<imgm_handle> h(new (std::nothrow) imgm_handle(std::make_shared<SharedData>()));
     if (!h) return fail(nullptr, IMGM_ERR_INVALID, "out of host memory");
     imgm::Problem pb = make_problem(geom, cfg);
     std::string err;
@@ -1135,3 +1190,179 @@ int imgm_host_coarse(const imgm_handle* h, int32_t* rows, double* inv) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------------
+// Solve contexts and batches
+
+int imgm_clone(const imgm_handle* src, imgm_handle** out) {
+    if (!out) return fail(nullptr, IMGM_ERR_INVALID, "null output handle");
+    *out = nullptr;
+    if (!src || !src->on_device) return fail(nullptr, IMGM_ERR_INVALID, "handle has no device data");
+    std::unique_ptr<imgm_handle> h(new (std::nothrow) imgm_handle(src->sh));
+    if (!h) return fail(nullptr, IMGM_ERR_INVALID, "out of host memory");
+    imgm_handle* hp = h.get();
+    hp->dim = src->dim;
+    hp->p = src->p;
+    hp->L = src->L;
+    hp->gamma = src->gamma;
+    hp->smoother = src->smoother;
+    hp->gamma_diag = src->gamma_diag;
+    hp->precision = src->precision;
+    hp->c_rows = src->c_rows;
+    hp->c_inv = src->c_inv;
+    hp->f_c_inv = src->f_c_inv;
+    hp->nc = src->nc;
+    hp->b = src->b;
+    hp->lv = src->lv;          // level tables shared; vectors replaced below
+    for (LevelDev& L : hp->lv) {
+        int rc = alloc_level_vectors(hp, L);
+        if (rc != IMGM_OK) {
+            g_setup_error = hp->err;
+            return rc;
+        }
+    }
+    int rc = alloc_context(hp);
+    if (rc == IMGM_OK && src->vc_top >= 0) rc = alloc_cluster_table(hp, src->vc_top);
+    if (rc != IMGM_OK) {
+        g_setup_error = hp->err;
+        return rc;
+    }
+    hp->vc_top = src->vc_top;
+    {
+        imgm_handle* h = hp;
+        CK(cudaDeviceSynchronize(), "clone sync");
+    }
+    hp->on_device = true;
+    *out = h.release();
+    return IMGM_OK;
+}
+
+struct imgm_batch {
+    std::vector<imgm_handle*> hs;
+    std::vector<cudaStream_t> streams;   // one capture stream per solve (the branches)
+    std::vector<cudaEvent_t> events;
+    cudaStream_t root = nullptr;
+    cudaEvent_t fork = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<int64_t> kernels;        // per solve: start, body, finish kernel counts
+    std::string err;
+    ~imgm_batch() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        for (cudaEvent_t e : events) cudaEventDestroy(e);
+        for (cudaStream_t s : streams) cudaStreamDestroy(s);
+        if (fork) cudaEventDestroy(fork);
+        if (root) cudaStreamDestroy(root);
+    }
+};
+
+namespace {
+int batch_fail(imgm_batch* b, int code, const std::string& msg) {
+    if (b) b->err = msg;
+    g_setup_error = msg;
+    return code;
+}
+}  // namespace
+
+int imgm_batch_create(imgm_handle* const* hs, int n, imgm_batch** out) {
+    if (!out) return batch_fail(nullptr, IMGM_ERR_INVALID, "null output batch");
+    *out = nullptr;
+    if (!hs || n <= 0) return batch_fail(nullptr, IMGM_ERR_INVALID, "empty batch");
+    for (int k = 0; k < n; ++k) {
+        if (!hs[k] || !hs[k]->on_device) return batch_fail(nullptr, IMGM_ERR_INVALID, "handle has no device data");
+        for (int j = 0; j < k; ++j)
+            if (hs[j] == hs[k])
+                return batch_fail(nullptr, IMGM_ERR_INVALID, "a context appears twice (use imgm_clone for more right-hand sides)");
+    }
+    std::unique_ptr<imgm_batch> b(new (std::nothrow) imgm_batch());
+    if (!b) return batch_fail(nullptr, IMGM_ERR_INVALID, "out of host memory");
+    b->hs.assign(hs, hs + n);
+    b->streams.assign(n, nullptr);
+    b->events.assign(n, nullptr);
+    b->kernels.assign(3 * (size_t)n, 0);
+    cudaError_t e = cudaStreamCreateWithFlags(&b->root, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+    for (int k = 0; k < n && e == cudaSuccess; ++k) {
+        e = cudaStreamCreateWithFlags(&b->streams[k], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->events[k], cudaEventDisableTiming);
+    }
+    if (e != cudaSuccess) return batch_fail(nullptr, IMGM_ERR_CUDA, std::string("batch streams: ") + cudaGetErrorString(e));
+    // one graph: fork from the root stream, every solve on its own branch (each with its own
+    // device-side convergence loop), join back on the root
+    cudaGraph_t g = nullptr;
+    do {
+        if ((e = cudaStreamBeginCapture(b->root, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) break;
+        cudaError_t ce = cudaEventRecord(b->fork, b->root);
+        for (int k = 0; k < n && ce == cudaSuccess; ++k) {
+            ce = cudaStreamWaitEvent(b->streams[k], b->fork, 0);
+            if (ce == cudaSuccess) ce = capture_solve(hs[k], b->streams[k]);
+            for (int q = 0; q < 3; ++q) b->kernels[3 * (size_t)k + q] = hs[k]->graph_kernels[q];
+            if (ce == cudaSuccess) ce = cudaEventRecord(b->events[k], b->streams[k]);
+            if (ce == cudaSuccess) ce = cudaStreamWaitEvent(b->root, b->events[k], 0);
+        }
+        e = cudaStreamEndCapture(b->root, &g);
+        if (ce != cudaSuccess) e = ce;
+        if (e != cudaSuccess) break;
+        e = cudaGraphInstantiate(&b->exec, g, 0);
+    } while (0);
+    if (e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return batch_fail(nullptr, IMGM_ERR_CUDA, std::string("batch graph: ") + cudaGetErrorString(e));
+    }
+    b->graph = g;
+    *out = b.release();
+    return IMGM_OK;
+}
+
+int imgm_batch_solve(imgm_batch* b, const double* const* dev_b, double* const* dev_x, double rtol, int maxit,
+                     imgm_result* out, void* stream) {
+    if (!b || !b->exec) return batch_fail(b, IMGM_ERR_INVALID, "no batch");
+    if (!dev_b || !dev_x || !out) return batch_fail(b, IMGM_ERR_INVALID, "null pointer");
+    const int n = (int)b->hs.size();
+    cudaStream_t s = (cudaStream_t)stream;
+    PcgState init;
+    std::memset(&init, 0, sizeof(init));
+    init.tol2 = rtol * rtol;
+    init.maxit = maxit;
+    for (int k = 0; k < n; ++k) {
+        imgm_handle* h = b->hs[k];
+        if (!dev_b[k] || !dev_x[k]) return batch_fail(b, IMGM_ERR_INVALID, "null vector");
+        if (maxit < 0 || maxit >= h->hist_cap || !(rtol >= 0.0)) return batch_fail(b, IMGM_ERR_INVALID, "bad rtol or maxit");
+        const int64_t N = h->lv[h->L - 1].d.N;
+        cudaError_t e = cudaMemcpyAsync(h->st, &init, sizeof(init), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h->cb, dev_b[k], N * sizeof(double), cudaMemcpyDeviceToDevice, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h->cx, dev_x[k], N * sizeof(double), cudaMemcpyDeviceToDevice, s);
+        if (e != cudaSuccess) return batch_fail(b, IMGM_ERR_CUDA, cudaGetErrorString(e));
+    }
+    cudaError_t e = cudaGraphLaunch(b->exec, s);
+    std::vector<PcgState> fin(n);
+    for (int k = 0; k < n && e == cudaSuccess; ++k) {
+        imgm_handle* h = b->hs[k];
+        const int64_t N = h->lv[h->L - 1].d.N;
+        e = cudaMemcpyAsync(dev_x[k], h->cx, N * sizeof(double), cudaMemcpyDeviceToDevice, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&fin[k], h->st, sizeof(PcgState), cudaMemcpyDeviceToHost, s);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return batch_fail(b, IMGM_ERR_CUDA, cudaGetErrorString(e));
+    int rc = IMGM_OK;
+    for (int k = 0; k < n; ++k) {
+        const PcgState& f = fin[k];
+        out[k].iterations = f.iter;
+        out[k].status = f.status;
+        out[k].rel_residual = f.bb > 0 ? std::sqrt(f.rr / f.bb) : 0.0;
+        out[k].true_rel_residual = f.bb > 0 ? std::sqrt(f.true_rr / f.bb) : 0.0;
+        out[k].kernel_launches = b->kernels[3 * (size_t)k] + (int64_t)f.iter * b->kernels[3 * (size_t)k + 1] +
+                                 b->kernels[3 * (size_t)k + 2];
+        const int ck = f.status == -5 ? IMGM_ERR_BREAKDOWN : (f.status == 1 ? IMGM_MAX_ITER : IMGM_OK);
+        if (rc == IMGM_OK) rc = ck;
+    }
+    return rc;
+}
+
+void imgm_batch_destroy(imgm_batch* b) {
+    if (!b) return;
+    cudaDeviceSynchronize();
+    delete b;
+}
