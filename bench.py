@@ -31,8 +31,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "DOF/s to rel. residual 1e-8 (PCG+MG) vs plain FP64 GPU; HBM GB/s of roofline"
 # DRAM bytes of one finest-level FP64 apply launch on this workload, from one ncu capture
-# (dram__bytes_read.sum 4.907 MB + dram__bytes_write.sum 0); null it when the kernel changes
-APPLY_TRAFFIC_BYTES = None
+# (dram__bytes_read.sum 4.908 MB + dram__bytes_write.sum 0); null it when the kernel changes
+APPLY_TRAFFIC_BYTES = 4.908032e6
 WORKLOAD = "poisson2d-512x512-10discs-bspline-p2-6levels-nitsche"
 PRESET = "discs10_512_p2"
 RTOL = 1e-8
