@@ -35,6 +35,16 @@ METRIC = "DOF/s to rel. residual 1e-8 (PCG+MG) vs plain FP64 GPU; HBM GB/s of ro
 APPLY_TRAFFIC_BYTES = 4.908032e6
 WORKLOAD = "poisson2d-512x512-10discs-bspline-p2-6levels-nitsche"
 PRESET = "discs10_512_p2"
+WORKLOADS = ("discs10_512_p2", "discs10_512_p1", "discs10_512_p3", "spheres20_128_p2", "disc1_32_p2")
+
+
+def workload_name(pr) -> str:
+    if pr.name == PRESET:
+        return WORKLOAD
+    holes = {"disc1": "1disc", "discs10": "10discs", "spheres20": "20spheres"}[pr.layout]
+    size = "x".join([str(pr.n)] * pr.dim)
+    basis = "bspline" if pr.basis == 0 else "lagrange"
+    return f"poisson{pr.dim}d-{size}-{holes}-{basis}-p{pr.degree}-{pr.levels}levels-depth{pr.depth}-nitsche"
 RTOL = 1e-8
 MAXIT = 2000
 FP64_PEAK_NOTE = "152 SMs x 2 FP64 FMA/clk x 2 flop x 2070 MHz"
@@ -228,9 +238,10 @@ def run_ours(args, rank, world, local_rank):
             dist.barrier()
         torch.cuda.synchronize()
 
-    pr = preset(PRESET)
+    pr = preset(args.workload)
     lay = config_layout(pr.layout, args.seed + rank)
     mixed = args.precision == "mixed"
+    headline = args.workload == PRESET
     t0 = time.perf_counter()
     S = lib.Solver(pr.dim, lay.centers, lay.radii, pr.n, pr.degree, pr.levels, pr.depth, pr.bc, basis=pr.basis,
                    precision=1 if mixed else 0)
@@ -269,12 +280,15 @@ def run_ours(args, rank, world, local_rank):
         t_dev, results = timed_solves(S, args.steps, args.warmup, "solve_mixed" if mixed else "solve_fp64")
     clocks = clk.summary()
     t64, res64 = (t_dev, results) if not mixed else timed_solves(S64, args.steps, args.warmup, "solve_fp64")
-    # the same solve with coloured multiplicative Schwarz (Sec. 3.4), beside the headline
-    SM = lib.Solver(pr.dim, lay.centers, lay.radii, pr.n, pr.degree, pr.levels, pr.depth, pr.bc, basis=pr.basis,
-                    precision=1 if mixed else 0, smoother=1)
-    t_mult, res_mult = timed_solves(SM, args.steps, args.warmup, "solve_multiplicative")
-    SM.close()
-    batched = run_batched(lib, torch, mixed, max(1, args.steps // 2), 1)
+    # the same solve with coloured multiplicative Schwarz (Sec. 3.4), and the batch, beside
+    # the headline workload (other workloads: the two precisions only)
+    t_mult, res_mult, batched = None, None, None
+    if headline:
+        SM = lib.Solver(pr.dim, lay.centers, lay.radii, pr.n, pr.degree, pr.levels, pr.depth, pr.bc,
+                        basis=pr.basis, precision=1 if mixed else 0, smoother=1)
+        t_mult, res_mult = timed_solves(SM, args.steps, args.warmup, "solve_multiplicative")
+        SM.close()
+        batched = run_batched(lib, torch, mixed, max(1, args.steps // 2), 1)
 
     # end to end: host (pinned) b in, host x out, through the C-ABI
     bh = torch.empty(n_grid, dtype=torch.float64, pin_memory=True)
@@ -341,7 +355,8 @@ def run_ours(args, rank, world, local_rank):
         "metric": METRIC, "value": value, "unit": "DOF/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * t_dev / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32" if mixed else "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "dim": 2, "n": pr.n, "basis": "bspline", "degree": pr.degree,
+        "config": {"workload": workload_name(pr), "dim": pr.dim, "n": pr.n,
+                   "basis": "bspline" if pr.basis == 0 else "lagrange", "degree": pr.degree,
                    "levels": pr.levels, "holes": lay.n_holes, "depth": pr.depth, "bc": "nitsche", "rtol": RTOL,
                    "n_active": n_active, "n_grid": n_grid, "seed": args.seed, "parallelism": f"replicas{world}",
                    "vcycle": "fp32 (Jacobi-scaled) in fp64 flexible CG" if mixed else "fp64",
@@ -351,20 +366,21 @@ def run_ours(args, rank, world, local_rank):
         "fp64": {"value": value64, "unit": "DOF/s", "ms_per_step": 1e3 * t64 / args.steps,
                  "iterations": res64[0]["iterations"], "true_rel_residual": res64[-1]["true_rel_residual"]},
         "speedup_vs_fp64": value / value64,
-        "multiplicative": {"value": total_units / t_mult, "unit": "DOF/s", "ms_per_step": 1e3 * t_mult / args.steps,
-                           "iterations": res_mult[0]["iterations"],
-                           "true_rel_residual": res_mult[-1]["true_rel_residual"],
-                           "gpu_launches_per_solve": int(res_mult[0]["kernel_launches"]),
-                           "smoother": "coloured multiplicative Schwarz, same precision as the headline"},
+        "multiplicative": None if t_mult is None else {
+            "value": total_units / t_mult, "unit": "DOF/s", "ms_per_step": 1e3 * t_mult / args.steps,
+            "iterations": res_mult[0]["iterations"], "true_rel_residual": res_mult[-1]["true_rel_residual"],
+            "gpu_launches_per_solve": int(res_mult[0]["kernel_launches"]),
+            "smoother": "coloured multiplicative Schwarz, same precision as the headline"},
         "batched": batched,
         "e2e": {"value": total_units / t_e2e, "unit": "DOF/s", "h2d_bytes_per_step": 8 * n_grid,
                 "d2h_bytes_per_step": 8 * n_grid},
         "gpu_launches": sum(int(r["kernel_launches"]) for r in results),
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                     "traffic": APPLY_TRAFFIC_BYTES,
+                     "traffic": APPLY_TRAFFIC_BYTES if headline else None,
                      "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of this kernel on this "
                                        "workload (profiles/k_apply_fp64_poisson2d_512_p2.md)",
-                     "kernel": "k_apply_tile2d<double> (finest-level operator apply, FP64)",
+                     "kernel": ("k_apply_tile2d<double>" if pr.dim == 2 else "k_apply<double, 3>")
+                               + " (finest-level operator apply, FP64)",
                      "peak_source": "derived: " + FP64_PEAK_NOTE, "flops_per_launch": flops,
                      "launch_ms": apply_ms,
                      "timing": "200 launches replayed from a CUDA graph" if apply_graph is not None
@@ -376,6 +392,8 @@ def run_ours(args, rank, world, local_rank):
             line["cpu_baseline"] = cpu_baseline_entry(run_oracle(reps=1, seed=args.seed))
         except Exception as e:  # the GPU number stands without it
             line["cpu_baseline"] = {"error": str(e)[:200]}
+    if not headline:
+        line["cpu_baseline_note"] = "cpu_baseline is measured on the headline workload's 128x128 sample"
     if S64 is not S:
         S64.close()
     S.close()
@@ -407,6 +425,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default=PRESET, choices=WORKLOADS,
+                    help="the headline is the 512x512 quadratic B-spline workload; the others are the other "
+                         "configurations of the same study")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"],
                     help="V-cycle arithmetic of the timed solves (the FP64 path is timed beside it)")
     args = ap.parse_args()

@@ -159,6 +159,50 @@ size_t vcycle_cluster_smem(int max_block);
 cudaError_t launch_vcycle_cluster(int dim, int p, const VcycleCoarse* V, size_t smem, const int* done,
                                   cudaStream_t s);
 
+// ---- the coarse levels of the FP32 V-cycle resident in distributed shared memory ----
+// One thread-block cluster holds levels 1..top+1 (indices 0..top) entirely on chip: the
+// rows of every level are split into `ch`-row chunks, block k of the cluster owning
+// chunk k.  Per-row vectors (x, r, t, e and the scales s, d) sit at the same offsets in
+// every block, so any row's value is reached through the owner's shared memory (DSMEM);
+// the tables a block needs only for its own rows (row kinds, stored coefficients, dinv,
+// the Schwarz blocks it applies) and the small 1-D tables are its private image, built at
+// setup and copied in at the start of each launch.  Offsets are in bytes from the start of
+// the dynamic shared memory.
+constexpr int DS_MAX_LEVELS = 8;
+constexpr int DS_TPB = 1024;
+struct DsLevel {
+    int m, N, ch, TW;                        // functions per direction, rows, rows per block, prolongation taps
+    int nst, nblk;                           // stored rows and Schwarz blocks of this block
+    uint32_t off_x, off_r, off_t, off_e, off_s, off_d;          // common per-row vectors (ch floats each)
+    uint32_t off_ri, off_coef, off_dinv;                        // own rows: kind / local stored id, coefficients, dinv
+    uint32_t off_K1, off_M1;                                    // 1-D rows [m][2p+1]
+    uint32_t off_bptr, off_bvptr, off_bidx, off_bval;           // own Schwarz blocks
+    uint32_t off_rfirst, off_rw, off_tfirst, off_tw;            // transfer to the next coarser level (index >= 1)
+};
+struct DsImage {                             // header of every block's image
+    DsLevel lv[DS_MAX_LEVELS];
+    int top, dim, p, max_block;
+    float gamma;
+    uint32_t vec_bytes;                      // common vector region (image starts there)
+    uint32_t image_bytes;                    // largest image (all blocks reserve it)
+    uint32_t scratch_off;                    // per-warp block scratch (max_block floats per warp)
+};
+struct DsVcycle {                            // launch parameters (by value)
+    const unsigned char* images;             // cluster-size images, image_bytes apart
+    const float* s_glob[DS_MAX_LEVELS];      // global scales s, d of each level (copied in per launch)
+    const float* d_glob[DS_MAX_LEVELS];
+    float* x_top;                            // global x, r of level top (from the finest restriction; x is written back)
+    float* r_top;
+    const int32_t* c_rows;                   // coarsest solve: kept rows and FP32 inverse (global)
+    const float* c_inv;
+    int nc, top, cs;
+    uint32_t vec_bytes, image_bytes;         // as in the images' header
+    uint32_t smem_bytes;                     // vec_bytes + image_bytes + block scratch
+};
+// dynamic shared memory and the launch; 0 when the device has no clusters of that size
+int ds_cluster_size();
+cudaError_t launch_vcycle_dsmem(int dim, int p, const DsVcycle& V, cudaStream_t s);
+
 int reduction_blocks();   // fixed number of blocks of every reducing kernel
 // programmatic dependent launch of the kernels issued by this host thread (default on)
 void set_programmatic_launch(bool on);
