@@ -99,10 +99,12 @@ struct imgm_handle {
     int nc = 0;
     int precision = 0;                 // 0: FP64 V-cycle, 1: FP32 V-cycle in the FP64 CG
     float *zf = nullptr, *rf = nullptr, *zpf = nullptr;   // finest FP32 V-cycle output, input, previous output
-    imgm::VcycleCoarse* vc = nullptr;  // device copy of the coarse levels for the cluster V-cycle (FP32)
-    int vc_top = -1;                   // highest level index the cluster kernel handles (-1: not used)
-    int vc_max_block = 1;
-    size_t vc_smem = 0;                // dynamic shared memory of the cluster launch
+    // FP32 V-cycle: levels 0..ds_top on one thread-block cluster, resident in distributed
+    // shared memory (-1: every level as separate launches)
+    int ds_top = -1;
+    imgm::DsVcycle dsv{};
+    std::vector<const unsigned char*> ds_images;   // per top: the blocks' images (shared tables), or null
+    std::vector<imgm::DsVcycle> ds_cand;           // per top: launch parameters of this context
     double* b = nullptr;               // built-in right-hand side
     // CG state
     double *cx = nullptr, *cr = nullptr, *cp = nullptr, *cq = nullptr, *cz = nullptr, *cb = nullptr;
@@ -206,7 +208,7 @@ int cluster_top(const imgm_handle* h);
 template <>
 int cluster_top<double>(const imgm_handle*) { return -1; }
 template <>
-int cluster_top<float>(const imgm_handle* h) { return h->vc_top; }
+int cluster_top<float>(const imgm_handle* h) { return h->ds_top; }
 
 // one colour c of the multiplicative Schwarz sweep on level F: x += B_c r
 template <typename T>
@@ -288,7 +290,7 @@ cudaError_t enqueue_vcycle(imgm_handle* h, const T* r, T* z, const int*, cudaStr
             if ((e = imgm::launch_restrict<T>(A::d(F), A::d(C), A::t(F), A::r(C), xc, g, done, s)) != cudaSuccess)
                 return e;
         }
-        if ((e = imgm::launch_vcycle_cluster(h->dim, h->p, h->vc, h->vc_smem, done, s)) != cudaSuccess) return e;
+        if ((e = imgm::launch_vcycle_dsmem(h->dim, h->p, h->dsv, s)) != cudaSuccess) return e;
         for (int li = ct + 1; li <= L - 1; ++li) {
             LevelDev& F = h->lv[li];
             LevelDev& C = h->lv[li - 1];
@@ -468,9 +470,147 @@ cudaError_t build_solve_graph(imgm_handle* h) {
     return e;
 }
 
+// Images of the cluster-resident coarse levels 0..top for a cluster of cs blocks (see
+// DsLevel): the common per-row vector layout, and per block its own rows' tables and the
+// Schwarz blocks it applies (the block of its first member's owner).  Returns false when
+// the levels do not fit the shared memory of one block.
+bool build_ds_images(const imgm_handle* h, int top, int cs, std::vector<unsigned char>& images, imgm::DsImage& hdr0) {
+    using imgm::DsLevel;
+    const imgm::Hierarchy& H = h->H;
+    const int dim = H.dim, p = H.p, W = 2 * p + 1, NC = H.ncoef;
+    auto al16 = [](size_t v) { return (v + 15) & ~size_t(15); };
+    std::vector<int> ch(top + 1);
+    uint32_t off = 0;
+    imgm::DsImage hdr{};
+    hdr.top = top;
+    hdr.dim = dim;
+    hdr.p = p;
+    hdr.gamma = (float)h->gamma;
+    int mb = 1;
+    for (int li = 0; li <= top; ++li) {
+        const imgm::LevelData& L = H.lv[li];
+        ch[li] = (int)(((L.N + cs - 1) / cs + 3) & ~int64_t(3));
+        DsLevel& d = hdr.lv[li];
+        d.m = L.m;
+        d.N = (int)L.N;
+        d.ch = ch[li];
+        d.TW = L.TW;
+        const uint32_t vb = (uint32_t)ch[li] * 4;
+        d.off_x = off;
+        d.off_r = off + vb;
+        d.off_t = off + 2 * vb;
+        d.off_e = off + 3 * vb;
+        d.off_s = off + 4 * vb;
+        d.off_d = off + 5 * vb;
+        off += 6 * vb;
+        if (li >= 1) mb = std::max(mb, (int)L.max_block);
+    }
+    hdr.max_block = mb;
+    hdr.vec_bytes = off;
+    // per block: sizes, then contents
+    std::vector<std::vector<unsigned char>> img(cs);
+    std::vector<imgm::DsImage> hd(cs, hdr);
+    size_t max_img = 0;
+    for (int k = 0; k < cs; ++k) {
+        std::vector<unsigned char>& B = img[k];
+        size_t pos = al16(sizeof(imgm::DsImage));
+        B.assign(pos, 0);
+        auto put = [&](const void* src, size_t bytes) -> uint32_t {
+            const size_t at = pos;
+            B.resize(al16(at + bytes), 0);
+            if (bytes) std::memcpy(B.data() + at, src, bytes);
+            pos = B.size();
+            return (uint32_t)(hdr.vec_bytes + at);
+        };
+        for (int li = 0; li <= top; ++li) {
+            const imgm::LevelData& L = H.lv[li];
+            DsLevel& d = hd[k].lv[li];
+            const int64_t lo = (int64_t)k * ch[li], hi = std::min<int64_t>(L.N, lo + ch[li]);
+            std::vector<int32_t> ri(ch[li], -2);
+            std::vector<float> coef, dinv(ch[li], 0.0f);
+            const int64_t nb = (int64_t)L.band_rows.size();
+            int nst = 0;
+            for (int64_t j = lo; j < hi; ++j) {
+                const int32_t r = L.rowinfo[j];
+                if (r >= 0) {
+                    ri[j - lo] = nst++;
+                    for (int c = 0; c < NC; ++c) coef.push_back(L.f_band_coef[(size_t)c * nb + r]);
+                } else {
+                    ri[j - lo] = r;
+                }
+                if (!L.f_dinv.empty()) dinv[j - lo] = L.f_dinv[j];
+            }
+            d.nst = nst;
+            d.off_ri = put(ri.data(), ri.size() * 4);
+            d.off_coef = put(coef.data(), coef.size() * 4);
+            d.off_dinv = put(dinv.data(), dinv.size() * 4);
+            d.off_K1 = put(L.f_K1.data(), L.f_K1.size() * 4);
+            d.off_M1 = put(L.f_M1.data(), L.f_M1.size() * 4);
+            // Schwarz blocks whose first member this block owns
+            std::vector<int32_t> bptr(1, 0), bvptr(1, 0), bidx;
+            std::vector<float> bval;
+            const int64_t nblk = L.blk_ptr.empty() ? 0 : (int64_t)L.blk_ptr.size() - 1;
+            for (int64_t b = 0; b < nblk; ++b) {
+                const int64_t s0 = L.blk_ptr[b], nj = L.blk_ptr[b + 1] - s0;
+                if (L.blk_idx[s0] / ch[li] != k) continue;
+                for (int64_t a = 0; a < nj; ++a) bidx.push_back(L.blk_idx[s0 + a]);
+                for (int64_t v = 0; v < nj * nj; ++v) bval.push_back(L.f_blk_val[L.blk_vptr[b] + v]);
+                bptr.push_back((int32_t)bidx.size());
+                bvptr.push_back((int32_t)bval.size());
+            }
+            d.nblk = (int)bptr.size() - 1;
+            d.off_bptr = put(bptr.data(), bptr.size() * 4);
+            d.off_bvptr = put(bvptr.data(), bvptr.size() * 4);
+            d.off_bidx = put(bidx.data(), bidx.size() * 4);
+            d.off_bval = put(bval.data(), bval.size() * 4);
+            if (li >= 1) {
+                d.off_rfirst = put(L.r_first.data(), L.r_first.size() * 4);
+                d.off_rw = put(L.f_r_w.data(), L.f_r_w.size() * 4);
+                d.off_tfirst = put(L.t_first.data(), L.t_first.size() * 4);
+                d.off_tw = put(L.f_t_w.data(), L.f_t_w.size() * 4);
+            }
+            (void)W;
+        }
+        max_img = std::max(max_img, B.size());
+    }
+    const uint32_t image_bytes = (uint32_t)al16(max_img);
+    const size_t smem = (size_t)hdr.vec_bytes + image_bytes + (size_t)(imgm::DS_TPB / 32) * mb * 4;
+    if (smem > imgm::DS_SMEM_MAX) return false;
+    images.assign((size_t)cs * image_bytes, 0);
+    for (int k = 0; k < cs; ++k) {
+        hd[k].image_bytes = image_bytes;
+        hd[k].scratch_off = hdr.vec_bytes + image_bytes;
+        std::memcpy(img[k].data(), &hd[k], sizeof(imgm::DsImage));
+        std::memcpy(images.data() + (size_t)k * image_bytes, img[k].data(), img[k].size());
+    }
+    hdr0 = hd[0];
+    return true;
+}
+
+// Launch parameters of the cluster V-cycle over levels 0..top for this context.
+imgm::DsVcycle ds_params(const imgm_handle* h, int top, const unsigned char* images, const imgm::DsImage& hdr, int cs) {
+    imgm::DsVcycle V{};
+    V.images = images;
+    for (int li = 0; li <= top; ++li) {
+        V.s_glob[li] = h->lv[li].fd.s;
+        V.d_glob[li] = h->lv[li].fd.d;
+    }
+    V.x_top = h->lv[top].fx;
+    V.r_top = h->lv[top].fr;
+    V.c_rows = h->c_rows;
+    V.c_inv = h->f_c_inv;
+    V.nc = h->nc;
+    V.top = top;
+    V.cs = cs;
+    V.vec_bytes = hdr.vec_bytes;
+    V.image_bytes = hdr.image_bytes;
+    V.smem_bytes = hdr.scratch_off + (uint32_t)((imgm::DS_TPB / 32) * hdr.max_block * 4);
+    return V;
+}
+
 // Chooses how many coarse levels of the FP32 V-cycle run in the cluster kernel (none,
 // or levels 1..top for some top) by timing whole V-cycles of each choice on this device.
-cudaError_t autotune_cluster(imgm_handle* h, imgm::VcycleCoarse& vc) {
+cudaError_t autotune_cluster(imgm_handle* h) {
     cudaStream_t s = nullptr;
     cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
     if (e != cudaSuccess) return e;
@@ -487,17 +627,9 @@ cudaError_t autotune_cluster(imgm_handle* h, imgm::VcycleCoarse& vc) {
         if (err == cudaSuccess) err = cudaEventElapsedTime(ms, e0, e1);
         return err;
     };
-    // makes `top` the cluster launch's highest level (-1: separate launches only)
-    auto install = [&](int top) -> cudaError_t {
-        int mb = 1;
-        for (int li = 1; li <= top; ++li) mb = std::max(mb, (int)h->lv[li].fd.max_block);
-        h->vc_top = top;
-        h->vc_max_block = mb;
-        h->vc_smem = imgm::vcycle_cluster_smem(mb);
-        if (top < 0) return cudaSuccess;
-        vc.top = top;
-        vc.max_block = mb;
-        return cudaMemcpy(h->vc, &vc, sizeof(vc), cudaMemcpyHostToDevice);
+    auto install = [&](int top) {
+        h->ds_top = top;
+        if (top >= 0) h->dsv = h->ds_cand[top];
     };
     const bool verbose = std::getenv("IMGM_VERBOSE") != nullptr;
     int best_top = -1;
@@ -506,23 +638,43 @@ cudaError_t autotune_cluster(imgm_handle* h, imgm::VcycleCoarse& vc) {
     e = time_vcycles(&best);
     if (verbose && e == cudaSuccess)
         std::fprintf(stderr, "imgm: V-cycle, all levels as separate launches: %.2f us\n", best * 50.0f);
-    for (int top = h->L - 2; top >= 0 && e == cudaSuccess; --top) {
-        if ((e = install(top)) != cudaSuccess) break;
+    for (int top = (int)h->ds_cand.size() - 1; top >= 0 && e == cudaSuccess; --top) {
+        if (!h->ds_images[top]) continue;
+        install(top);
         float t = 0.0f;
         e = time_vcycles(&t);
         if (verbose && e == cudaSuccess)
-            std::fprintf(stderr, "imgm: V-cycle, levels 1..%d in one cluster launch: %.2f us\n", top + 1, t * 50.0f);
+            std::fprintf(stderr, "imgm: V-cycle, levels 1..%d resident on one cluster: %.2f us\n", top + 1, t * 50.0f);
         if (e == cudaSuccess && t < best) {
             best = t;
             best_top = top;
         }
     }
-    const cudaError_t ei = install(e == cudaSuccess ? best_top : -1);
-    if (e == cudaSuccess) e = ei;
+    install(e == cudaSuccess ? best_top : -1);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaStreamDestroy(s);
     return e;
+}
+
+// Builds and uploads the cluster images of every top that fits, and this context's launch
+// parameters for each.
+int prepare_ds(imgm_handle* h) {
+    const int cs = imgm::ds_cluster_size();
+    const int maxtop = std::min(h->L - 2, imgm::DS_MAX_LEVELS - 1);
+    h->ds_images.assign(std::max(maxtop + 1, 0), nullptr);
+    h->ds_cand.assign(std::max(maxtop + 1, 0), imgm::DsVcycle{});
+    if (cs <= 0) return IMGM_OK;
+    for (int top = 0; top <= maxtop; ++top) {
+        std::vector<unsigned char> images;
+        imgm::DsImage hdr{};
+        if (!build_ds_images(h, top, cs, images, hdr)) break;     // larger tops do not fit either
+        unsigned char* dev = nullptr;
+        CK(h->upload(&dev, images), "upload cluster images");
+        h->ds_images[top] = dev;
+        h->ds_cand[top] = ds_params(h, top, dev, hdr, cs);
+    }
+    return IMGM_OK;
 }
 
 // one level's vectors and tile counter: per solve context
@@ -551,34 +703,6 @@ int alloc_level_vectors(imgm_handle* h, LevelDev& dst) {
         CK(cudaMemset(dst.ft, 0, N * sizeof(float)), "memset");
         CK(cudaMemset(dst.fe, 0, N * sizeof(float)), "memset");
     }
-    return IMGM_OK;
-}
-
-// The FP32 V-cycle's coarse levels as one cluster launch: the level table of this
-// context (its vectors) in device memory.
-int alloc_cluster_table(imgm_handle* h, int top) {
-    imgm::VcycleCoarse vc{};
-    vc.top = top;
-    int mb = 1;
-    for (int li = 0; li <= h->L - 2 && li < imgm::VCYCLE_MAX_LEVELS; ++li) {
-        LevelDev& Ld = h->lv[li];
-        vc.lv[li] = Ld.fd;
-        vc.x[li] = Ld.fx;
-        vc.r[li] = Ld.fr;
-        vc.t[li] = Ld.ft;
-        vc.e[li] = Ld.fe;
-        if (li >= 1 && li <= top) mb = std::max(mb, (int)Ld.fd.max_block);
-    }
-    vc.c_rows = h->c_rows;
-    vc.c_inv = h->f_c_inv;
-    vc.nc = h->nc;
-    vc.max_block = mb;
-    vc.gamma = h->gamma;
-    if (!h->vc) CK(h->alloc(&h->vc, 1), "alloc cluster levels");
-    CK(cudaMemcpy(h->vc, &vc, sizeof(vc), cudaMemcpyHostToDevice), "upload cluster levels");
-    h->vc_top = top;
-    h->vc_max_block = mb;
-    h->vc_smem = imgm::vcycle_cluster_smem(mb);
     return IMGM_OK;
 }
 
@@ -796,18 +920,28 @@ int imgm_setup(const imgm_geometry* geom, const imgm_config* cfg, imgm_handle** 
             g_setup_error = h->err;
             return rc;
         }
-        // the coarse levels of the FP32 V-cycle as one cluster launch, when the device has
-        // clusters and the autotuner finds it faster
-        if (h->precision == 1 && h->smoother == 0 && h->L >= 2 && h->L - 1 <= imgm::VCYCLE_MAX_LEVELS &&
-            imgm::vcycle_cluster_size() > 0) {
-            rc = alloc_cluster_table(h, h->L - 2);
+        // the coarse levels of the FP32 V-cycle resident on one cluster, when the device has
+        // clusters, the levels fit and the autotuner finds it faster
+        if (h->precision == 1 && h->smoother == 0 && h->L >= 2) {
+            rc = prepare_ds(h);
             if (rc != IMGM_OK) {
                 g_setup_error = h->err;
                 return rc;
             }
-            imgm::VcycleCoarse vc{};
-            CK(cudaMemcpy(&vc, h->vc, sizeof(vc), cudaMemcpyDeviceToHost), "read cluster levels");
-            CK(autotune_cluster(h, vc), "cluster autotune");
+            CK(autotune_cluster(h), "cluster autotune");
+            // IMGM_CLUSTER_TOP=k forces levels 1..k+1 onto the cluster (when they fit), -1 none
+            if (const char* v = std::getenv("IMGM_CLUSTER_TOP")) {
+                const int t = std::atoi(v);
+                if (t < 0) {
+                    h->ds_top = -1;
+                } else {
+                    int best = -1;
+                    for (int q = 0; q <= t && q < (int)h->ds_images.size(); ++q)
+                        if (h->ds_images[q]) best = q;
+                    h->ds_top = best;
+                    if (best >= 0) h->dsv = h->ds_cand[best];
+                }
+            }
         }
         CK(cudaDeviceSynchronize(), "setup sync");
     }
@@ -1222,12 +1356,21 @@ int imgm_clone(const imgm_handle* src, imgm_handle** out) {
         }
     }
     int rc = alloc_context(hp);
-    if (rc == IMGM_OK && src->vc_top >= 0) rc = alloc_cluster_table(hp, src->vc_top);
     if (rc != IMGM_OK) {
         g_setup_error = hp->err;
         return rc;
     }
-    hp->vc_top = src->vc_top;
+    // the cluster images are shared; the launch parameters point at this context's vectors
+    hp->ds_images = src->ds_images;
+    hp->ds_cand.assign(src->ds_cand.size(), imgm::DsVcycle{});
+    for (size_t t = 0; t < src->ds_cand.size(); ++t)
+        if (src->ds_images[t]) {
+            hp->ds_cand[t] = src->ds_cand[t];
+            hp->ds_cand[t].x_top = hp->lv[t].fx;
+            hp->ds_cand[t].r_top = hp->lv[t].fr;
+        }
+    hp->ds_top = src->ds_top;
+    if (hp->ds_top >= 0) hp->dsv = hp->ds_cand[hp->ds_top];
     {
         imgm_handle* h = hp;
         CK(cudaDeviceSynchronize(), "clone sync");

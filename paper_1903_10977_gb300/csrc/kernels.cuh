@@ -134,31 +134,6 @@ cudaError_t launch_true_residual_norm(int64_t N, const double* v, double* partia
 // sets the conditional of the solve loop to !done
 cudaError_t launch_set_continue(PcgState* st, unsigned long long handle, cudaStream_t s);
 
-// The coarse part of the FP32 V-cycle (levels top .. 1 and the level-1 solve) as one
-// thread-block-cluster launch.  V lives in device memory (a multiple of 4 bytes; the
-// kernel copies it to shared memory).
-constexpr int VCYCLE_MAX_LEVELS = 16;
-constexpr size_t VCYCLE_SMEM_MAX = 48 * 1024;       // dynamic shared memory per block, at most
-struct VcycleCoarse {
-    DevLevelT<float> lv[VCYCLE_MAX_LEVELS];
-    float* x[VCYCLE_MAX_LEVELS];
-    float* r[VCYCLE_MAX_LEVELS];
-    float* t[VCYCLE_MAX_LEVELS];
-    float* e[VCYCLE_MAX_LEVELS];
-    const int32_t* c_rows;
-    const float* c_inv;
-    int nc;
-    int top;            // highest level index handled (the finest level's restriction fills r[top], x[top])
-    int max_block;      // largest Schwarz block over levels 1..top
-    double gamma;
-};
-// cluster size the device supports for it (0: none)
-int vcycle_cluster_size();
-// dynamic shared memory of the launch (the block-inverse scratch of its warps)
-size_t vcycle_cluster_smem(int max_block);
-cudaError_t launch_vcycle_cluster(int dim, int p, const VcycleCoarse* V, size_t smem, const int* done,
-                                  cudaStream_t s);
-
 // ---- the coarse levels of the FP32 V-cycle resident in distributed shared memory ----
 // One thread-block cluster holds levels 1..top+1 (indices 0..top) entirely on chip: the
 // rows of every level are split into `ch`-row chunks, block k of the cluster owning
@@ -170,6 +145,7 @@ cudaError_t launch_vcycle_cluster(int dim, int p, const VcycleCoarse* V, size_t 
 // the dynamic shared memory.
 constexpr int DS_MAX_LEVELS = 8;
 constexpr int DS_TPB = 1024;
+constexpr uint32_t DS_SMEM_MAX = 200 * 1024;   // dynamic shared memory per block, at most
 struct DsLevel {
     int m, N, ch, TW;                        // functions per direction, rows, rows per block, prolongation taps
     int nst, nblk;                           // stored rows and Schwarz blocks of this block
