@@ -379,7 +379,7 @@ def run_ours(args, rank, world, local_rank):
                      "traffic": APPLY_TRAFFIC_BYTES if headline else None,
                      "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of this kernel on this "
                                        "workload (profiles/k_apply_fp64_poisson2d_512_p2.md)",
-                     "kernel": ("k_apply_tile2d<double>" if pr.dim == 2 else "k_apply<double, 3>")
+                     "kernel": ("k_apply_tile2d<double>" if pr.dim == 2 else "k_apply_tile3d<double>")
                                + " (finest-level operator apply, FP64)",
                      "peak_source": "derived: " + FP64_PEAK_NOTE, "flops_per_launch": flops,
                      "launch_ms": apply_ms,

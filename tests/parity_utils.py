@@ -23,9 +23,9 @@ def layout_for(name: str, seed: int = 0, **overrides):
 
 @functools.lru_cache(maxsize=8)
 def oracle_for(name: str, seed: int = 0, n: int | None = None, levels: int | None = None, depth: int | None = None,
-               bc: int | None = None, smoother: str = "additive"):
+               bc: int | None = None, smoother: str = "additive", degree: int | None = None):
     """(preset, layout, Discretization, Hierarchy) of the oracle for a workload (optionally resized)."""
-    ov = {k: v for k, v in dict(n=n, levels=levels, depth=depth, bc=bc).items() if v is not None}
+    ov = {k: v for k, v in dict(n=n, levels=levels, depth=depth, bc=bc, degree=degree).items() if v is not None}
     pr, lay = layout_for(name, seed, **ov)
     d = _disc_for(name, seed, tuple(sorted(ov.items())))
     H = MG.Hierarchy(d, pr.levels, smoother=smoother)
