@@ -211,6 +211,20 @@ def run_batched(lib, torch, mixed, steps, warmup):
             "launch": "one CUDA graph: every solve a branch with its own device-side CG loop"}
 
 
+def reduce_replicas(dist, device, times, units):
+    """Whole-job figures of N independent replicas: each time is the maximum over ranks
+    (the job ends with its slowest rank) and the work is the sum of every rank's units
+    (the ranks solve different seeded geometries, so their DOF counts differ)."""
+    import torch
+    if dist is None:
+        return list(times), float(units)
+    t = torch.tensor(list(times), dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return [float(v) for v in t.tolist()], float(u.item())
+
+
 def apply_flops(S) -> float:
     """Algorithmic FP64 flops of one finest-level operator apply: 8(2p+1) per tensor row
     (sum factorisation) + 2 (2p+1)^d per stored row."""
@@ -337,14 +351,11 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.nvtx.range_pop()
     apply_ms = k0.elapsed_time(k1) / reps
 
+    (t_dev, t64, t_e2e), total_units = reduce_replicas(dist, "cuda", [t_dev, t64, t_e2e], n_active * args.steps)
     if dist is not None:
-        t = torch.tensor([t_dev, t64, t_e2e], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_dev, t64, t_e2e = (float(v) for v in t.tolist())
         dist.destroy_process_group()
     if rank != 0:
         return None
-    total_units = n_active * args.steps * world
     value = total_units / t_dev
     value64 = total_units / t64
     its = [r["iterations"] for r in results]
