@@ -1364,7 +1364,9 @@ cudaError_t launch_tile3d(const DevLevelT<T>& L, int mode, const T* x, const T* 
                           const int* done, cudaStream_t s) {
     if (sizeof(T) == 8 && L.tile_ctr == nullptr) return cudaErrorInvalidValue;
     const int64_t n = tiles_3d(L.m);
-    const int64_t g = (sizeof(T) == 8 && mode == APPLY) ? std::min<int64_t>(n, 2 * num_sms()) : n;
+    // FP64 apply: blocks drawing tiles from the level's counter, four per SM (3-D levels
+    // have many tiles, and more resident blocks hide the tile loads)
+    const int64_t g = (sizeof(T) == 8 && mode == APPLY) ? std::min<int64_t>(n, 4 * num_sms()) : n;
     if (g > 2147483647LL) return cudaErrorInvalidValue;
     if (mode == APPLY)
         launch_pdl(k_apply_tile3d<T, P, APPLY, false>, (unsigned)g, TPB, 0, s, L, x, rin, out, xs, gamma, done, nullptr, nullptr);
@@ -1448,7 +1450,7 @@ cudaError_t launch_apply_pq(const DevLevel& L, const double* p, double* q, doubl
     }
     if (L.dim == 3 && use_tiles_3d(L.m)) {
         if (L.tile_ctr == nullptr) return cudaErrorInvalidValue;
-        const int g = (int)std::min<int64_t>(std::min<int64_t>(tiles_3d(L.m), 2 * num_sms()), reduction_blocks());
+        const int g = (int)std::min<int64_t>(std::min<int64_t>(tiles_3d(L.m), 4 * num_sms()), reduction_blocks());
         if (L.p == 1)
             launch_pdl(k_apply_tile3d<double, 1, APPLY, true>, g, TPB, 0, s, L, p, nullptr, q, nullptr, 0.0, &st->done, partial, st);
         else if (L.p == 2)
