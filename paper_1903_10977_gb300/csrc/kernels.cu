@@ -1081,14 +1081,6 @@ __global__ void __launch_bounds__(DS_TPB) k_vcycle_dsmem(const DsVcycle V) {
     cl.sync();     // no block leaves while others may still read its shared memory
 }
 
-template <typename TI, typename TO>
-__global__ void __launch_bounds__(TPB) k_convert(int64_t N, const TI* __restrict__ in, TO* __restrict__ out,
-                                                 const int* done) {
-    pdl_begin();
-    if (done && *done) return;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) out[i] = (TO)in[i];
-}
 
 // V-cycle input from an FP64 residual: r_lo = (TZ)(rs .* r) (or (TZ) r), xv = gamma dinv .* r_lo
 template <typename TZ>
@@ -1582,12 +1574,6 @@ cudaError_t launch_vcycle_dsmem(int dim, int p, const DsVcycle& V, cudaStream_t 
     return cudaErrorInvalidValue;
 }
 
-template <typename TI, typename TO>
-cudaError_t launch_convert(int64_t N, const TI* in, TO* out, const int* done, cudaStream_t s) {
-    const RowLaunch rl = row_launch(N);
-    launch_pdl(k_convert<TI, TO>, rl.grid, rl.block, 0, s, N, in, out, done);
-    return cudaGetLastError();
-}
 
 template <typename TZ>
 cudaError_t launch_vcycle_in(int64_t N, const double* r, const TZ* rs, const TZ* dinv, double gamma, TZ* r_lo, TZ* xv,
@@ -1676,7 +1662,5 @@ cudaError_t launch_set_continue(PcgState* st, unsigned long long handle, cudaStr
     template cudaError_t launch_vcycle_out<T>(int64_t, const T*, const T*, double*, cudaStream_t);
 IMGM_INST(double)
 IMGM_INST(float)
-template cudaError_t launch_convert<double, float>(int64_t, const double*, float*, const int*, cudaStream_t);
-template cudaError_t launch_convert<float, double>(int64_t, const float*, double*, const int*, cudaStream_t);
 
 }  // namespace imgm

@@ -89,9 +89,6 @@ cudaError_t launch_prolong(const DevLevelT<T>& F, const DevLevelT<T>& C, const T
 template <typename T>
 cudaError_t launch_coarse(const int32_t* rows, const T* Cinv, int nc, const T* r, T* x, const int* done,
                           cudaStream_t s);
-// elementwise type conversion out = (TO) in
-template <typename TI, typename TO>
-cudaError_t launch_convert(int64_t N, const TI* in, TO* out, const int* done, cudaStream_t s);
 
 // V-cycle input from an FP64 residual: r_lo = (TZ)(rs .* r) (rs == nullptr: (TZ) r) and
 // xv = gamma * dinv .* r_lo (the diagonal part of the first smoothing step)
