@@ -35,13 +35,13 @@ METRIC = "DOF/s to rel. residual 1e-8 (PCG+MG) vs plain FP64 GPU; HBM GB/s of ro
 APPLY_TRAFFIC_BYTES = 4.908032e6
 WORKLOAD = "poisson2d-512x512-10discs-bspline-p2-6levels-nitsche"
 PRESET = "discs10_512_p2"
-WORKLOADS = ("discs10_512_p2", "discs10_512_p1", "discs10_512_p3", "spheres20_128_p2", "disc1_32_p2")
+WORKLOADS = ("discs10_512_p2", "discs10_512_p1", "discs10_512_p3", "spheres20_128_p2", "disc1_32_p2", "box_256_p2")
 
 
 def workload_name(pr) -> str:
     if pr.name == PRESET:
         return WORKLOAD
-    holes = {"disc1": "1disc", "discs10": "10discs", "spheres20": "20spheres"}[pr.layout]
+    holes = {"disc1": "1disc", "discs10": "10discs", "spheres20": "20spheres", "none3": "noholes"}[pr.layout]
     size = "x".join([str(pr.n)] * pr.dim)
     basis = "bspline" if pr.basis == 0 else "lagrange"
     return f"poisson{pr.dim}d-{size}-{holes}-{basis}-p{pr.degree}-{pr.levels}levels-depth{pr.depth}-nitsche"
@@ -211,6 +211,44 @@ def run_batched(lib, torch, mixed, steps, warmup):
             "launch": "one CUDA graph: every solve a branch with its own device-side CG loop"}
 
 
+def vcycle_bandwidth(S, torch, stream, mixed):
+    """One V-cycle (imgm_apply_preconditioner) timed from a captured CUDA graph of 20, with
+    its algorithmic vector traffic: per level (13 + 2/2^d) s N_l bytes (pre-smoothing 2,
+    residual 3, restriction 1 + 2^-d, prolongation and residual update 4 + 2^-d, post-
+    smoothing 3 passes over vectors of s = 4 (FP32) or 8 bytes and N_l rows), against the
+    measured HBM copy bandwidth (the V-cycle's vectors exceed L2 only on large grids)."""
+    d = S.dim
+    s_bytes = 4 if mixed else 8
+    nbytes = sum((13 + 2 / 2 ** d) * s_bytes * S.level_info(l)["n_grid"] for l in range(2, S.L + 1))
+    r = S.rhs()
+    z = torch.empty_like(r)
+    reps = 20
+    try:
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            for _ in range(reps):
+                S.apply_preconditioner(r, z)
+        g.replay()
+        torch.cuda.synchronize()
+    except Exception:
+        g = None
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    if g is not None:
+        g.replay()
+    else:
+        for _ in range(reps):
+            S.apply_preconditioner(r, z)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / 1e3 / reps
+    peak = measured_peaks().get("hbm_gbs")
+    gbs = nbytes / t / 1e9
+    return {"us": 1e6 * t, "algorithmic_bytes": nbytes, "achieved_gbs": gbs, "hbm_peak_gbs": peak,
+            "frac_of_hbm": gbs / peak if peak else None,
+            "note": "vector passes only (tables excluded); L2-resident at the 2-D sizes"}
+
+
 def reduce_replicas(dist, device, times, units):
     """Whole-job figures of N independent replicas: each time is the maximum over ranks
     (the job ends with its slowest rank) and the work is the sum of every rank's units
@@ -351,6 +389,7 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.nvtx.range_pop()
     apply_ms = k0.elapsed_time(k1) / reps
 
+    vcycle = vcycle_bandwidth(S, torch, stream, mixed)
     (t_dev, t64, t_e2e), total_units = reduce_replicas(dist, "cuda", [t_dev, t64, t_e2e], n_active * args.steps)
     if dist is not None:
         dist.destroy_process_group()
@@ -383,6 +422,7 @@ def run_ours(args, rank, world, local_rank):
             "gpu_launches_per_solve": int(res_mult[0]["kernel_launches"]),
             "smoother": "coloured multiplicative Schwarz, same precision as the headline"},
         "batched": batched,
+        "vcycle": vcycle,
         "e2e": {"value": total_units / t_e2e, "unit": "DOF/s", "h2d_bytes_per_step": 8 * n_grid,
                 "d2h_bytes_per_step": 8 * n_grid},
         "gpu_launches": sum(int(r["kernel_launches"]) for r in results),

@@ -31,6 +31,9 @@ PRESETS = {
     "discs10_512_p3": Preset("discs10_512_p3", 2, 512, 0, 3, 6, 0, 1, "discs10"),
     # 3-D, 128^3, quadratic B-splines, twenty spheres, depth 2, 5 levels
     "spheres20_128_p2": Preset("spheres20_128_p2", 3, 128, 0, 2, 5, 2, 1, "spheres20"),
+    # 3-D, 256^3 box without holes, quadratic B-splines, 6 levels: every vector is larger
+    # than L2, so the V-cycle streams from HBM
+    "box_256_p2": Preset("box_256_p2", 3, 256, 0, 2, 6, 0, 1, "none3"),
 }
 
 

@@ -65,6 +65,9 @@ def config_layout(name: str, seed: int) -> HoleLayout:
         return random_holes(2, 10, 0.03, 0.1, seed)
     if name == "spheres20":
         return random_holes(3, 20, 0.05, 0.15, seed)
+    if name in ("none2", "none3"):
+        d = int(name[-1])
+        return HoleLayout(d, np.zeros((0, d)), np.zeros(0), 0.0, 1.0)
     if name.startswith("discs"):
         return random_holes(2, int(name[5:]), 0.03, 0.1, seed)
     if name.startswith("spheres"):
