@@ -292,11 +292,12 @@ def run_ours(args, rank, world, local_rank):
 
     pr = preset(args.workload)
     lay = config_layout(pr.layout, args.seed + rank)
-    mixed = args.precision == "mixed"
+    code = {"fp64": 0, "mixed": 1, "hybrid": 2}[args.precision]
+    mixed = code != 0            # an FP32 V-cycle (all levels, or below an FP64 finest level)
     headline = args.workload == PRESET
     t0 = time.perf_counter()
     S = lib.Solver(pr.dim, lay.centers, lay.radii, pr.n, pr.degree, pr.levels, pr.depth, pr.bc, basis=pr.basis,
-                   precision=1 if mixed else 0)
+                   precision=code)
     setup_s = time.perf_counter() - t0
     S64 = S if not mixed else lib.Solver(pr.dim, lay.centers, lay.radii, pr.n, pr.degree, pr.levels, pr.depth,
                                          pr.bc, basis=pr.basis, precision=0)
@@ -329,7 +330,7 @@ def run_ours(args, rank, world, local_rank):
         return sum(a.elapsed_time(c) for a, c in ev) / 1e3, res
 
     with ClockSampler(local_rank) as clk:
-        t_dev, results = timed_solves(S, args.steps, args.warmup, "solve_mixed" if mixed else "solve_fp64")
+        t_dev, results = timed_solves(S, args.steps, args.warmup, f"solve_{args.precision}")
     clocks = clk.summary()
     t64, res64 = (t_dev, results) if not mixed else timed_solves(S64, args.steps, args.warmup, "solve_fp64")
     # the same solve with coloured multiplicative Schwarz (Sec. 3.4), and the batch, beside
@@ -389,7 +390,7 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.nvtx.range_pop()
     apply_ms = k0.elapsed_time(k1) / reps
 
-    vcycle = vcycle_bandwidth(S, torch, stream, mixed)
+    vcycle = vcycle_bandwidth(S, torch, stream, code == 1)
     (t_dev, t64, t_e2e), total_units = reduce_replicas(dist, "cuda", [t_dev, t64, t_e2e], n_active * args.steps)
     if dist is not None:
         dist.destroy_process_group()
@@ -409,7 +410,8 @@ def run_ours(args, rank, world, local_rank):
                    "basis": "bspline" if pr.basis == 0 else "lagrange", "degree": pr.degree,
                    "levels": pr.levels, "holes": lay.n_holes, "depth": pr.depth, "bc": "nitsche", "rtol": RTOL,
                    "n_active": n_active, "n_grid": n_grid, "seed": args.seed, "parallelism": f"replicas{world}",
-                   "vcycle": "fp32 (Jacobi-scaled) in fp64 flexible CG" if mixed else "fp64",
+                   "vcycle": {0: "fp64", 1: "fp32 (Jacobi-scaled) in fp64 flexible CG",
+                              2: "fp64 finest level, fp32 (Jacobi-scaled) below, in fp64 flexible CG"}[code],
                    "l2": "flushed (256 MiB write) before every timed solve, flush outside the events",
                    "iterations": its[0], "true_rel_residual": results[-1]["true_rel_residual"],
                    "setup_s": setup_s},
@@ -479,7 +481,7 @@ def main():
     ap.add_argument("--workload", default=PRESET, choices=WORKLOADS,
                     help="the headline is the 512x512 quadratic B-spline workload; the others are the other "
                          "configurations of the same study")
-    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"],
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64", "hybrid"],
                     help="V-cycle arithmetic of the timed solves (the FP64 path is timed beside it)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))

@@ -65,7 +65,9 @@ typedef struct {
     int bc;                  /* 0 = penalty beta = 2/h (the paper's), 1 = symmetric Nitsche */
     double gamma;            /* additive Schwarz relaxation; <= 0 selects 1/(p+1)^d (Eq. applyCS) */
     int precision;           /* V-cycle arithmetic: 0 = FP64; 1 = FP32 on Jacobi-scaled data inside the
-                                FP64 CG, which then uses the flexible (Polak-Ribiere) beta */
+                                FP64 CG, which then uses the flexible (Polak-Ribiere) beta; 2 = the
+                                finest level in FP64 and the levels below it in FP32 (flexible CG;
+                                additive smoother only) */
     int smoother;            /* 0 = additive Schwarz with relaxation gamma (Sec. 3.4, Eq. applyCS);
                                 1 = coloured multiplicative Schwarz (Sec. 3.4): (p+1)^d colours by the
                                 owner's index mod p+1, residual updated after each colour, colours

@@ -17,6 +17,7 @@
 #include <new>
 #include <string>
 #include <vector>
+#include <type_traits>
 
 #include "../../include/imgm.h"
 #include "kernels.cuh"
@@ -108,6 +109,7 @@ struct imgm_handle {
     double* b = nullptr;               // built-in right-hand side
     // CG state
     double *cx = nullptr, *cr = nullptr, *cp = nullptr, *cq = nullptr, *cz = nullptr, *cb = nullptr;
+    double* czp = nullptr;             // previous preconditioned residual (flexible CG, precision 2)
     double* hist = nullptr;
     int hist_cap = 0;
     double* partial = nullptr;
@@ -265,24 +267,19 @@ cudaError_t enqueue_vcycle_mult(imgm_handle* h, const T* r, T* z, const int*, cu
 }
 
 template <typename T>
-cudaError_t enqueue_vcycle(imgm_handle* h, const T* r, T* z, const int*, cudaStream_t s) {
-    // The V-cycle kernels are not told the convergence flag: they touch only the V-cycle's
-    // own vectors, so the one V-cycle after convergence is harmless, while reading the flag
-    // would put a dependent memory round trip in front of every one of them.
+cudaError_t enqueue_vcycle_top(imgm_handle* h, int top, const T* r, T* z, cudaStream_t s) {
     const int* done = nullptr;
-    if (h->smoother == 1) return enqueue_vcycle_mult<T>(h, r, z, done, s);
     using A = Acc<T>;
-    const int L = h->L;
     const double g = h->gamma;
     cudaError_t e;
     const int ct = cluster_top<T>(h);
     if (ct >= 0) {
         // levels above the cluster's: separate kernels, then one cluster launch for the rest
-        for (int li = L - 1; li > ct; --li) {
+        for (int li = top; li > ct; --li) {
             LevelDev& F = h->lv[li];
             LevelDev& C = h->lv[li - 1];
-            const T* rl = (li == L - 1) ? r : A::r(F);
-            T* xl = (li == L - 1) ? z : A::x(F);
+            const T* rl = (li == top) ? r : A::r(F);
+            T* xl = (li == top) ? z : A::x(F);
             if ((e = imgm::launch_blocks<T>(A::d(F), rl, xl, g, done, s)) != cudaSuccess) return e;
             if ((e = imgm::launch_apply<T>(A::d(F), imgm::RESID, xl, rl, A::t(F), nullptr, g, done, s)) != cudaSuccess)
                 return e;
@@ -291,10 +288,10 @@ cudaError_t enqueue_vcycle(imgm_handle* h, const T* r, T* z, const int*, cudaStr
                 return e;
         }
         if ((e = imgm::launch_vcycle_dsmem(h->dim, h->p, h->dsv, s)) != cudaSuccess) return e;
-        for (int li = ct + 1; li <= L - 1; ++li) {
+        for (int li = ct + 1; li <= top; ++li) {
             LevelDev& F = h->lv[li];
             LevelDev& C = h->lv[li - 1];
-            T* xl = (li == L - 1) ? z : A::x(F);
+            T* xl = (li == top) ? z : A::x(F);
             if ((e = imgm::launch_prolong<T>(A::d(F), A::d(C), A::x(C), A::e(F), xl, done, s)) != cudaSuccess)
                 return e;
             if ((e = imgm::launch_apply<T>(A::d(F), imgm::RESID_SMOOTH, A::e(F), A::t(F), A::t(F), xl, g, done, s)) !=
@@ -304,11 +301,11 @@ cudaError_t enqueue_vcycle(imgm_handle* h, const T* r, T* z, const int*, cudaStr
         }
         return cudaSuccess;
     }
-    for (int li = L - 1; li >= 1; --li) {
+    for (int li = top; li >= 1; --li) {
         LevelDev& F = h->lv[li];
         LevelDev& C = h->lv[li - 1];
-        const T* rl = (li == L - 1) ? r : A::r(F);
-        T* xl = (li == L - 1) ? z : A::x(F);
+        const T* rl = (li == top) ? r : A::r(F);
+        T* xl = (li == top) ? z : A::x(F);
         // line 4: x = gamma M^{-1} r (the one-function blocks were applied by the producer of r)
         if ((e = imgm::launch_blocks<T>(A::d(F), rl, xl, g, done, s)) != cudaSuccess) return e;
         // line 5: t = r - A x
@@ -322,10 +319,10 @@ cudaError_t enqueue_vcycle(imgm_handle* h, const T* r, T* z, const int*, cudaStr
     if ((e = imgm::launch_coarse<T>(h->c_rows, coarse_inverse<T>(h), h->nc, A::r(h->lv[0]), A::x(h->lv[0]), done, s)) !=
         cudaSuccess)
         return e;
-    for (int li = 1; li <= L - 1; ++li) {
+    for (int li = 1; li <= top; ++li) {
         LevelDev& F = h->lv[li];
         LevelDev& C = h->lv[li - 1];
-        T* xl = (li == L - 1) ? z : A::x(F);
+        T* xl = (li == top) ? z : A::x(F);
         // line 9: e = R^T x_c, x += e
         if ((e = imgm::launch_prolong<T>(A::d(F), A::d(C), A::x(C), A::e(F), xl, done, s)) != cudaSuccess) return e;
         // line 10: t -= A e; line 12 (one-function blocks): x += gamma dinv .* t
@@ -336,6 +333,42 @@ cudaError_t enqueue_vcycle(imgm_handle* h, const T* r, T* z, const int*, cudaStr
         if ((e = imgm::launch_blocks<T>(A::d(F), A::t(F), xl, g, done, s)) != cudaSuccess) return e;
     }
     return cudaSuccess;
+}
+
+// The V-cycle with its finest level in FP64 and the levels below it in FP32 on
+// Jacobi-scaled data (precision 2): the finest level's residual and its restriction keep
+// FP64, so the rounding of the coarse levels' input is that of a restricted FP64 residual.
+// On entry z = gamma dinv .* r (FP64), as for the FP64 V-cycle.
+cudaError_t enqueue_vcycle_hybrid(imgm_handle* h, const double* r, double* z, cudaStream_t s) {
+    const int L = h->L;
+    const double g = h->gamma;
+    LevelDev& F = h->lv[L - 1];
+    LevelDev& C = h->lv[L - 2];
+    cudaError_t e;
+    if ((e = imgm::launch_blocks<double>(F.d, r, z, g, nullptr, s)) != cudaSuccess) return e;
+    if ((e = imgm::launch_apply<double>(F.d, imgm::RESID, z, r, F.t, nullptr, g, nullptr, s)) != cudaSuccess) return e;
+    if ((e = imgm::launch_restrict_64to32(F.d, C.fd, F.t, C.fr, L - 2 >= 1 ? C.fx : nullptr, g, s)) != cudaSuccess)
+        return e;
+    if (L - 2 >= 1) {
+        if ((e = enqueue_vcycle_top<float>(h, L - 2, C.fr, C.fx, s)) != cudaSuccess) return e;
+    } else if ((e = imgm::launch_coarse<float>(h->c_rows, h->f_c_inv, h->nc, C.fr, C.fx, nullptr, s)) != cudaSuccess) {
+        return e;
+    }
+    if ((e = imgm::launch_prolong_32to64(F.d, C.fd, C.fx, F.e, z, s)) != cudaSuccess) return e;
+    if ((e = imgm::launch_apply<double>(F.d, imgm::RESID_SMOOTH, F.e, F.t, F.t, z, g, nullptr, s)) != cudaSuccess)
+        return e;
+    return imgm::launch_blocks<double>(F.d, F.t, z, g, nullptr, s);
+}
+
+template <typename T>
+cudaError_t enqueue_vcycle(imgm_handle* h, const T* r, T* z, const int*, cudaStream_t s) {
+    // The V-cycle kernels are not told the convergence flag: they touch only the V-cycle's
+    // own vectors, so the one V-cycle after convergence is harmless, while reading the flag
+    // would put a dependent memory round trip in front of every one of them.
+    if (h->smoother == 1) return enqueue_vcycle_mult<T>(h, r, z, nullptr, s);
+    if (std::is_same<T, double>::value && h->precision == 2)
+        return enqueue_vcycle_hybrid(h, reinterpret_cast<const double*>(r), reinterpret_cast<double*>(z), s);
+    return enqueue_vcycle_top<T>(h, h->L - 1, r, z, s);
 }
 
 // The whole CG solve on the handle's own vectors (cb -> cx): start, loop, final check.
@@ -357,7 +390,7 @@ cudaError_t enqueue_solve_start(imgm_handle* h, cudaStream_t s) {
     }
     if ((e = imgm::launch_scale_diag<double>(F.d, h->cr, h->cz, h->gamma_diag, done, s)) != cudaSuccess) return e;
     if ((e = enqueue_vcycle<double>(h, h->cr, h->cz, done, s)) != cudaSuccess) return e;
-    return imgm::launch_pcg_init_dir<double>(N, h->cr, h->cz, nullptr, h->cp, nullptr, h->partial, h->st, s);
+    return imgm::launch_pcg_init_dir<double>(N, h->cr, h->cz, nullptr, h->cp, h->czp, h->partial, h->st, s);
 }
 
 cudaError_t enqueue_iteration(imgm_handle* h, cudaStream_t s) {
@@ -379,9 +412,10 @@ cudaError_t enqueue_iteration(imgm_handle* h, cudaStream_t s) {
                                              h->gamma_diag, h->partial, h->st, h->hist, s)) != cudaSuccess)
         return e;
     if ((e = enqueue_vcycle<double>(h, h->cr, h->cz, done, s)) != cudaSuccess) return e;
-    if ((e = imgm::launch_pcg_rz<double>(N, h->cr, h->cz, nullptr, nullptr, h->partial, h->st, s)) != cudaSuccess)
+    // FP64 V-cycle: standard beta (czp null); FP32 levels below an FP64 finest one: flexible
+    if ((e = imgm::launch_pcg_rz<double>(N, h->cr, h->cz, nullptr, h->czp, h->partial, h->st, s)) != cudaSuccess)
         return e;
-    return imgm::launch_pcg_xpay<double>(N, h->cz, nullptr, h->cp, nullptr, h->st, s);
+    return imgm::launch_pcg_xpay<double>(N, h->cz, nullptr, h->cp, h->czp, h->st, s);
 }
 
 cudaError_t enqueue_solve_finish(imgm_handle* h, cudaStream_t s) {
@@ -693,7 +727,7 @@ int alloc_level_vectors(imgm_handle* h, LevelDev& dst) {
     CK(cudaMemset(dst.r, 0, N * sizeof(double)), "memset");
     CK(cudaMemset(dst.t, 0, N * sizeof(double)), "memset");
     CK(cudaMemset(dst.e, 0, N * sizeof(double)), "memset");
-    if (h->precision == 1) {
+    if (h->precision >= 1) {
         CK(h->alloc(&dst.fx, N), "alloc x32");
         CK(h->alloc(&dst.fr, N), "alloc r32");
         CK(h->alloc(&dst.ft, N), "alloc t32");
@@ -724,6 +758,10 @@ int alloc_context(imgm_handle* h) {
     CK(h->alloc(&h->cq, N), "alloc");
     CK(h->alloc(&h->cz, N), "alloc");
     CK(h->alloc(&h->cb, N), "alloc");
+    if (h->precision == 2) {
+        CK(h->alloc(&h->czp, N), "alloc");
+        CK(cudaMemset(h->czp, 0, N * sizeof(double)), "memset");
+    }
     CK(h->alloc(&h->partial, 2 * (size_t)imgm::reduction_blocks()), "alloc");
     CK(h->alloc(&h->st, 1), "alloc");
     CK(cudaMemset(h->st, 0, sizeof(PcgState)), "memset");
@@ -778,7 +816,7 @@ int upload_level(imgm_handle* h, const imgm::LevelData& src, LevelDev& dst, int 
     d.r_w = rw;
     d.t_first = tf;
     d.t_w = tw;
-    if (h->precision == 1) {
+    if (h->precision >= 1) {
         imgm::DevLevelT<float>& f = dst.fd;
         f.dim = d.dim;
         f.p = d.p;
@@ -821,7 +859,7 @@ int upload_level(imgm_handle* h, const imgm::LevelData& src, LevelDev& dst, int 
     if (src.ncolour > 0) {
         CK(h->upload(&dst.sg_row, src.sg_row), "upload one-function blocks");
         CK(h->upload(&dst.sg_inv, src.sg_inv), "upload one-function blocks");
-        if (h->precision == 1) CK(h->upload(&dst.f_sg_inv, src.f_sg_inv), "upload fp32 one-function blocks");
+        if (h->precision >= 1) CK(h->upload(&dst.f_sg_inv, src.f_sg_inv), "upload fp32 one-function blocks");
     }
     imgm_level_info& in = dst.info;
     in.n_grid = src.N;
@@ -913,7 +951,7 @@ int imgm_setup(const imgm_geometry* geom, const imgm_config* cfg, imgm_handle** 
         CK(h->upload(&h->c_rows, h->H.c_rows), "upload coarse rows");
         CK(h->upload(&h->c_inv, h->H.c_inv), "upload coarse inverse");
         h->nc = (int)h->H.c_rows.size();
-        if (h->precision == 1) CK(h->upload(&h->f_c_inv, h->H.f_c_inv), "upload fp32 coarse inverse");
+        if (h->precision >= 1) CK(h->upload(&h->f_c_inv, h->H.f_c_inv), "upload fp32 coarse inverse");
         CK(h->upload(&h->b, h->H.b), "upload rhs");
         int rc = alloc_context(h);
         if (rc != IMGM_OK) {

@@ -651,10 +651,13 @@ __global__ void __launch_bounds__(TPB) k_colour_smooth(DevLevelT<T> L, int64_t b
                     sm + (int64_t)wib * L.max_block);
 }
 
-template <typename T, int DIM, int P>
-__device__ __forceinline__ void restrict_rows(const DevLevelT<T>& F, const DevLevelT<T>& C, const T* __restrict__ rf,
-                                              T* __restrict__ rc, T* __restrict__ xc, T gamma, int64_t start,
+// fine level in type TF, coarse level in type TC (equal, or FP64 fine and FP32 coarse in
+// the V-cycle whose finest level is FP64); sums in TF
+template <typename TF, typename TC, int DIM, int P>
+__device__ __forceinline__ void restrict_rows(const DevLevelT<TF>& F, const DevLevelT<TC>& C, const TF* __restrict__ rf,
+                                              TC* __restrict__ rc, TC* __restrict__ xc, TC gamma, int64_t start,
                                               int64_t stride) {
+    using T = TF;
     constexpr int P2 = P + 2;
     const int mc = C.m, mf = F.m;
     const T* __restrict__ df = F.d;      // fine scale d (FP32 path) or nullptr
@@ -680,27 +683,30 @@ __device__ __forceinline__ void restrict_rows(const DevLevelT<T>& F, const DevLe
                 s = fmaT(wyz, t, s);
             }
         }
-        if (C.s) s *= ro(C.s + i);
+        if (C.s) s *= (T)ro(C.s + i);
         if (inactive) s = T(0);
-        rc[i] = s;
-        if (xc) xc[i] = gamma * ro(C.dinv + i) * s;
+        const TC sc = (TC)s;
+        rc[i] = sc;
+        if (xc) xc[i] = gamma * ro(C.dinv + i) * sc;
     }
 }
 
-template <typename T, int DIM, int P>
-__global__ void __launch_bounds__(TPB) k_restrict(DevLevelT<T> F, DevLevelT<T> C, const T* __restrict__ rf,
-                                                  T* __restrict__ rc, T* __restrict__ xc, T gamma, const int* done) {
+template <typename TF, typename TC, int DIM, int P>
+__global__ void __launch_bounds__(TPB) k_restrict(DevLevelT<TF> F, DevLevelT<TC> C, const TF* __restrict__ rf,
+                                                  TC* __restrict__ rc, TC* __restrict__ xc, TC gamma, const int* done) {
     pdl_begin();
     if (done && *done) return;
-    restrict_rows<T, DIM, P>(F, C, rf, rc, xc, gamma, (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
-                             (int64_t)gridDim.x * blockDim.x);
+    restrict_rows<TF, TC, DIM, P>(F, C, rf, rc, xc, gamma, (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
+                                  (int64_t)gridDim.x * blockDim.x);
 }
 
-template <typename T, int DIM, int P>
-__device__ __forceinline__ void prolong_rows(const DevLevelT<T>& F, const DevLevelT<T>& C, const T* __restrict__ xc,
-                                             T* __restrict__ e, T* __restrict__ x, int64_t start, int64_t stride) {
+// fine level in type TF, coarse in TC (see restrict_rows); sums in TF
+template <typename TF, typename TC, int DIM, int P>
+__device__ __forceinline__ void prolong_rows(const DevLevelT<TF>& F, const DevLevelT<TC>& C, const TC* __restrict__ xc,
+                                             TF* __restrict__ e, TF* __restrict__ x, int64_t start, int64_t stride) {
+    using T = TF;
     const int mc = C.m, mf = F.m, TW = F.TW;
-    const T* __restrict__ sc = C.s;      // coarse scale 1/d (FP32 path) or nullptr
+    const TC* __restrict__ sc = C.s;     // coarse scale 1/d (FP32 path) or nullptr
     for (int64_t a = start; a < F.N; a += stride) {
         const bool inactive = F.rowinfo[a] == -2;    // applied at the end (overlapping loads)
         const int ax = (int)(a % mf), ay = (int)((a / mf) % mf), az = (DIM == 3) ? (int)(a / ((int64_t)mf * mf)) : 0;
@@ -715,7 +721,8 @@ __device__ __forceinline__ void prolong_rows(const DevLevelT<T>& F, const DevLev
                 const T wyz = ro(wy + ty) * wzk;
                 const int64_t rb = (int64_t)cx + (int64_t)mc * ((cy + ty) + (DIM == 3 ? (int64_t)mc * (cz + tz) : 0));
                 T t = T(0);
-                for (int tx = 0; tx < TW; ++tx) t = fmaT(ro(wx + tx), sc ? xc[rb + tx] * ro(sc + rb + tx) : xc[rb + tx], t);
+                for (int tx = 0; tx < TW; ++tx)
+                    t = fmaT(ro(wx + tx), (T)(sc ? xc[rb + tx] * ro(sc + rb + tx) : xc[rb + tx]), t);
                 s = fmaT(wyz, t, s);
             }
         }
@@ -726,13 +733,13 @@ __device__ __forceinline__ void prolong_rows(const DevLevelT<T>& F, const DevLev
     }
 }
 
-template <typename T, int DIM, int P>
-__global__ void __launch_bounds__(TPB) k_prolong(DevLevelT<T> F, DevLevelT<T> C, const T* __restrict__ xc,
-                                                 T* __restrict__ e, T* __restrict__ x, const int* done) {
+template <typename TF, typename TC, int DIM, int P>
+__global__ void __launch_bounds__(TPB) k_prolong(DevLevelT<TF> F, DevLevelT<TC> C, const TC* __restrict__ xc,
+                                                 TF* __restrict__ e, TF* __restrict__ x, const int* done) {
     pdl_begin();
     if (done && *done) return;
-    prolong_rows<T, DIM, P>(F, C, xc, e, x, (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
-                            (int64_t)gridDim.x * blockDim.x);
+    prolong_rows<TF, TC, DIM, P>(F, C, xc, e, x, (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
+                                 (int64_t)gridDim.x * blockDim.x);
 }
 
 // one warp per kept coarse row
@@ -1492,7 +1499,24 @@ template <typename T>
 cudaError_t launch_restrict(const DevLevelT<T>& F, const DevLevelT<T>& C, const T* rf, T* rc, T* xc, double gamma,
                             const int* done, cudaStream_t s) {
     const RowLaunch rl = row_launch(C.N);
-    IMGM_DISPATCH(F.dim, F.p, (launch_pdl(k_restrict<T, D, Q>, rl.grid, rl.block, 0, s, F, C, rf, rc, xc, (T)gamma, done)));
+    IMGM_DISPATCH(F.dim, F.p, (launch_pdl(k_restrict<T, T, D, Q>, rl.grid, rl.block, 0, s, F, C, rf, rc, xc, (T)gamma, done)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_restrict_64to32(const DevLevel& F, const DevLevelT<float>& C, const double* rf, float* rc, float* xc,
+                                   double gamma, cudaStream_t s) {
+    const RowLaunch rl = row_launch(C.N);
+    const int* done = nullptr;
+    IMGM_DISPATCH(F.dim, F.p,
+                  (launch_pdl(k_restrict<double, float, D, Q>, rl.grid, rl.block, 0, s, F, C, rf, rc, xc, (float)gamma, done)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prolong_32to64(const DevLevel& F, const DevLevelT<float>& C, const float* xc, double* e, double* x,
+                                  cudaStream_t s) {
+    const RowLaunch rl = row_launch(F.N);
+    const int* done = nullptr;
+    IMGM_DISPATCH(F.dim, F.p, (launch_pdl(k_prolong<double, float, D, Q>, rl.grid, rl.block, 0, s, F, C, xc, e, x, done)));
     return cudaGetLastError();
 }
 
@@ -1500,7 +1524,7 @@ template <typename T>
 cudaError_t launch_prolong(const DevLevelT<T>& F, const DevLevelT<T>& C, const T* xc, T* e, T* x, const int* done,
                            cudaStream_t s) {
     const RowLaunch rl = row_launch(F.N);
-    IMGM_DISPATCH(F.dim, F.p, (launch_pdl(k_prolong<T, D, Q>, rl.grid, rl.block, 0, s, F, C, xc, e, x, done)));
+    IMGM_DISPATCH(F.dim, F.p, (launch_pdl(k_prolong<T, T, D, Q>, rl.grid, rl.block, 0, s, F, C, xc, e, x, done)));
     return cudaGetLastError();
 }
 

@@ -85,6 +85,12 @@ cudaError_t launch_restrict(const DevLevelT<T>& F, const DevLevelT<T>& C, const 
 template <typename T>
 cudaError_t launch_prolong(const DevLevelT<T>& F, const DevLevelT<T>& C, const T* xc, T* e, T* x, const int* done,
                            cudaStream_t s);
+// the transfers between an FP64 finest level and the FP32 (Jacobi-scaled) level below it:
+// rc = D_c^{-1} R rf (and xc = gamma dinv_c .* rc when xc != nullptr), e = R^T D_c^{-1} xc, x += e
+cudaError_t launch_restrict_64to32(const DevLevel& F, const DevLevelT<float>& C, const double* rf, float* rc, float* xc,
+                                   double gamma, cudaStream_t s);
+cudaError_t launch_prolong_32to64(const DevLevel& F, const DevLevelT<float>& C, const float* xc, double* e, double* x,
+                                  cudaStream_t s);
 // x[rows] = Cinv r[rows] (dense coarsest-level inverse, row-major nc x nc)
 template <typename T>
 cudaError_t launch_coarse(const int32_t* rows, const T* Cinv, int nc, const T* r, T* x, const int* done,

@@ -1472,7 +1472,7 @@ struct Builder {
         for (int li = L - 1; li >= 1; --li)
             if (!build_blocks(li, err)) return false;
         phase("Schwarz blocks");
-        if (pb.precision == 1) build_fp32();
+        if (pb.precision >= 1) build_fp32();
         phase("FP32 copies");
         return true;
     }
@@ -1492,7 +1492,11 @@ bool build_hierarchy(const Problem& pb, Hierarchy& H, std::string& err) {
     if (pb.depth < 0 || pb.depth > 6) { err = "depth must be in 0..6"; return false; }
     if (pb.bc != 0 && pb.bc != 1) { err = "bc must be 0 (penalty) or 1 (Nitsche)"; return false; }
     if (!(pb.hi > pb.lo)) { err = "hi must exceed lo"; return false; }
-    if (pb.precision != 0 && pb.precision != 1) { err = "precision must be 0 (FP64) or 1 (FP32 V-cycle)"; return false; }
+    if (pb.precision < 0 || pb.precision > 2) {
+        err = "precision must be 0 (FP64), 1 (FP32 V-cycle) or 2 (FP64 finest level, FP32 below)";
+        return false;
+    }
+    if (pb.precision == 2 && pb.smoother != 0) { err = "precision 2 is built for the additive smoother only"; return false; }
     if (pb.smoother != 0 && pb.smoother != 1) { err = "smoother must be 0 (additive) or 1 (multiplicative)"; return false; }
     double Nd = std::pow((double)(pb.n + pb.p), pb.dim);
     if (Nd > 2.0e9) { err = "grid too large for 32-bit row indices"; return false; }

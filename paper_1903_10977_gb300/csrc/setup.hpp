@@ -19,7 +19,7 @@ struct Problem {
     double lo = 0.0, hi = 1.0;
     int n = 32, basis = 0, p = 2, levels = 3, depth = 0, bc = 1;
     double gamma = 0.0;
-    int precision = 0;   // 0: FP64 V-cycle, 1: FP32 V-cycle (FP32 copies are built)
+    int precision = 0;   // 0: FP64 V-cycle, 1: FP32 V-cycle, 2: FP64 finest level + FP32 below (FP32 copies for 1, 2)
     int smoother = 0;    // 0: additive Schwarz, 1: coloured multiplicative Schwarz
 };
 

@@ -142,6 +142,8 @@ def test_coarse_inverse(pair):
     (dict(basis=1, degree=2), "Lagrange"),
     (dict(levels=1), "levels"),
     (dict(n=256, levels=2), "dense inverse allows at most"),   # coarsest level too large to invert densely
+    (dict(precision=3), "precision"),
+    (dict(precision=2, smoother=1), "additive smoother only"),
 ])
 def test_invalid_configurations_are_rejected(kw, err):
     args = dict(dim=2, centers=[[0.5, 0.5]], radii=[0.2], n=32, degree=2, levels=3, depth=0, bc=1, host_only=True)
