@@ -18,8 +18,9 @@ of the published methods it uses:
   omega = (r1 . c) / (c . A c) that minimises the A-norm of the error left in the
   correction equation A e = r (omega = 0 when c . A c is not positive);
 * training data: the V-cycle's own residual/error pairs, e1 = (I - B A) e0 and
-  r1 = A e1 for random e0, both divided by the root mean square of e1 over the active
-  functions; the loss is the masked squared error sum_v m_v (N(r1)_v - e1_v)^2 times a
+  r1 = A e1 for random e0, each divided by its own root mean square over the active
+  functions (A scales with the mesh size, so the pair is learned as a map between shapes
+  and the stage's step omega restores the size); the loss is the masked squared error sum_v m_v (N(r1)_v - e1_v)^2 times a
   caller-given scale (1 / number of active functions);
 * gradients by the chain rule (reverse mode), Adam (Kingma and Ba, 2015, Algorithm 1)
   with bias correction on FP32 master weights;
@@ -98,6 +99,7 @@ def conv3d_weight_grad(dy, x):
 def forward(w, r_grid, mask, bf16: bool = True):
     """N(r) on a grid (nz, ny, nx) with the active mask (same shape, 0/1).
 
+    The network sees the input on the active functions only (zero elsewhere).
     Returns the output (masked, FP64) and the activations (input, a1, a2) as stored.
     With bf16, the weights, the input and the hidden activations are rounded to bfloat16
     where the kernels store them; the sums and the output stay exact.
@@ -105,7 +107,8 @@ def forward(w, r_grid, mask, bf16: bool = True):
     Ws = split_weights(w)
     rnd = round_bf16 if bf16 else (lambda v: v)
     Ws = [rnd(W) for W in Ws]
-    x = (to_input(r_grid) if bf16 else np.asarray(r_grid, dtype=np.float64))[None]
+    r_grid = np.asarray(r_grid, dtype=np.float64) * mask
+    x = (to_input(r_grid) if bf16 else r_grid)[None]
     a1 = rnd(np.maximum(conv3d(x, Ws[0]), 0.0))
     a2 = rnd(np.maximum(conv3d(a1, Ws[1]), 0.0))
     out = conv3d(a2, Ws[2])[0] * mask
@@ -146,13 +149,12 @@ class Adam:
         return w - self.lr * mhat / (np.sqrt(vhat) + self.eps)
 
 
-def training_pair(A, precondition, e0, active_mask_full=None):
+def training_pair(A, precondition, e0):
     """One V-cycle's residual/error pair from a random error e0 (active functions):
-    e1 = e0 - B A e0, r1 = A e1, both divided by rms(e1)."""
+    e1 = e0 - B A e0, r1 = A e1, each divided by its own root mean square."""
     e1 = e0 - precondition(A @ e0)
     r1 = A @ e1
-    s = np.sqrt(np.mean(e1 * e1))
-    return r1 / s, e1 / s
+    return r1 / np.sqrt(np.mean(r1 * r1)), e1 / np.sqrt(np.mean(e1 * e1))
 
 
 def stage(A, r, z, net):
