@@ -46,6 +46,10 @@ def workload_name(pr) -> str:
     basis = "bspline" if pr.basis == 0 else "lagrange"
     return f"poisson{pr.dim}d-{size}-{holes}-{basis}-p{pr.degree}-{pr.levels}levels-depth{pr.depth}-nitsche"
 RTOL = 1e-8
+# learned stage (--learned): training geometries of the workload's hole layout at
+# LEARN_N^3, pairs per geometry, Adam steps, pairs per step, step size
+LEARN_GEOMS, LEARN_N, LEARN_PAIRS, LEARN_STEPS, LEARN_BATCH, LEARN_LR = 4, 64, 8, 800, 4, 1e-3
+FP32_PEAK_NOTE = "152 SMs x 128 FP32 FMA/clk x 2 flop x 2070 MHz"
 MAXIT = 2000
 FP64_PEAK_NOTE = "152 SMs x 2 FP64 FMA/clk x 2 flop x 2070 MHz"
 CPU_SAMPLE_N, CPU_SAMPLE_LEVELS = 128, 4
@@ -272,6 +276,77 @@ def apply_flops(S) -> float:
     return (8 * (2 * p + 1) if d == 2 else 16 * (2 * p + 1)) * tensor_rows + 2 * (2 * p + 1) ** d * info["n_band"]
 
 
+def run_learned(args, lib, torch, pr, S64, timed_solves, total_units, t64, res64):
+    """The learned stage on a 3-D workload: train the network on the V-cycle's own
+    residual/error pairs of LEARN_GEOMS seeded geometries of the same hole layout at
+    LEARN_N^3 (one level fewer), then time the FP64 solve of the workload with the stage
+    against the plain FP64 solve (same solver, same right-hand side, same tolerance)."""
+    from synthetic import config_layout, initial_weights, preset, random_error
+    tr = preset(args.workload, n=LEARN_N, levels=pr.levels - 1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    pairs, shape = [], None
+    for g in range(LEARN_GEOMS):
+        lay_g = config_layout(tr.layout, 1000 + g)
+        Sg = lib.Solver(tr.dim, lay_g.centers, lay_g.radii, tr.n, tr.degree, tr.levels, tr.depth, tr.bc,
+                        basis=tr.basis, precision=0)
+        m = Sg.level_info(Sg.L)["m"]
+        shape = (m, m, m)
+        mask_h = Sg.active_mask()
+        mask = torch.as_tensor(mask_h, device="cuda")
+        for k in range(LEARN_PAIRS):
+            e0 = torch.as_tensor(random_error(mask_h.size, 10_000 * g + k) * mask_h, device="cuda")
+            r1, e1 = Sg.learned_pair(e0)
+            pairs.append((r1, e1, mask))
+        torch.cuda.synchronize()
+        Sg.close()
+    t_pairs = time.perf_counter() - t0
+    net = lib.Net(initial_weights(args.seed))
+    t1 = time.perf_counter()
+    losses = lib.train_net(net, pairs, shape, steps=LEARN_STEPS, lr=LEARN_LR, batch=LEARN_BATCH).cpu().numpy()
+    t_train = time.perf_counter() - t1
+    # the network's forward pass on the workload's grid alone (20 launches after warm-up)
+    info = S64.level_info(S64.L)
+    m = info["m"]
+    mask_w = torch.as_tensor(S64.active_mask(), device="cuda")
+    xin = torch.randn(info["n_grid"], dtype=torch.float64, device="cuda") * mask_w
+    yout = torch.empty_like(xin)
+    for _ in range(3):
+        net.forward(xin, (m, m, m), mask=mask_w, out=yout)
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stream = torch.cuda.current_stream()
+    f0.record(stream)
+    for _ in range(20):
+        net.forward(xin, (m, m, m), mask=mask_w, out=yout)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    fwd_ms = f0.elapsed_time(f1) / 20
+    fwd_flops = 2.0 * m ** 3 * 27 * (16 + 16 * 16 + 16)
+    S64.set_net(net)
+    t_l, res_l = timed_solves(S64, args.steps, args.warmup, "solve_learned")
+    S64.set_net(None)
+    net.close()
+    return {
+        "value": total_units / t_l, "unit": "DOF/s", "ms_per_step": 1e3 * t_l / args.steps,
+        "iterations": res_l[0]["iterations"], "true_rel_residual": res_l[-1]["true_rel_residual"],
+        "gpu_launches_per_solve": int(res_l[0]["kernel_launches"]),
+        "plain_fp64": {"value": total_units / t64, "ms_per_step": 1e3 * t64 / args.steps,
+                       "iterations": res64[0]["iterations"],
+                       "gpu_launches_per_solve": int(res64[0]["kernel_launches"])},
+        "speedup_vs_plain_fp64": t64 / t_l,
+        "training": {"geometries": LEARN_GEOMS, "n": LEARN_N, "levels": tr.levels, "pairs": len(pairs),
+                     "steps": LEARN_STEPS, "batch": LEARN_BATCH, "lr": LEARN_LR, "pairs_s": t_pairs,
+                     "train_s": t_train, "loss_first": float(losses[:4].mean()),
+                     "loss_last": float(losses[-20:].mean())},
+        "stage": "z += omega N(r - A z) after every FP64 V-cycle, Polak-Ribiere beta",
+        "forward": {"ms": fwd_ms, "flops": fwd_flops, "achieved_tflops": fwd_flops / (fwd_ms * 1e-3) / 1e12,
+                    "peak_tflops": 152 * 128 * 2 * 2.07e9 / 1e12, "peak_source": "derived: " + FP32_PEAK_NOTE,
+                    "frac": fwd_flops / (fwd_ms * 1e-3) / (152 * 128 * 2 * 2.07e9),
+                    "kernels": "k_pack + 3 x k_conv (FP32 FMA on CUDA cores, bf16 storage)",
+                    "timing": "20 stream launches of the whole forward, CUDA events"},
+    }
+
+
 def run_ours(args, rank, world, local_rank):
     import numpy as np
     import torch
@@ -342,6 +417,9 @@ def run_ours(args, rank, world, local_rank):
         t_mult, res_mult = timed_solves(SM, args.steps, args.warmup, "solve_multiplicative")
         SM.close()
         batched = run_batched(lib, torch, mixed, max(1, args.steps // 2), 1)
+    learned = None
+    if args.learned and pr.dim == 3:
+        learned = run_learned(args, lib, torch, pr, S64, timed_solves, n_active * args.steps, t64, res64)
 
     # end to end: host (pinned) b in, host x out, through the C-ABI
     bh = torch.empty(n_grid, dtype=torch.float64, pin_memory=True)
@@ -424,6 +502,7 @@ def run_ours(args, rank, world, local_rank):
             "gpu_launches_per_solve": int(res_mult[0]["kernel_launches"]),
             "smoother": "coloured multiplicative Schwarz, same precision as the headline"},
         "batched": batched,
+        "learned": learned,
         "vcycle": vcycle,
         "e2e": {"value": total_units / t_e2e, "unit": "DOF/s", "h2d_bytes_per_step": 8 * n_grid,
                 "d2h_bytes_per_step": 8 * n_grid},
@@ -481,6 +560,8 @@ def main():
     ap.add_argument("--workload", default=PRESET, choices=WORKLOADS,
                     help="the headline is the 512x512 quadratic B-spline workload; the others are the other "
                          "configurations of the same study")
+    ap.add_argument("--learned", action="store_true",
+                    help="3-D workloads: also train the learned stage and time the FP64 solve with it")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64", "hybrid"],
                     help="V-cycle arithmetic of the timed solves (the FP64 path is timed beside it)")
     args = ap.parse_args()

@@ -208,6 +208,65 @@ int imgm_batch_solve(imgm_batch* b, const double* const* dev_b, double* const* d
 
 void imgm_batch_destroy(imgm_batch* b);
 
+/* ---- Learned correction stage ------------------------------------------------------
+ * An extension beside the paper's method (which has no learned part): after the V-cycle
+ * of Algorithm 1 gives z = B r, a small network proposes c = N(r - A z) and z becomes
+ * z + omega c with omega = ((r - A z) . c) / (c . A c), the step that minimises the A-norm
+ * of the error of A e = r along c (omega = 0 unless c . A c > 0).  CG then takes the
+ * Polak-Ribiere beta z_{k+1} . (r_{k+1} - r_k) / (z_k . r_k), as the preconditioner now
+ * varies from step to step.
+ *
+ * N: three 3-D convolutions on the grid of basis functions (1 -> 16 -> 16 -> 1 channels,
+ * 3 x 3 x 3 kernels, zero padding, no biases, ReLU after the first two), weights read as
+ * bfloat16, activations stored as bfloat16, sums in FP32.  The input is rounded FP64 ->
+ * FP32 -> bfloat16 and zeroed off the mask; the output is zero off the mask.
+ * Weights: IMGM_NET_WEIGHTS floats, layer by layer, each layer [tap][out][in] with
+ * tap = 9 (dz + 1) + 3 (dy + 1) + (dx + 1); a grid vector of nx * ny * nz entries is
+ * indexed x + nx (y + ny z) (a finest-level vector of a 3-D problem: nx = ny = nz = m).
+ * Network calls report errors through imgm_last_error(NULL). */
+#define IMGM_NET_WEIGHTS 7776
+
+typedef struct imgm_net imgm_net;
+
+/* A network with the given FP32 weights (host array, copied) and zero Adam state. */
+int imgm_net_create(const float* host_weights, imgm_net** out);
+/* Frees the network (waits for the device).  Detach it from every handle first. */
+void imgm_net_destroy(imgm_net* net);
+/* Copies the FP32 master weights / the gradient accumulator to the host (waits). */
+int imgm_net_get_weights(const imgm_net* net, float* host_weights);
+int imgm_net_get_grads(const imgm_net* net, float* host_grads);
+
+/* dev_out = N(dev_in) on an nx x ny x nz grid (device doubles; dev_mask: device bytes,
+ * 1 = active, or NULL for all).  Uses the network's own activation buffers (grown on
+ * demand, which waits for the stream), so calls on one network must not overlap. */
+int imgm_net_forward(imgm_net* net, int nx, int ny, int nz, const double* dev_in, const uint8_t* dev_mask,
+                     double* dev_out, void* stream);
+
+/* Training.  zero_grad clears the gradient accumulator; accumulate adds the gradient of
+ * L = scale * sum_v m_v (N(in)_v - target_v)^2 (reverse mode through the stored
+ * activations) and adds L to dev_loss[0] (a device double the caller zeroes);
+ * adam_step applies one Adam step (Kingma and Ba, 2015) with bias correction to the
+ * FP32 weights and refreshes their bfloat16 copies. */
+int imgm_net_zero_grad(imgm_net* net, void* stream);
+int imgm_net_accumulate(imgm_net* net, int nx, int ny, int nz, const double* dev_in, const double* dev_target,
+                        const uint8_t* dev_mask, double scale, double* dev_loss, void* stream);
+int imgm_net_adam_step(imgm_net* net, float lr, float beta1, float beta2, float eps, void* stream);
+
+/* Attaches net to h's solves (NULL detaches): imgm_pcg_solve then runs the stage after
+ * every V-cycle.  The network must outlive the attachment.  IMGM_ERR_UNSUPPORTED for a
+ * 2-D problem or precision 1 (the stage follows an FP64 V-cycle output).  Rebuilds the
+ * solve graph on the next solve; batches created earlier keep the plain V-cycle. */
+int imgm_set_net(imgm_handle* h, imgm_net* net);
+
+/* One stage with the attached network: dev_z (in: B dev_r, out: the corrected value);
+ * dev_omega (device double, may be NULL) receives omega. */
+int imgm_learned_stage(imgm_handle* h, const double* dev_r, double* dev_z, double* dev_omega, void* stream);
+
+/* A training pair from the V-cycle of h: e1 = e0 - B A e0, r1 = A e1, each divided by its
+ * own root mean square over the active functions (dev_e0 active-supported; three distinct
+ * device vectors of n_grid doubles). */
+int imgm_learned_pair(imgm_handle* h, const double* dev_e0, double* dev_r1, double* dev_e1, void* stream);
+
 /* ---- Setup inspection (host only; no GPU needed) --------------------------------
  * imgm_setup_host builds the same hierarchy as imgm_setup without touching the GPU;
  * such a handle serves only the imgm_host_* calls below, imgm_levels,

@@ -82,7 +82,19 @@ _SIGS = {
     "imgm_batch_create": (_I, [ctypes.POINTER(_H), _I, ctypes.POINTER(_P)]),
     "imgm_batch_solve": (_I, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), _D, _I, ctypes.POINTER(Result), _P]),
     "imgm_batch_destroy": (None, [_P]),
+    "imgm_net_create": (_I, [_P, ctypes.POINTER(_P)]),
+    "imgm_net_destroy": (None, [_P]),
+    "imgm_net_get_weights": (_I, [_P, _P]),
+    "imgm_net_get_grads": (_I, [_P, _P]),
+    "imgm_net_forward": (_I, [_P, _I, _I, _I, _P, _P, _P, _P]),
+    "imgm_net_zero_grad": (_I, [_P, _P]),
+    "imgm_net_accumulate": (_I, [_P, _I, _I, _I, _P, _P, _P, _D, _P, _P]),
+    "imgm_net_adam_step": (_I, [_P, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, _P]),
+    "imgm_set_net": (_I, [_H, _P]),
+    "imgm_learned_stage": (_I, [_H, _P, _P, _P, _P]),
+    "imgm_learned_pair": (_I, [_H, _P, _P, _P, _P]),
 }
+NET_WEIGHTS = 7776
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(_lib, _name)
     _f.restype = _res
@@ -238,6 +250,26 @@ class Solver:
             hbuf = hbuf[: res.iterations + 1]
         return x, out, hbuf
 
+    # ------------------------------------------------------ learned stage
+    def set_net(self, net: "Net | None"):
+        """Attach a network to this context's solves (None detaches); see imgm_set_net."""
+        self._check(_lib.imgm_set_net(self._h, net._n if net is not None else None))
+        self._net = net               # keeps the network alive while attached
+
+    def learned_stage(self, r, z, omega=None, stream=None):
+        """z <- z + omega N(r - A z) in place with the attached network (z = B r on entry)."""
+        self._check(_lib.imgm_learned_stage(self._h, _ptr(r), _ptr(z), _ptr(omega) if omega is not None else None,
+                                            _stream(stream)))
+        return z
+
+    def learned_pair(self, e0, r1=None, e1=None, stream=None):
+        """Training pair of the V-cycle: e1 = e0 - B A e0, r1 = A e1, each divided by its own rms."""
+        import torch
+        r1 = torch.empty_like(e0) if r1 is None else r1
+        e1 = torch.empty_like(e0) if e1 is None else e1
+        self._check(_lib.imgm_learned_pair(self._h, _ptr(e0), _ptr(r1), _ptr(e1), _stream(stream)))
+        return r1, e1
+
     def residual_norm2(self, b, x, out=None, stream=None):
         """||b - A x||^2 on the finest level, into a one-element CUDA tensor."""
         import torch
@@ -361,3 +393,94 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def _mask_ptr(mask):
+    import torch
+    if mask is None:
+        return None
+    if not isinstance(mask, torch.Tensor) or not mask.is_cuda or mask.dtype != torch.uint8 or not mask.is_contiguous():
+        raise TypeError("expected a contiguous uint8 CUDA mask")
+    return ctypes.c_void_p(mask.data_ptr())
+
+
+class Net:
+    """The learned stage's network (imgm_net): FP32 master weights, Adam state, bf16 copies.
+
+    weights: IMGM_NET_WEIGHTS floats, layers 1 -> 16 -> 16 -> 1, each [tap][out][in]."""
+
+    def __init__(self, weights):
+        w = np.ascontiguousarray(np.asarray(weights, dtype=np.float32).reshape(-1))
+        if w.size != NET_WEIGHTS:
+            raise ValueError(f"expected {NET_WEIGHTS} weights, got {w.size}")
+        n = _P()
+        rc = _lib.imgm_net_create(w.ctypes.data_as(ctypes.c_void_p), ctypes.byref(n))
+        if rc != IMGM_OK:
+            raise ImgmError(f"network creation failed ({ERRORS.get(rc, rc)}): {_lib.imgm_last_error(None).decode()}")
+        self._n = n
+
+    def _check(self, rc):
+        if rc < 0:
+            raise ImgmError(f"{ERRORS.get(rc, rc)}: {_lib.imgm_last_error(None).decode()}")
+        return rc
+
+    def close(self):
+        if getattr(self, "_n", None):
+            _lib.imgm_net_destroy(self._n)
+            self._n = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def weights(self) -> np.ndarray:
+        out = np.zeros(NET_WEIGHTS, dtype=np.float32)
+        self._check(_lib.imgm_net_get_weights(self._n, out.ctypes.data_as(ctypes.c_void_p)))
+        return out
+
+    def grads(self) -> np.ndarray:
+        out = np.zeros(NET_WEIGHTS, dtype=np.float32)
+        self._check(_lib.imgm_net_get_grads(self._n, out.ctypes.data_as(ctypes.c_void_p)))
+        return out
+
+    def forward(self, x, shape, mask=None, out=None, stream=None):
+        """N(x) on a grid of shape (nz, ny, nx) (x: float64 CUDA vector, x fastest)."""
+        import torch
+        nz, ny, nx = shape
+        out = torch.empty_like(x) if out is None else out
+        self._check(_lib.imgm_net_forward(self._n, nx, ny, nz, _ptr(x), _mask_ptr(mask), _ptr(out), _stream(stream)))
+        return out
+
+    def zero_grad(self, stream=None):
+        self._check(_lib.imgm_net_zero_grad(self._n, _stream(stream)))
+
+    def accumulate(self, x, target, shape, loss, mask=None, scale=1.0, stream=None):
+        """Adds the gradient of scale * sum m (N(x) - target)^2; adds the loss to loss[0]."""
+        nz, ny, nx = shape
+        self._check(_lib.imgm_net_accumulate(self._n, nx, ny, nz, _ptr(x), _ptr(target), _mask_ptr(mask), scale,
+                                             _ptr(loss), _stream(stream)))
+
+    def adam_step(self, lr, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+        self._check(_lib.imgm_net_adam_step(self._n, lr, beta1, beta2, eps, _stream(stream)))
+
+
+def train_net(net: Net, pairs, shape, steps: int, lr: float = 1e-3, batch: int = 1, stream=None):
+    """Adam on the V-cycle's residual/error pairs [(r1, e1, mask), ...] on grids of one
+    shape (nz, ny, nx) (mask: uint8 CUDA vector of the pair's active functions): each step
+    accumulates the gradient of `batch` pairs, taken in turn, and applies one update.  The
+    loss of a pair is scaled by 1 / (batch * its number of active functions).  Returns
+    the per-step losses (device tensor)."""
+    import torch
+    losses = torch.zeros(steps, dtype=torch.float64, device="cuda")
+    scales = [1.0 / (batch * max(int(m.sum().item()), 1)) for _, _, m in pairs]
+    k = 0
+    for it in range(steps):
+        net.zero_grad(stream)
+        for _ in range(batch):
+            r1, e1, mask = pairs[k % len(pairs)]
+            net.accumulate(r1, e1, shape, losses[it:it + 1], mask=mask, scale=scales[k % len(pairs)], stream=stream)
+            k += 1
+        net.adam_step(lr, stream=stream)
+    return losses

@@ -21,6 +21,7 @@
 
 #include "../../include/imgm.h"
 #include "kernels.cuh"
+#include "learned.cuh"
 #include "setup.hpp"
 
 using imgm::DevLevel;
@@ -83,6 +84,20 @@ struct SharedData {
     }
 };
 
+// The learned stage's network: FP32 master weights, gradient and Adam moments, the bf16
+// copies the convolutions read, and the activations of the last standalone call.
+struct imgm_net {
+    float *w = nullptr, *g = nullptr, *m = nullptr, *v = nullptr;
+    uint16_t *wb = nullptr, *wbt = nullptr;
+    int64_t t = 0;                 // Adam steps taken
+    imgm::NetWorkspace ws;
+    ~imgm_net() {
+        for (void* p : {(void*)w, (void*)g, (void*)m, (void*)v, (void*)wb, (void*)wbt})
+            if (p) cudaFree(p);
+        ws.release();
+    }
+};
+
 struct imgm_handle {
     std::shared_ptr<SharedData> sh;
     imgm::Hierarchy& H;
@@ -121,6 +136,12 @@ struct imgm_handle {
     bool graph_failed = false;
     cudaStream_t capture = nullptr;    // the solve graph is captured here (the caller's stream may be the legacy one)
     int64_t graph_kernels[3] = {0, 0, 0};   // kernel nodes of the solve graph: start, loop body, finish
+    // learned stage (dim 3, FP64 V-cycle output): the attached network, its activations on
+    // the finest grid, the stage's vectors (r1 = r - A z, c = N(r1), A c), the active mask
+    imgm_net* net = nullptr;
+    imgm::NetWorkspace lws;
+    double *l_r1 = nullptr, *l_c = nullptr, *l_q = nullptr;
+    uint8_t* l_mask = nullptr;
     std::string err;
 
     template <class T>
@@ -147,6 +168,7 @@ struct imgm_handle {
         if (exec) cudaGraphExecDestroy(exec);
         if (capture) cudaStreamDestroy(capture);
         if (graph) cudaGraphDestroy(graph);
+        lws.release();
         for (void* v : allocs) cudaFree(v);
     }
 };
@@ -371,6 +393,21 @@ cudaError_t enqueue_vcycle(imgm_handle* h, const T* r, T* z, const int*, cudaStr
     return enqueue_vcycle_top<T>(h, h->L - 1, r, z, s);
 }
 
+// The learned stage on the FP64 V-cycle's output: z += omega N(r - A z) with the
+// energy-minimising omega = (r1 . c) / (c . A c) (0 unless positive curvature).
+cudaError_t enqueue_learned(imgm_handle* h, const double* r, double* z, double* omega_out, cudaStream_t s) {
+    LevelDev& F = h->lv[h->L - 1];
+    const int64_t N = F.d.N;
+    cudaError_t e;
+    if ((e = imgm::launch_apply<double>(F.d, imgm::RESID, z, r, h->l_r1, nullptr, h->gamma, nullptr, s)) != cudaSuccess)
+        return e;
+    if ((e = imgm::net_forward(h->net->wb, h->lws, h->l_r1, h->l_mask, h->l_c, nullptr, s)) != cudaSuccess) return e;
+    if ((e = imgm::launch_apply<double>(F.d, imgm::APPLY, h->l_c, nullptr, h->l_q, nullptr, 0.0, nullptr, s)) !=
+        cudaSuccess)
+        return e;
+    return imgm::stage_update(N, h->l_r1, h->l_c, h->l_q, z, h->lws.partial, omega_out, s);
+}
+
 // The whole CG solve on the handle's own vectors (cb -> cx): start, loop, final check.
 cudaError_t enqueue_solve_start(imgm_handle* h, cudaStream_t s) {
     LevelDev& F = h->lv[h->L - 1];
@@ -390,6 +427,7 @@ cudaError_t enqueue_solve_start(imgm_handle* h, cudaStream_t s) {
     }
     if ((e = imgm::launch_scale_diag<double>(F.d, h->cr, h->cz, h->gamma_diag, done, s)) != cudaSuccess) return e;
     if ((e = enqueue_vcycle<double>(h, h->cr, h->cz, done, s)) != cudaSuccess) return e;
+    if (h->net && (e = enqueue_learned(h, h->cr, h->cz, nullptr, s)) != cudaSuccess) return e;
     return imgm::launch_pcg_init_dir<double>(N, h->cr, h->cz, nullptr, h->cp, h->czp, h->partial, h->st, s);
 }
 
@@ -412,6 +450,14 @@ cudaError_t enqueue_iteration(imgm_handle* h, cudaStream_t s) {
                                              h->gamma_diag, h->partial, h->st, h->hist, s)) != cudaSuccess)
         return e;
     if ((e = enqueue_vcycle<double>(h, h->cr, h->cz, done, s)) != cudaSuccess) return e;
+    if (h->net) {
+        // the learned stage makes the preconditioner vary: Polak-Ribiere beta from A p (cq)
+        if ((e = enqueue_learned(h, h->cr, h->cz, nullptr, s)) != cudaSuccess) return e;
+        if ((e = imgm::launch_pcg_rz<double>(N, h->cr, h->cz, nullptr, nullptr, h->partial, h->st, s, h->cq)) !=
+            cudaSuccess)
+            return e;
+        return imgm::launch_pcg_xpay<double>(N, h->cz, nullptr, h->cp, nullptr, h->st, s);
+    }
     // FP64 V-cycle: standard beta (czp null); FP32 levels below an FP64 finest one: flexible
     if ((e = imgm::launch_pcg_rz<double>(N, h->cr, h->cz, nullptr, h->czp, h->partial, h->st, s)) != cudaSuccess)
         return e;
@@ -1079,21 +1125,26 @@ int imgm_coarse_solve(imgm_handle* h, const double* dev_r, double* dev_x, void* 
     return IMGM_OK;
 }
 
+// z = B r, one V-cycle (FP64, or FP32 on Jacobi-scaled data for precision 1)
+cudaError_t enqueue_precondition(imgm_handle* h, const double* r, double* z, cudaStream_t s) {
+    LevelDev& F = h->lv[h->L - 1];
+    cudaError_t e;
+    if (h->precision == 1) {
+        if ((e = imgm::launch_vcycle_in<float>(F.d.N, r, F.fd.s, F.fd.dinv, h->gamma_diag, h->rf, h->zf, nullptr, s)) !=
+            cudaSuccess)
+            return e;
+        if ((e = enqueue_vcycle<float>(h, h->rf, h->zf, nullptr, s)) != cudaSuccess) return e;
+        return imgm::launch_vcycle_out<float>(F.d.N, h->zf, F.fd.s, z, s);
+    }
+    if ((e = imgm::launch_scale_diag<double>(F.d, r, z, h->gamma_diag, nullptr, s)) != cudaSuccess) return e;
+    return enqueue_vcycle<double>(h, r, z, nullptr, s);
+}
+
 int imgm_apply_preconditioner(imgm_handle* h, const double* dev_r, double* dev_z, void* stream) {
     int c = check_level(h, h ? h->L : 0, 1);
     if (c) return c;
     if (!dev_r || !dev_z || dev_r == dev_z) return fail(h, IMGM_ERR_INVALID, "bad vector pointers");
-    cudaStream_t s = (cudaStream_t)stream;
-    LevelDev& F = h->lv[h->L - 1];
-    if (h->precision == 1) {
-        CK(imgm::launch_vcycle_in<float>(F.d.N, dev_r, F.fd.s, F.fd.dinv, h->gamma_diag, h->rf, h->zf, nullptr, s),
-           "vcycle input");
-        CK(enqueue_vcycle<float>(h, h->rf, h->zf, nullptr, s), "vcycle");
-        CK(imgm::launch_vcycle_out<float>(F.d.N, h->zf, F.fd.s, dev_z, s), "vcycle output");
-        return IMGM_OK;
-    }
-    CK(imgm::launch_scale_diag<double>(F.d, dev_r, dev_z, h->gamma_diag, nullptr, s), "vcycle diag");
-    CK(enqueue_vcycle<double>(h, dev_r, dev_z, nullptr, s), "vcycle");
+    CK(enqueue_precondition(h, dev_r, dev_z, (cudaStream_t)stream), "vcycle");
     return IMGM_OK;
 }
 
@@ -1546,4 +1597,170 @@ void imgm_batch_destroy(imgm_batch* b) {
     if (!b) return;
     cudaDeviceSynchronize();
     delete b;
+}
+
+// ---- learned correction stage --------------------------------------------------------
+
+namespace {
+
+int net_fail(int code, const std::string& msg) { return fail(nullptr, code, msg); }
+
+#define NCK(call, where)                                                                      \
+    do {                                                                                      \
+        cudaError_t _e = (call);                                                              \
+        if (_e != cudaSuccess) return net_fail(IMGM_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(_e)); \
+    } while (0)
+
+bool net_dims_ok(int nx, int ny, int nz) {
+    return nx >= 1 && ny >= 1 && nz >= 1 && (int64_t)nx * ny * nz <= (int64_t(1) << 31);
+}
+
+// the stage's vectors, mask and activations on h's finest grid (allocated once)
+int ensure_learned_vectors(imgm_handle* h) {
+    if (h->l_r1) return IMGM_OK;
+    LevelDev& F = h->lv[h->L - 1];
+    const int64_t N = F.d.N;
+    CK(h->alloc(&h->l_r1, N), "alloc");
+    CK(h->alloc(&h->l_c, N), "alloc");
+    CK(h->alloc(&h->l_q, N), "alloc");
+    CK(h->alloc(&h->l_mask, N), "alloc");
+    const std::vector<uint8_t>& a = h->H.lv[h->L - 1].active;
+    CK(cudaMemcpy(h->l_mask, a.data(), (size_t)N, cudaMemcpyHostToDevice), "mask upload");
+    CK(cudaMemset(h->l_r1, 0, N * sizeof(double)), "memset");
+    CK(cudaMemset(h->l_c, 0, N * sizeof(double)), "memset");
+    CK(cudaMemset(h->l_q, 0, N * sizeof(double)), "memset");
+    CK(h->lws.ensure(F.d.m, F.d.m, F.d.m, false), "activations");
+    return IMGM_OK;
+}
+
+}  // namespace
+
+int imgm_net_create(const float* host_weights, imgm_net** out) {
+    if (!out) return net_fail(IMGM_ERR_INVALID, "null output network");
+    *out = nullptr;
+    if (!host_weights) return net_fail(IMGM_ERR_INVALID, "null weights");
+    std::unique_ptr<imgm_net> n(new (std::nothrow) imgm_net());
+    if (!n) return net_fail(IMGM_ERR_INVALID, "out of host memory");
+    const size_t nw = imgm::NET_NW;
+    NCK(cudaMalloc(&n->w, nw * sizeof(float)), "alloc");
+    NCK(cudaMalloc(&n->g, nw * sizeof(float)), "alloc");
+    NCK(cudaMalloc(&n->m, nw * sizeof(float)), "alloc");
+    NCK(cudaMalloc(&n->v, nw * sizeof(float)), "alloc");
+    NCK(cudaMalloc(&n->wb, nw * sizeof(uint16_t)), "alloc");
+    NCK(cudaMalloc(&n->wbt, nw * sizeof(uint16_t)), "alloc");
+    NCK(cudaMemcpy(n->w, host_weights, nw * sizeof(float), cudaMemcpyHostToDevice), "weights upload");
+    NCK(cudaMemset(n->g, 0, nw * sizeof(float)), "memset");
+    NCK(cudaMemset(n->m, 0, nw * sizeof(float)), "memset");
+    NCK(cudaMemset(n->v, 0, nw * sizeof(float)), "memset");
+    NCK(imgm::net_convert(n->w, n->wb, n->wbt, nullptr), "convert");
+    NCK(cudaDeviceSynchronize(), "sync");
+    *out = n.release();
+    return IMGM_OK;
+}
+
+void imgm_net_destroy(imgm_net* net) {
+    if (!net) return;
+    cudaDeviceSynchronize();
+    delete net;
+}
+
+int imgm_net_get_weights(const imgm_net* net, float* host_weights) {
+    if (!net || !host_weights) return net_fail(IMGM_ERR_INVALID, "null pointer");
+    NCK(cudaDeviceSynchronize(), "sync");
+    NCK(cudaMemcpy(host_weights, net->w, imgm::NET_NW * sizeof(float), cudaMemcpyDeviceToHost), "weights");
+    return IMGM_OK;
+}
+
+int imgm_net_get_grads(const imgm_net* net, float* host_grads) {
+    if (!net || !host_grads) return net_fail(IMGM_ERR_INVALID, "null pointer");
+    NCK(cudaDeviceSynchronize(), "sync");
+    NCK(cudaMemcpy(host_grads, net->g, imgm::NET_NW * sizeof(float), cudaMemcpyDeviceToHost), "gradients");
+    return IMGM_OK;
+}
+
+int imgm_net_forward(imgm_net* net, int nx, int ny, int nz, const double* dev_in, const uint8_t* dev_mask,
+                     double* dev_out, void* stream) {
+    if (!net || !dev_in || !dev_out || dev_in == dev_out) return net_fail(IMGM_ERR_INVALID, "bad pointers");
+    if (!net_dims_ok(nx, ny, nz)) return net_fail(IMGM_ERR_INVALID, "bad grid size");
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((int64_t)nx * ny * nz > net->ws.cap) NCK(cudaStreamSynchronize(s), "sync");
+    NCK(net->ws.ensure(nx, ny, nz, net->ws.train), "activations");
+    NCK(imgm::net_forward(net->wb, net->ws, dev_in, dev_mask, dev_out, nullptr, s), "forward");
+    return IMGM_OK;
+}
+
+int imgm_net_zero_grad(imgm_net* net, void* stream) {
+    if (!net) return net_fail(IMGM_ERR_INVALID, "null network");
+    NCK(cudaMemsetAsync(net->g, 0, imgm::NET_NW * sizeof(float), (cudaStream_t)stream), "memset");
+    return IMGM_OK;
+}
+
+int imgm_net_accumulate(imgm_net* net, int nx, int ny, int nz, const double* dev_in, const double* dev_target,
+                        const uint8_t* dev_mask, double scale, double* dev_loss, void* stream) {
+    if (!net || !dev_in || !dev_target || !dev_loss) return net_fail(IMGM_ERR_INVALID, "null pointer");
+    if (!net_dims_ok(nx, ny, nz)) return net_fail(IMGM_ERR_INVALID, "bad grid size");
+    if (!(scale >= 0.0) || !std::isfinite(scale)) return net_fail(IMGM_ERR_INVALID, "bad loss scale");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t nvox = (int64_t)nx * ny * nz;
+    if (nvox > net->ws.cap || !net->ws.train) NCK(cudaStreamSynchronize(s), "sync");
+    NCK(net->ws.ensure(nx, ny, nz, true), "activations");
+    NCK(imgm::net_forward(net->wb, net->ws, dev_in, dev_mask, nullptr, net->ws.o, s), "forward");
+    NCK(imgm::net_backward(net->wbt, net->ws, dev_target, dev_mask, scale, net->g, dev_loss, s), "backward");
+    return IMGM_OK;
+}
+
+int imgm_net_adam_step(imgm_net* net, float lr, float beta1, float beta2, float eps, void* stream) {
+    if (!net) return net_fail(IMGM_ERR_INVALID, "null network");
+    if (!(lr >= 0.f) || !(beta1 >= 0.f && beta1 < 1.f) || !(beta2 >= 0.f && beta2 < 1.f) || !(eps > 0.f))
+        return net_fail(IMGM_ERR_INVALID, "bad Adam parameters");
+    net->t += 1;
+    const float c1 = (float)(1.0 / (1.0 - std::pow((double)beta1, (double)net->t)));
+    const float c2 = (float)(1.0 / (1.0 - std::pow((double)beta2, (double)net->t)));
+    NCK(imgm::net_adam(net->w, net->g, net->m, net->v, net->wb, net->wbt, lr, beta1, beta2, eps, c1, c2,
+                       (cudaStream_t)stream),
+        "adam");
+    return IMGM_OK;
+}
+
+int imgm_set_net(imgm_handle* h, imgm_net* net) {
+    int c = check_level(h, h ? h->L : 0, 1);
+    if (c) return c;
+    if (net && h->dim != 3) return fail(h, IMGM_ERR_UNSUPPORTED, "the learned stage is three-dimensional");
+    if (net && h->precision == 1)
+        return fail(h, IMGM_ERR_UNSUPPORTED, "the learned stage follows an FP64 V-cycle output (precision 0 or 2)");
+    if (net && (c = ensure_learned_vectors(h)) != IMGM_OK) return c;
+    CK(cudaDeviceSynchronize(), "sync");
+    if (h->exec) cudaGraphExecDestroy(h->exec);
+    if (h->graph) cudaGraphDestroy(h->graph);
+    h->exec = nullptr;
+    h->graph = nullptr;
+    h->graph_failed = false;
+    h->net = net;
+    return IMGM_OK;
+}
+
+int imgm_learned_stage(imgm_handle* h, const double* dev_r, double* dev_z, double* dev_omega, void* stream) {
+    int c = check_level(h, h ? h->L : 0, 1);
+    if (c) return c;
+    if (!h->net) return fail(h, IMGM_ERR_INVALID, "no network attached");
+    if (!dev_r || !dev_z || dev_r == dev_z) return fail(h, IMGM_ERR_INVALID, "bad vector pointers");
+    CK(enqueue_learned(h, dev_r, dev_z, dev_omega, (cudaStream_t)stream), "learned stage");
+    return IMGM_OK;
+}
+
+int imgm_learned_pair(imgm_handle* h, const double* dev_e0, double* dev_r1, double* dev_e1, void* stream) {
+    int c = check_level(h, h ? h->L : 0, 1);
+    if (c) return c;
+    if (!dev_e0 || !dev_r1 || !dev_e1 || dev_e0 == dev_r1 || dev_e0 == dev_e1 || dev_r1 == dev_e1)
+        return fail(h, IMGM_ERR_INVALID, "bad vector pointers");
+    if ((c = ensure_learned_vectors(h)) != IMGM_OK) return c;
+    cudaStream_t s = (cudaStream_t)stream;
+    LevelDev& F = h->lv[h->L - 1];
+    const int64_t N = F.d.N;
+    CK(imgm::launch_apply<double>(F.d, imgm::APPLY, dev_e0, nullptr, h->l_r1, nullptr, 0.0, nullptr, s), "A e0");
+    CK(enqueue_precondition(h, h->l_r1, h->l_c, s), "vcycle");
+    CK(imgm::pair_error(N, dev_e0, h->l_c, dev_e1, s), "e1");
+    CK(imgm::launch_apply<double>(F.d, imgm::APPLY, dev_e1, nullptr, dev_r1, nullptr, 0.0, nullptr, s), "A e1");
+    CK(imgm::pair_normalise(N, dev_r1, dev_e1, (double)F.info.n_active, h->lws.partial, s), "normalise");
+    return IMGM_OK;
 }

@@ -1163,7 +1163,7 @@ __global__ void __launch_bounds__(TPB) k_pcg_update(int64_t N, const TZ* __restr
 template <typename TZ>
 __global__ void __launch_bounds__(TPB) k_pcg_rz(int64_t N, const double* __restrict__ r, const TZ* __restrict__ z,
                                                 const TZ* __restrict__ zs, const TZ* __restrict__ zprev,
-                                                double* partial, PcgState* st) {
+                                                double* partial, PcgState* st, const double* __restrict__ qprev) {
     pdl_begin();
     if (st->done) return;
     double acc = 0.0, accp = 0.0;
@@ -1171,10 +1171,11 @@ __global__ void __launch_bounds__(TPB) k_pcg_rz(int64_t N, const double* __restr
     for (int64_t i = (int64_t)blockIdx.x * TPB + threadIdx.x; i < N; i += stride) {
         acc = fma(r[i], zval(z, zs, i), acc);
         if (zprev) accp = fma(r[i], zval(zprev, zs, i), accp);
+        else if (qprev) accp = fma(zval(z, zs, i), qprev[i], accp);
     }
     double rz, rzp;
     if (finish_reduction2(acc, accp, partial, &st->ticket[2], &rz, &rzp) && threadIdx.x == 0) {
-        const double num = zprev ? rz - rzp : rz;
+        const double num = zprev ? rz - rzp : (qprev ? -st->alpha * rzp : rz);
         st->beta = num / st->rz;
         st->rz = rz;
         if (!isfinite(rz)) {
@@ -1395,6 +1396,7 @@ cudaError_t launch_tile2d(const DevLevelT<T>& L, int mode, const T* x, const T* 
 
 void set_programmatic_launch(bool on) { t_pdl = on; }
 int64_t launch_count() { return t_launches; }
+void add_launches(int64_t k) { t_launches += k; }
 
 int reduction_blocks() {
     if (g_red_blocks == 0) g_red_blocks = num_sms() * 4;
@@ -1624,8 +1626,8 @@ cudaError_t launch_pcg_update(const DevLevel& L, const TZ* dinv_z, double* x, do
 
 template <typename TZ>
 cudaError_t launch_pcg_rz(int64_t N, const double* r, const TZ* z, const TZ* zs, const TZ* zprev, double* partial,
-                          PcgState* st, cudaStream_t s) {
-    launch_pdl(k_pcg_rz<TZ>, reduction_blocks(), TPB, 0, s, N, r, z, zs, zprev, partial, st);
+                          PcgState* st, cudaStream_t s, const double* qprev) {
+    launch_pdl(k_pcg_rz<TZ>, reduction_blocks(), TPB, 0, s, N, r, z, zs, zprev, partial, st, qprev);
     return cudaGetLastError();
 }
 
@@ -1677,7 +1679,7 @@ cudaError_t launch_set_continue(PcgState* st, unsigned long long handle, cudaStr
                                               const double*, T*, T*, const T*, double, double*, PcgState*,          \
                                               double*, cudaStream_t);                                              \
     template cudaError_t launch_pcg_rz<T>(int64_t, const double*, const T*, const T*, const T*, double*, PcgState*, \
-                                          cudaStream_t);                                                           \
+                                          cudaStream_t, const double*);                                            \
     template cudaError_t launch_pcg_xpay<T>(int64_t, const T*, const T*, double*, T*, PcgState*, cudaStream_t);     \
     template cudaError_t launch_pcg_init_dir<T>(int64_t, const double*, const T*, const T*, double*, T*, double*,   \
                                                 PcgState*, cudaStream_t);                                          \

@@ -116,11 +116,13 @@ template <typename TZ>
 cudaError_t launch_pcg_update(const DevLevel& L, const TZ* dinv_z, double* x, double* r, const double* p,
                               const double* q, TZ* xv, TZ* r_lo, const TZ* rs, double gamma, double* partial,
                               PcgState* st, double* hist, cudaStream_t s);
-// rz_new = r^T z (and r^T z_prev when zprev != nullptr: flexible CG); beta; rz = rz_new.
+// rz_new = r^T z; beta = rz_new / rz, or (r^T (z - z_prev)) / rz when zprev != nullptr, or
+// -alpha (z^T q_prev) / rz when qprev (= A p of the step just taken) != nullptr: the
+// Polak-Ribiere beta z^T (r - r_prev) / rz of flexible CG; rz = rz_new.
 // z = zs .* z^ when zs != nullptr (scaled V-cycle), z otherwise.
 template <typename TZ>
 cudaError_t launch_pcg_rz(int64_t N, const double* r, const TZ* z, const TZ* zs, const TZ* zprev, double* partial,
-                          PcgState* st, cudaStream_t s);
+                          PcgState* st, cudaStream_t s, const double* qprev = nullptr);
 // p = z + beta p (and zprev = z^ when zprev != nullptr)
 template <typename TZ>
 cudaError_t launch_pcg_xpay(int64_t N, const TZ* z, const TZ* zs, double* p, TZ* zprev, PcgState* st,
@@ -187,5 +189,7 @@ int reduction_blocks();   // fixed number of blocks of every reducing kernel
 void set_programmatic_launch(bool on);
 // kernels launched (or captured) so far by this host thread
 int64_t launch_count();
+// counts k kernels launched by this host thread outside this file's launch helper
+void add_launches(int64_t k);
 
 }  // namespace imgm

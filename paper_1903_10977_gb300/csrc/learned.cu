@@ -1,0 +1,458 @@
+// Kernels of the learned correction stage (declarations and conventions in learned.cuh).
+//
+// Convolutions: one thread per output voxel, all output channels in registers, the
+// layer's weights converted to FP32 in shared memory (read as warp-wide broadcasts), the
+// input channels of a neighbour read as one or two 16-byte loads (bf16, channels
+// innermost).  The input gradient of a layer is the forward convolution of the output
+// gradient with the transposed, tap-reversed weights, gated by the ReLU of the layer's
+// input.  Weight gradients: each thread owns one (out, in) channel pair and a slice of
+// the voxels, keeps the 27 tap sums in registers, the block adds its slices in shared
+// memory and issues one atomic add per weight.
+#include <cuda_bf16.h>
+
+#include <cmath>
+
+#include "kernels.cuh"
+#include "learned.cuh"
+
+namespace imgm {
+namespace {
+
+constexpr int CTPB = 128;     // convolution threads per block
+constexpr int WTPB = 256;     // weight-gradient threads per block
+constexpr int RTPB = 256;     // reduction threads per block (= NET_PARTIALS)
+static_assert(RTPB == NET_PARTIALS, "one partial per reduction block");
+
+enum ConvEpilogue { EPI_RELU = 0, EPI_GATE = 1, EPI_OUT = 2 };
+
+__device__ __forceinline__ float bf(uint16_t u) { return __uint_as_float((uint32_t)u << 16); }
+__device__ __forceinline__ uint32_t bf_bits(float f) { return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(f)); }
+
+// the CI channels of voxel u as floats
+template <int CI, typename TIN>
+__device__ __forceinline__ void load_channels(const TIN* __restrict__ x, int64_t u, float* out) {
+    if constexpr (CI == 1) {
+        if constexpr (sizeof(TIN) == 2) out[0] = bf(x[u]);
+        else out[0] = x[u];
+    } else if constexpr (sizeof(TIN) == 2) {
+        static_assert(CI % 8 == 0, "bf16 channels come in 16-byte groups");
+        const uint4* p = reinterpret_cast<const uint4*>(x + u * CI);
+#pragma unroll
+        for (int q = 0; q < CI / 8; ++q) {
+            const uint4 a = p[q];
+            const uint32_t w[4] = {a.x, a.y, a.z, a.w};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                out[8 * q + 2 * k] = __uint_as_float(w[k] << 16);
+                out[8 * q + 2 * k + 1] = __uint_as_float(w[k] & 0xffff0000u);
+            }
+        }
+    } else {
+        static_assert(CI % 4 == 0, "float channels come in 16-byte groups");
+        const float4* p = reinterpret_cast<const float4*>(x + u * CI);
+#pragma unroll
+        for (int q = 0; q < CI / 4; ++q) {
+            const float4 a = p[q];
+            out[4 * q] = a.x;
+            out[4 * q + 1] = a.y;
+            out[4 * q + 2] = a.z;
+            out[4 * q + 3] = a.w;
+        }
+    }
+}
+
+// y[v][o] = sum_tap sum_i W[tap][o][i] x[v + off_tap][i], zero outside the grid, then
+// EPI_RELU: yb = bf16(max(y, 0)); EPI_GATE: yf = y where gate > 0, else 0;
+// EPI_OUT (one channel): yd = y (FP64) and/or yf = y on the mask, 0 elsewhere.
+template <int CI, int CO, typename TIN, int EPI>
+__global__ void __launch_bounds__(CTPB) k_conv(const TIN* __restrict__ x, const uint16_t* __restrict__ w,
+                                               const uint16_t* __restrict__ gate, const uint8_t* __restrict__ mask,
+                                               uint16_t* __restrict__ yb, float* __restrict__ yf,
+                                               double* __restrict__ yd, int nx, int ny, int nz) {
+    __shared__ __align__(16) float ws[27 * CO * CI];
+    for (int i = threadIdx.x; i < 27 * CO * CI; i += blockDim.x) ws[i] = bf(w[i]);
+    __syncthreads();
+    const int64_t nvox = (int64_t)nx * ny * nz;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < nvox; v += (int64_t)gridDim.x * blockDim.x) {
+        const int ix = (int)(v % nx);
+        const int64_t q = v / nx;
+        const int iy = (int)(q % ny);
+        const int iz = (int)(q / ny);
+        float acc[CO];
+#pragma unroll
+        for (int o = 0; o < CO; ++o) acc[o] = 0.f;
+#pragma unroll 1
+        for (int dz = -1; dz <= 1; ++dz) {
+            const int jz = iz + dz;
+            if (jz < 0 || jz >= nz) continue;
+#pragma unroll 1
+            for (int dy = -1; dy <= 1; ++dy) {
+                const int jy = iy + dy;
+                if (jy < 0 || jy >= ny) continue;
+                const int64_t row = (int64_t)nx * (jy + (int64_t)ny * jz);
+                const float* wrow = ws + (9 * (dz + 1) + 3 * (dy + 1)) * CO * CI;
+#pragma unroll
+                for (int dx = -1; dx <= 1; ++dx) {
+                    const int jx = ix + dx;
+                    if (jx < 0 || jx >= nx) continue;
+                    float xin[CI];
+                    load_channels<CI, TIN>(x, row + jx, xin);
+                    const float* wt = wrow + (dx + 1) * CO * CI;
+#pragma unroll
+                    for (int o = 0; o < CO; ++o)
+#pragma unroll
+                        for (int i = 0; i < CI; ++i) acc[o] = fmaf(wt[o * CI + i], xin[i], acc[o]);
+                }
+            }
+        }
+        if constexpr (EPI == EPI_RELU) {
+            static_assert(CO % 8 == 0, "bf16 output in 16-byte groups");
+            uint4* p = reinterpret_cast<uint4*>(yb + v * CO);
+#pragma unroll
+            for (int g = 0; g < CO / 8; ++g) {
+                uint32_t wv[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    wv[k] = bf_bits(fmaxf(acc[8 * g + 2 * k], 0.f)) | (bf_bits(fmaxf(acc[8 * g + 2 * k + 1], 0.f)) << 16);
+                p[g] = make_uint4(wv[0], wv[1], wv[2], wv[3]);
+            }
+        } else if constexpr (EPI == EPI_GATE) {
+            static_assert(CO % 4 == 0, "float output in 16-byte groups");
+            float gv[CO];
+            load_channels<CO, uint16_t>(gate, v, gv);
+            float4* p = reinterpret_cast<float4*>(yf + v * CO);
+#pragma unroll
+            for (int g = 0; g < CO / 4; ++g)
+                p[g] = make_float4(gv[4 * g] > 0.f ? acc[4 * g] : 0.f, gv[4 * g + 1] > 0.f ? acc[4 * g + 1] : 0.f,
+                                   gv[4 * g + 2] > 0.f ? acc[4 * g + 2] : 0.f, gv[4 * g + 3] > 0.f ? acc[4 * g + 3] : 0.f);
+        } else {
+            static_assert(CO == 1, "one output channel");
+            const bool on = !mask || mask[v];
+            if (yd) yd[v] = on ? (double)acc[0] : 0.0;
+            if (yf) yf[v] = on ? acc[0] : 0.f;
+        }
+    }
+}
+
+// gw[tap][o][i] += sum_v dy[v][o] x[v + off_tap][i]
+template <int CI, int CO>
+__global__ void __launch_bounds__(WTPB) k_wgrad(const float* __restrict__ dy, const uint16_t* __restrict__ x,
+                                                float* __restrict__ gw, int nx, int ny, int nz) {
+    constexpr int P = CI * CO;
+    constexpr int S = WTPB / P;
+    static_assert(P * S == WTPB, "channel pairs must divide the block");
+    __shared__ float red[27 * WTPB];
+    const int pair = threadIdx.x % P, slice = threadIdx.x / P;
+    const int co = pair / CI, ci = pair % CI;
+    const int64_t nvox = (int64_t)nx * ny * nz;
+    float acc[27];
+#pragma unroll
+    for (int t = 0; t < 27; ++t) acc[t] = 0.f;
+    for (int64_t v = (int64_t)blockIdx.x * S + slice; v < nvox; v += (int64_t)gridDim.x * S) {
+        const float g = dy[v * CO + co];
+        if (g == 0.f) continue;
+        const int ix = (int)(v % nx);
+        const int64_t q = v / nx;
+        const int iy = (int)(q % ny);
+        const int iz = (int)(q / ny);
+#pragma unroll
+        for (int dz = -1; dz <= 1; ++dz) {
+#pragma unroll
+            for (int dy_ = -1; dy_ <= 1; ++dy_) {
+#pragma unroll
+                for (int dx = -1; dx <= 1; ++dx) {
+                    const int jx = ix + dx, jy = iy + dy_, jz = iz + dz;
+                    if (jx < 0 || jx >= nx || jy < 0 || jy >= ny || jz < 0 || jz >= nz) continue;
+                    const int64_t u = jx + (int64_t)nx * (jy + (int64_t)ny * jz);
+                    const int t = 9 * (dz + 1) + 3 * (dy_ + 1) + (dx + 1);
+                    acc[t] = fmaf(g, bf(x[u * CI + ci]), acc[t]);
+                }
+            }
+        }
+    }
+    if constexpr (S > 1) {
+#pragma unroll
+        for (int t = 0; t < 27; ++t) red[t * WTPB + threadIdx.x] = acc[t];
+        __syncthreads();
+        if (slice == 0) {
+#pragma unroll
+            for (int t = 0; t < 27; ++t) {
+                float s = 0.f;
+                for (int k = 0; k < S; ++k) s += red[t * WTPB + k * P + pair];
+                acc[t] = s;
+            }
+        }
+    }
+    if (slice == 0) {
+#pragma unroll
+        for (int t = 0; t < 27; ++t)
+            if (acc[t] != 0.f) atomicAdd(&gw[(t * CO + co) * CI + ci], acc[t]);
+    }
+}
+
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s += sh[k];
+    __syncthreads();
+    return s;   // valid in thread 0
+}
+
+__global__ void __launch_bounds__(RTPB) k_pack(int64_t n, const double* __restrict__ in, const uint8_t* __restrict__ mask,
+                                               uint16_t* __restrict__ a0) {
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+        a0[v] = (!mask || mask[v]) ? (uint16_t)bf_bits((float)in[v]) : (uint16_t)0;
+}
+
+__global__ void __launch_bounds__(RTPB) k_loss(int64_t n, const float* __restrict__ o, const double* __restrict__ t,
+                                               const uint8_t* __restrict__ mask, double scale, float* __restrict__ d3,
+                                               double* loss) {
+    __shared__ double sh[RTPB / 32];
+    double acc = 0.0;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        const double diff = (!mask || mask[v]) ? ((double)o[v] - t[v]) : 0.0;
+        d3[v] = (float)(2.0 * diff * scale);
+        acc = fma(diff, diff, acc);
+    }
+    const double s = block_sum(acc, sh);
+    if (threadIdx.x == 0 && s != 0.0) atomicAdd(loss, s * scale);
+}
+
+// weight k of the flat vector: its layer's (tap, out, in) and its places in wb and wbt
+__device__ __forceinline__ void net_places(int k, int& fwd, int& bwd) {
+    int off, CI, CO;
+    if (k < NET_OFF2) {
+        off = 0, CI = 1, CO = NET_C;
+    } else if (k < NET_OFF3) {
+        off = NET_OFF2, CI = NET_C, CO = NET_C;
+    } else {
+        off = NET_OFF3, CI = NET_C, CO = 1;
+    }
+    const int r = k - off;
+    const int tap = r / (CO * CI), rem = r % (CO * CI);
+    const int co = rem / CI, ci = rem % CI;
+    fwd = k;
+    bwd = off + ((26 - tap) * CI + ci) * CO + co;
+}
+
+__global__ void k_adam(float* __restrict__ w, const float* __restrict__ g, float* __restrict__ m, float* __restrict__ v,
+                       uint16_t* __restrict__ wb, uint16_t* __restrict__ wbt, float lr, float b1, float b2, float eps,
+                       float c1, float c2, int update) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= NET_NW) return;
+    float wk = w[k];
+    if (update) {
+        const float gk = g[k];
+        const float mk = b1 * m[k] + (1.f - b1) * gk;
+        const float vk = b2 * v[k] + (1.f - b2) * gk * gk;
+        m[k] = mk;
+        v[k] = vk;
+        wk -= lr * (mk * c1) / (sqrtf(vk * c2) + eps);
+        w[k] = wk;
+    }
+    int f, b;
+    net_places(k, f, b);
+    const uint16_t q = (uint16_t)bf_bits(wk);
+    wb[f] = q;
+    wbt[b] = q;
+}
+
+// partial[2 blk] = sum a b, partial[2 blk + 1] = sum c d (c null: 0)
+__global__ void __launch_bounds__(RTPB) k_dots(int64_t n, const double* __restrict__ a, const double* __restrict__ b,
+                                               const double* __restrict__ c, const double* __restrict__ d,
+                                               double* partial) {
+    __shared__ double sh[RTPB / 32];
+    double s0 = 0.0, s1 = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        s0 = fma(a[i], b[i], s0);
+        if (c) s1 = fma(c[i], d[i], s1);
+    }
+    const double t0 = block_sum(s0, sh);
+    const double t1 = block_sum(s1, sh);
+    if (threadIdx.x == 0) {
+        partial[2 * blockIdx.x] = t0;
+        partial[2 * blockIdx.x + 1] = t1;
+    }
+}
+
+// both sums of the NET_PARTIALS partials, in a fixed order (every block gets the same)
+__device__ __forceinline__ void sum_partials(const double* partial, double* s0, double* s1) {
+    __shared__ double a[RTPB], b[RTPB];
+    a[threadIdx.x] = partial[2 * threadIdx.x];
+    b[threadIdx.x] = partial[2 * threadIdx.x + 1];
+    __syncthreads();
+    for (int h = RTPB / 2; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h) {
+            a[threadIdx.x] += a[threadIdx.x + h];
+            b[threadIdx.x] += b[threadIdx.x + h];
+        }
+        __syncthreads();
+    }
+    *s0 = a[0];
+    *s1 = b[0];
+}
+
+__global__ void __launch_bounds__(RTPB) k_stage_axpy(int64_t n, double* __restrict__ z, const double* __restrict__ c,
+                                                     const double* __restrict__ partial, double* omega_out) {
+    double num, den;
+    sum_partials(partial, &num, &den);
+    double omega = 0.0;
+    if (den > 0.0) {
+        omega = num / den;
+        if (!isfinite(omega)) omega = 0.0;
+    }
+    if (omega_out && blockIdx.x == 0 && threadIdx.x == 0) omega_out[0] = omega;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        z[i] = fma(omega, c[i], z[i]);
+}
+
+__global__ void __launch_bounds__(RTPB) k_sub(int64_t n, const double* __restrict__ a, const double* __restrict__ b,
+                                              double* __restrict__ out) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = a[i] - b[i];
+}
+
+__global__ void __launch_bounds__(RTPB) k_scale2(int64_t n, double* __restrict__ a, double* __restrict__ b, double count,
+                                                 const double* __restrict__ partial) {
+    double sa, sb;
+    sum_partials(partial, &sa, &sb);
+    const double ka = (sa > 0.0 && count > 0.0) ? 1.0 / sqrt(sa / count) : 1.0;
+    const double kb = (sb > 0.0 && count > 0.0) ? 1.0 / sqrt(sb / count) : 1.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        a[i] *= ka;
+        b[i] *= kb;
+    }
+}
+
+int sm_count() {
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 148;
+    }
+    return sms;
+}
+
+int grid_for(int64_t work, int per_block, int max_per_sm) {
+    const int64_t want = (work + per_block - 1) / per_block;
+    const int64_t cap = (int64_t)max_per_sm * sm_count();
+    return (int)std::max<int64_t>(1, std::min(want, cap));
+}
+
+int elementwise_grid(int64_t n) { return grid_for(n, RTPB, 8); }
+
+}  // namespace
+
+cudaError_t NetWorkspace::ensure(int nx_, int ny_, int nz_, bool train_) {
+    const int64_t nvox = (int64_t)nx_ * ny_ * nz_;
+    if (nvox > cap || (train_ && !train)) {
+        release();
+        const int64_t n = std::max<int64_t>(nvox, 1);
+        cudaError_t e;
+        if ((e = cudaMalloc(&a0, n * sizeof(uint16_t))) != cudaSuccess) return e;
+        if ((e = cudaMalloc(&a1, n * NET_C * sizeof(uint16_t))) != cudaSuccess) return e;
+        if ((e = cudaMalloc(&a2, n * NET_C * sizeof(uint16_t))) != cudaSuccess) return e;
+        if ((e = cudaMalloc(&partial, 2 * NET_PARTIALS * sizeof(double))) != cudaSuccess) return e;
+        if (train_) {
+            if ((e = cudaMalloc(&o, n * sizeof(float))) != cudaSuccess) return e;
+            if ((e = cudaMalloc(&d3, n * sizeof(float))) != cudaSuccess) return e;
+            if ((e = cudaMalloc(&d2, n * NET_C * sizeof(float))) != cudaSuccess) return e;
+            if ((e = cudaMalloc(&d1, n * NET_C * sizeof(float))) != cudaSuccess) return e;
+        }
+        cap = n;
+        train = train_;
+    }
+    nx = nx_, ny = ny_, nz = nz_;
+    return cudaSuccess;
+}
+
+void NetWorkspace::release() {
+    for (void* p : {(void*)a0, (void*)a1, (void*)a2, (void*)o, (void*)d3, (void*)d2, (void*)d1, (void*)partial})
+        if (p) cudaFree(p);
+    a0 = a1 = a2 = nullptr;
+    o = d3 = d2 = d1 = nullptr;
+    partial = nullptr;
+    cap = 0;
+    train = false;
+}
+
+cudaError_t net_convert(const float* w, uint16_t* wb, uint16_t* wbt, cudaStream_t s) {
+    k_adam<<<(NET_NW + 255) / 256, 256, 0, s>>>(const_cast<float*>(w), nullptr, nullptr, nullptr, wb, wbt, 0.f, 0.f,
+                                                0.f, 0.f, 0.f, 0.f, 0);
+    add_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t net_forward(const uint16_t* wb, NetWorkspace& ws, const double* in, const uint8_t* mask, double* out64,
+                        float* out32, cudaStream_t s) {
+    const int64_t nvox = (int64_t)ws.nx * ws.ny * ws.nz;
+    if (nvox == 0) return cudaSuccess;
+    const int gc = grid_for(nvox, CTPB, 16);
+    k_pack<<<elementwise_grid(nvox), RTPB, 0, s>>>(nvox, in, mask, ws.a0);
+    k_conv<1, NET_C, uint16_t, EPI_RELU><<<gc, CTPB, 0, s>>>(ws.a0, wb, nullptr, nullptr, ws.a1, nullptr, nullptr,
+                                                             ws.nx, ws.ny, ws.nz);
+    k_conv<NET_C, NET_C, uint16_t, EPI_RELU><<<gc, CTPB, 0, s>>>(ws.a1, wb + NET_OFF2, nullptr, nullptr, ws.a2, nullptr,
+                                                                 nullptr, ws.nx, ws.ny, ws.nz);
+    k_conv<NET_C, 1, uint16_t, EPI_OUT><<<gc, CTPB, 0, s>>>(ws.a2, wb + NET_OFF3, nullptr, mask, nullptr, out32, out64,
+                                                            ws.nx, ws.ny, ws.nz);
+    add_launches(4);
+    return cudaGetLastError();
+}
+
+cudaError_t net_backward(const uint16_t* wbt, NetWorkspace& ws, const double* target, const uint8_t* mask,
+                         double scale, float* grad, double* loss, cudaStream_t s) {
+    const int64_t nvox = (int64_t)ws.nx * ws.ny * ws.nz;
+    if (nvox == 0) return cudaSuccess;
+    const int gc = grid_for(nvox, CTPB, 16);
+    k_loss<<<elementwise_grid(nvox), RTPB, 0, s>>>(nvox, ws.o, target, mask, scale, ws.d3, loss);
+    // layer 3: dW3 from (d3, a2); d2 = (W3^T d3) where a2 > 0
+    k_wgrad<NET_C, 1><<<grid_for(nvox, (WTPB / NET_C) * 32, 4), WTPB, 0, s>>>(ws.d3, ws.a2, grad + NET_OFF3, ws.nx,
+                                                                              ws.ny, ws.nz);
+    k_conv<1, NET_C, float, EPI_GATE><<<gc, CTPB, 0, s>>>(ws.d3, wbt + NET_OFF3, ws.a2, nullptr, nullptr, ws.d2,
+                                                          nullptr, ws.nx, ws.ny, ws.nz);
+    // layer 2: dW2 from (d2, a1); d1 = (W2^T d2) where a1 > 0
+    k_wgrad<NET_C, NET_C><<<grid_for(nvox, 32, 4), WTPB, 0, s>>>(ws.d2, ws.a1, grad + NET_OFF2, ws.nx, ws.ny, ws.nz);
+    k_conv<NET_C, NET_C, float, EPI_GATE><<<gc, CTPB, 0, s>>>(ws.d2, wbt + NET_OFF2, ws.a1, nullptr, nullptr, ws.d1,
+                                                              nullptr, ws.nx, ws.ny, ws.nz);
+    // layer 1: dW1 from (d1, a0)
+    k_wgrad<1, NET_C><<<grid_for(nvox, (WTPB / NET_C) * 32, 4), WTPB, 0, s>>>(ws.d1, ws.a0, grad, ws.nx, ws.ny,
+                                                                              ws.nz);
+    add_launches(6);
+    return cudaGetLastError();
+}
+
+cudaError_t net_adam(float* w, const float* g, float* m, float* v, uint16_t* wb, uint16_t* wbt, float lr, float beta1,
+                     float beta2, float eps, float c1, float c2, cudaStream_t s) {
+    k_adam<<<(NET_NW + 255) / 256, 256, 0, s>>>(w, g, m, v, wb, wbt, lr, beta1, beta2, eps, c1, c2, 1);
+    add_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t stage_update(int64_t n, const double* r1, const double* c, const double* Ac, double* z, double* partial,
+                         double* omega_out, cudaStream_t s) {
+    k_dots<<<NET_PARTIALS, RTPB, 0, s>>>(n, r1, c, c, Ac, partial);
+    k_stage_axpy<<<elementwise_grid(n), RTPB, 0, s>>>(n, z, c, partial, omega_out);
+    add_launches(2);
+    return cudaGetLastError();
+}
+
+cudaError_t pair_error(int64_t n, const double* e0, const double* z, double* e1, cudaStream_t s) {
+    k_sub<<<elementwise_grid(n), RTPB, 0, s>>>(n, e0, z, e1);
+    add_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t pair_normalise(int64_t n, double* a, double* b, double count, double* partial, cudaStream_t s) {
+    k_dots<<<NET_PARTIALS, RTPB, 0, s>>>(n, a, a, b, b, partial);
+    k_scale2<<<elementwise_grid(n), RTPB, 0, s>>>(n, a, b, count, partial);
+    add_launches(2);
+    return cudaGetLastError();
+}
+
+}  // namespace imgm

@@ -1,0 +1,269 @@
+"""GPU parity of the learned correction stage against the oracle (oracle/learned.py),
+through the C-ABI.
+
+Tolerances follow from the arithmetic.  Both sides round the input (FP64 -> FP32 ->
+bfloat16) and the weights (FP32 -> bfloat16) identically; they differ in the sums (FP32
+on the GPU, exact in the oracle) and therefore, now and then, in which way a stored
+bfloat16 activation rounds.  With S_l = |W_l| * S_{l-1} (S_0 = |input|) the componentwise
+scale of layer l, a stored activation differs by at most 2^-8 S_l per rounding it went
+through (one bfloat16 unit of S_l) plus the FP32 sums' 432 * 2^-24 S_l, and ReLU does not
+enlarge differences, so the output differs by at most 2 * 2^-8 S_3 + 3 * 432 * 2^-24 S_3
+< 3 * 2^-8 S_3 entry by entry.  Gradients and the stage's step omega inherit relative
+differences of that order, compared normwise at 5 %.  FP64 parts (training pairs) are
+held to 1e-9 in the energy norm, like the V-cycle itself.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+lib = pytest.importorskip("paper_1903_10977_gb300")
+from parity_utils import energy_rel, oracle_for, solver_for  # noqa: E402
+from oracle import learned as NL  # noqa: E402
+from synthetic import initial_weights, random_error  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+_LOG = os.environ.get("IMGM_PARITY_LOG")
+SHAPE = (7, 9, 11)                 # (nz, ny, nx): ragged against the 128-thread blocks
+
+
+def record(**kw):
+    if _LOG:
+        with open(_LOG, "a") as f:
+            f.write(json.dumps({"test": os.environ.get("PYTEST_CURRENT_TEST", "").split(" ")[0], **kw}) + "\n")
+
+
+def dev(v, dtype=torch.float64):
+    return torch.as_tensor(np.ascontiguousarray(v), dtype=dtype, device="cuda")
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.detach().cpu().numpy()
+
+
+def grid_case(seed):
+    rng = np.random.default_rng(seed)
+    mask = (rng.random(SHAPE) < 0.8).astype(np.float64)
+    x = rng.standard_normal(SHAPE) * mask
+    y = rng.standard_normal(SHAPE) * mask
+    w = initial_weights(seed) * 2.0
+    return mask, x, y, w.astype(np.float32).astype(np.float64)
+
+
+def scale_chain(w, x, mask):
+    Ws = [np.abs(NL.round_bf16(W)) for W in NL.split_weights(w)]
+    s = np.abs(NL.to_input(x * mask))[None]
+    for W in Ws:
+        s = NL.conv3d(s, W)
+    return s[0] * mask
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_net_forward_matches_oracle(seed):
+    mask, x, _, w = grid_case(seed)
+    net = lib.Net(w)
+    out = host(net.forward(dev(x.ravel()), SHAPE, mask=dev(mask.ravel(), torch.uint8))).reshape(SHAPE)
+    ref, _ = NL.forward(w, x, mask, bf16=True)
+    S3 = scale_chain(w, x, mask)
+    err = np.abs(out - ref)
+    assert np.all(err <= 3 * 2.0 ** -8 * S3 + 1e-300), float((err / (S3 + 1e-300)).max())
+    assert np.linalg.norm(out - ref) <= 1e-2 * np.linalg.norm(ref)
+    assert not np.any(out[mask == 0])
+    record(seed=seed, rel_l2=float(np.linalg.norm(out - ref) / np.linalg.norm(ref)),
+           max_err_over_scale=float((err / (S3 + 1e-300)).max()))
+    # no mask: the whole grid is active
+    out = host(net.forward(dev(x.ravel()), SHAPE)).reshape(SHAPE)
+    ref, _ = NL.forward(w, x, np.ones(SHAPE), bf16=True)
+    assert np.linalg.norm(out - ref) <= 1e-2 * np.linalg.norm(ref)
+    net.close()
+
+
+@pytest.mark.parametrize("seed", [3, 4])
+def test_net_gradient_matches_oracle(seed):
+    mask, x, y, w = grid_case(seed)
+    scale = 1.0 / mask.sum()
+    net = lib.Net(w)
+    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    net.zero_grad()
+    net.accumulate(dev(x.ravel()), dev(y.ravel()), SHAPE, loss, mask=dev(mask.ravel(), torch.uint8), scale=scale)
+    g = net.grads().astype(np.float64)
+    L_ref, g_ref = NL.loss_and_grads(w, x, y, mask, scale, bf16=True)
+    assert abs(float(host(loss)[0]) - L_ref) <= 1e-2 * L_ref
+    rel = []
+    for lo, hi in ((0, 432), (432, 432 + 6912), (432 + 6912, 7776)):
+        d = np.linalg.norm(g[lo:hi] - g_ref[lo:hi]) / np.linalg.norm(g_ref[lo:hi])
+        rel.append(float(d))
+        assert d <= 0.05, (lo, d)
+    # two accumulations add up
+    net.accumulate(dev(x.ravel()), dev(y.ravel()), SHAPE, loss, mask=dev(mask.ravel(), torch.uint8), scale=scale)
+    assert np.allclose(net.grads(), 2 * g, rtol=1e-5, atol=1e-6 * np.abs(g).max())
+    record(seed=seed, grad_rel_l2=rel, loss_gpu=float(host(loss)[0]) / 2, loss_oracle=L_ref)
+    net.close()
+
+
+def test_adam_constant_gradient_closed_form():
+    """With the gradient held fixed, Adam's bias-corrected moments are g and g^2 at every
+    step, so k steps move each weight by k lr g / (|g| + eps)."""
+    mask, x, y, w = grid_case(5)
+    net = lib.Net(w)
+    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    net.zero_grad()
+    net.accumulate(dev(x.ravel()), dev(y.ravel()), SHAPE, loss, mask=dev(mask.ravel(), torch.uint8),
+                   scale=1.0 / mask.sum())
+    g = net.grads().astype(np.float64)
+    w0 = net.weights().astype(np.float64)
+    lr, k = 1e-3, 3
+    for _ in range(k):
+        net.adam_step(lr)
+    w3 = net.weights().astype(np.float64)
+    expect = w0 - k * lr * g / (np.abs(g) + 1e-8)
+    assert np.abs(w3 - expect).max() <= 1e-4 * lr + 4 * np.finfo(np.float32).eps * np.abs(w0).max()
+    net.close()
+
+
+def test_net_argument_errors():
+    w = initial_weights(0)
+    net = lib.Net(w)
+    x = torch.zeros(10, dtype=torch.float64, device="cuda")
+    with pytest.raises(lib.ImgmError):
+        net.forward(x, (1, 1, 0))
+    with pytest.raises(lib.ImgmError):
+        net.adam_step(-1.0)
+    with pytest.raises(ValueError):
+        lib.Net(w[:10])
+    net.close()
+
+
+# ---------------------------------------------------------------- on a solver
+N3 = dict(n=16, levels=3, depth=0)
+
+
+@pytest.fixture(scope="module")
+def problem():
+    pr, lay, d, H = oracle_for("spheres20_128_p2", **N3)
+    S = solver_for(lib, pr, lay, precision=0)
+    yield pr, lay, d, H, S
+    S.close()
+
+
+def oracle_net(w, d):
+    m = d.tb.m
+    mask = np.zeros(m ** 3)
+    mask[d.active] = 1.0
+    mask = mask.reshape(m, m, m)
+
+    def net(r_active):
+        g = d.to_full(r_active).reshape(m, m, m)
+        return NL.forward(w, g, mask, bf16=True)[0].reshape(-1)[d.active]
+    return net
+
+
+def test_training_pair_matches_oracle(problem):
+    pr, lay, d, H, S = problem
+    e0 = random_error(d.n_active, 21)
+    r1, e1 = S.learned_pair(dev(d.to_full(e0)))
+    r_ref, e_ref = NL.training_pair(d.A, H.precondition, e0)
+    e_gpu, r_gpu = host(e1), host(r1)
+    assert energy_rel(e_gpu[d.active] - e_ref, e_ref, d.A) <= 1e-9
+    assert np.linalg.norm(r_gpu[d.active] - r_ref) <= 1e-8 * np.linalg.norm(r_ref)
+    assert not np.any(np.delete(e_gpu, d.active)) and not np.any(np.delete(r_gpu, d.active))
+    assert abs(np.sqrt(np.mean(e_gpu[d.active] ** 2)) - 1.0) <= 1e-12
+    assert abs(np.sqrt(np.mean(r_gpu[d.active] ** 2)) - 1.0) <= 1e-12
+
+
+def test_stage_matches_oracle(problem):
+    pr, lay, d, H, S = problem
+    w = initial_weights(7) * 3.0
+    w = w.astype(np.float32).astype(np.float64)
+    net = lib.Net(w)
+    S.set_net(net)
+    r = random_error(d.n_active, 22)
+    rd = dev(d.to_full(r))
+    z = S.apply_preconditioner(rd)
+    omega = torch.zeros(1, dtype=torch.float64, device="cuda")
+    S.learned_stage(rd, z, omega)
+    z_ref0 = H.precondition(r)
+    z_ref, om_ref = NL.stage(d.A, r, z_ref0, oracle_net(w, d))
+    om = float(host(omega)[0])
+    assert om_ref != 0.0 and abs(om - om_ref) <= 0.05 * abs(om_ref), (om, om_ref)
+    c_norm = energy_rel(z_ref - z_ref0, z_ref0, d.A)          # ||omega c||_A / ||z0||_A
+    err = energy_rel(host(z)[d.active] - z_ref, z_ref0, d.A)
+    assert err <= 1e-9 + 0.1 * c_norm, (err, c_norm)
+    record(omega=om, omega_oracle=om_ref, stage_rel=err, step_rel=c_norm)
+    S.set_net(None)
+    net.close()
+
+
+def a_norm_ratio(S, r1, e1, z):
+    """||e - z||_A / ||e||_A for the error e = A^-1 r1 of the pair (r1 and e1 are scaled
+    separately, so e = e1 ||r1|| / ||A e1||)."""
+    Ae1 = S.apply_operator(e1)
+    e = e1 * (torch.linalg.vector_norm(r1) / torch.linalg.vector_norm(Ae1))
+    Az = S.apply_operator(z)
+    ee = float(e @ r1)
+    left = ee - 2 * float(z @ r1) + float(z @ Az)
+    return float(np.sqrt(max(left, 0.0) / ee))
+
+
+def test_training_gains_and_learned_solve(problem):
+    """Training on the V-cycle's own pairs lowers the loss; on held-out pairs the trained
+    stage removes more of the error left by the V-cycle than the untrained one; the
+    learned PCG converges to the solution of the plain PCG in no more iterations."""
+    pr, lay, d, H, S = problem
+    m = d.tb.m
+    shape = (m, m, m)
+    mask = dev(S.active_mask(), torch.uint8)
+    pairs = [S.learned_pair(dev(d.to_full(random_error(d.n_active, 100 + k)))) for k in range(8)]
+    held = [S.learned_pair(dev(d.to_full(random_error(d.n_active, 200 + k)))) for k in range(4)]
+    w0 = initial_weights(11)
+    net0, net = lib.Net(w0), lib.Net(w0)
+    losses = host(lib.train_net(net, [(r, e, mask) for r, e in pairs], shape, steps=300, lr=1e-3, batch=2))
+    assert np.all(np.isfinite(losses))
+    assert losses[-40:].mean() < 0.95 * losses[:2].mean(), (losses[:2], losses[-40:].mean())
+
+    def held_ratio(n):
+        S.set_net(n)
+        out = []
+        for r1, e1 in held:
+            z = torch.zeros_like(r1)
+            S.learned_stage(r1, z)
+            out.append(a_norm_ratio(S, r1, e1, z))
+        return float(np.mean(out))
+    ratio0, ratio1 = held_ratio(net0), held_ratio(net)
+    assert ratio1 <= 1.0 + 1e-12 and ratio0 <= 1.0 + 1e-12
+    assert ratio1 < ratio0, (ratio0, ratio1)
+
+    b = S.rhs()
+    S.set_net(None)
+    x0, res0, _ = S.pcg_solve(b, rtol=1e-8, maxit=1000)
+    S.set_net(net)
+    x1, res1, _ = S.pcg_solve(b, rtol=1e-8, maxit=1000)
+    assert res1["status"] == lib.IMGM_OK and res1["true_rel_residual"] <= 2e-8
+    xe = host(x0)[d.active]
+    assert energy_rel(host(x1)[d.active] - xe, xe, d.A) <= 1e-6
+    assert res1["iterations"] <= res0["iterations"], (res0["iterations"], res1["iterations"])
+    record(loss_first=float(losses[:2].mean()), loss_last=float(losses[-40:].mean()), held_ratio_untrained=ratio0,
+           held_ratio_trained=ratio1, plain_iterations=res0["iterations"], learned_iterations=res1["iterations"],
+           plain_launches=res0["kernel_launches"], learned_launches=res1["kernel_launches"])
+    S.set_net(None)
+    net.close()
+    net0.close()
+
+
+def test_set_net_rejects_2d_and_fp32_vcycle():
+    from parity_utils import layout_for
+    pr, lay = layout_for("disc1_32_p2")
+    S2 = solver_for(lib, pr, lay)
+    net = lib.Net(initial_weights(0))
+    with pytest.raises(lib.ImgmError):
+        S2.set_net(net)
+    pr3, lay3 = layout_for("spheres20_128_p2", n=16, levels=3)
+    S3 = solver_for(lib, pr3, lay3, precision=1)
+    with pytest.raises(lib.ImgmError):
+        S3.set_net(net)
+    S2.close()
+    S3.close()
+    net.close()
