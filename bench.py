@@ -286,6 +286,7 @@ def run_learned(args, lib, torch, pr, S64, timed_solves, total_units, t64, res64
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     pairs, shape = [], None
+    rms = torch.zeros(LEARN_GEOMS * LEARN_PAIRS, dtype=torch.float64, device="cuda")
     for g in range(LEARN_GEOMS):
         lay_g = config_layout(tr.layout, 1000 + g)
         Sg = lib.Solver(tr.dim, lay_g.centers, lay_g.radii, tr.n, tr.degree, tr.levels, tr.depth, tr.bc,
@@ -296,14 +297,17 @@ def run_learned(args, lib, torch, pr, S64, timed_solves, total_units, t64, res64
         mask = torch.as_tensor(mask_h, device="cuda")
         for k in range(LEARN_PAIRS):
             e0 = torch.as_tensor(random_error(mask_h.size, 10_000 * g + k) * mask_h, device="cuda")
-            r1, e1 = Sg.learned_pair(e0)
+            j = g * LEARN_PAIRS + k
+            r1, e1 = Sg.learned_pair(e0, r_rms=rms[j:j + 1])
             pairs.append((r1, e1, mask))
         torch.cuda.synchronize()
         Sg.close()
     t_pairs = time.perf_counter() - t0
     net = lib.Net(initial_weights(args.seed))
     t1 = time.perf_counter()
-    losses = lib.train_net(net, pairs, shape, steps=LEARN_STEPS, lr=LEARN_LR, batch=LEARN_BATCH).cpu().numpy()
+    sigma = 1.0 / float(rms.mean().item())          # the set's input scale
+    losses = lib.train_net(net, pairs, shape, steps=LEARN_STEPS, lr=LEARN_LR, batch=LEARN_BATCH,
+                           in_scale=sigma).cpu().numpy()
     t_train = time.perf_counter() - t1
     # the network's forward pass on the workload's grid alone (20 launches after warm-up)
     info = S64.level_info(S64.L)
@@ -335,7 +339,8 @@ def run_learned(args, lib, torch, pr, S64, timed_solves, total_units, t64, res64
                        "gpu_launches_per_solve": int(res64[0]["kernel_launches"])},
         "speedup_vs_plain_fp64": t64 / t_l,
         "training": {"geometries": LEARN_GEOMS, "n": LEARN_N, "levels": tr.levels, "pairs": len(pairs),
-                     "steps": LEARN_STEPS, "batch": LEARN_BATCH, "lr": LEARN_LR, "pairs_s": t_pairs,
+                     "steps": LEARN_STEPS, "batch": LEARN_BATCH, "lr": LEARN_LR, "input_scale": sigma,
+                     "pairs_s": t_pairs,
                      "train_s": t_train, "loss_first": float(losses[:4].mean()),
                      "loss_last": float(losses[-20:].mean())},
         "stage": "z += omega N(r - A z) after every FP64 V-cycle, Polak-Ribiere beta",

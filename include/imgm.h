@@ -243,13 +243,14 @@ int imgm_net_forward(imgm_net* net, int nx, int ny, int nz, const double* dev_in
                      double* dev_out, void* stream);
 
 /* Training.  zero_grad clears the gradient accumulator; accumulate adds the gradient of
- * L = scale * sum_v m_v (N(in)_v - target_v)^2 (reverse mode through the stored
- * activations) and adds L to dev_loss[0] (a device double the caller zeroes);
+ * L = scale * sum_v m_v (N(in_scale in)_v - target_v)^2 (reverse mode through the stored
+ * activations; in_scale > 0 multiplies the input before its rounding to bfloat16) and
+ * adds L to dev_loss[0] (a device double the caller zeroes);
  * adam_step applies one Adam step (Kingma and Ba, 2015) with bias correction to the
  * FP32 weights and refreshes their bfloat16 copies. */
 int imgm_net_zero_grad(imgm_net* net, void* stream);
 int imgm_net_accumulate(imgm_net* net, int nx, int ny, int nz, const double* dev_in, const double* dev_target,
-                        const uint8_t* dev_mask, double scale, double* dev_loss, void* stream);
+                        const uint8_t* dev_mask, double in_scale, double scale, double* dev_loss, void* stream);
 int imgm_net_adam_step(imgm_net* net, float lr, float beta1, float beta2, float eps, void* stream);
 
 /* Attaches net to h's solves (NULL detaches): imgm_pcg_solve then runs the stage after
@@ -262,10 +263,14 @@ int imgm_set_net(imgm_handle* h, imgm_net* net);
  * dev_omega (device double, may be NULL) receives omega. */
 int imgm_learned_stage(imgm_handle* h, const double* dev_r, double* dev_z, double* dev_omega, void* stream);
 
-/* A training pair from the V-cycle of h: e1 = e0 - B A e0, r1 = A e1, each divided by its
- * own root mean square over the active functions (dev_e0 active-supported; three distinct
- * device vectors of n_grid doubles). */
-int imgm_learned_pair(imgm_handle* h, const double* dev_e0, double* dev_r1, double* dev_e1, void* stream);
+/* A training pair from the V-cycle of h: e1 = e0 - B A e0, r1 = A e1, both divided by the
+ * root mean square of e1 over the active functions (dev_e0 active-supported; three
+ * distinct device vectors of n_grid doubles).  dev_r_rms (device double, may be NULL)
+ * receives the root mean square of the scaled r1: the mean over a training set gives the
+ * set's input scale (1 / mean), one factor for every pair, since r1 shrinks with the mesh
+ * size while e1 does not. */
+int imgm_learned_pair(imgm_handle* h, const double* dev_e0, double* dev_r1, double* dev_e1, double* dev_r_rms,
+                      void* stream);
 
 /* ---- Setup inspection (host only; no GPU needed) --------------------------------
  * imgm_setup_host builds the same hierarchy as imgm_setup without touching the GPU;

@@ -18,9 +18,10 @@ of the published methods it uses:
   omega = (r1 . c) / (c . A c) that minimises the A-norm of the error left in the
   correction equation A e = r (omega = 0 when c . A c is not positive);
 * training data: the V-cycle's own residual/error pairs, e1 = (I - B A) e0 and
-  r1 = A e1 for random e0, each divided by its own root mean square over the active
-  functions (A scales with the mesh size, so the pair is learned as a map between shapes
-  and the stage's step omega restores the size); the loss is the masked squared error sum_v m_v (N(r1)_v - e1_v)^2 times a
+  r1 = A e1 for random e0, both divided by the root mean square of e1 over the active
+  functions, and every input multiplied by the set's scale 1 / mean(rms(r1)) (A scales
+  with the mesh size; one factor for the whole set keeps the pairs one consistent map, and
+  the stage's step omega makes the factor irrelevant when the network is used); the loss is the masked squared error sum_v m_v (N(r1)_v - e1_v)^2 times a
   caller-given scale (1 / number of active functions);
 * gradients by the chain rule (reverse mode), Adam (Kingma and Ba, 2015, Algorithm 1)
   with bias correction on FP32 master weights;
@@ -96,7 +97,7 @@ def conv3d_weight_grad(dy, x):
     return np.stack([np.einsum("ozyx,izyx->oi", dy, shift(x, off)) for off in OFFSETS])
 
 
-def forward(w, r_grid, mask, bf16: bool = True):
+def forward(w, r_grid, mask, bf16: bool = True, in_scale: float = 1.0):
     """N(r) on a grid (nz, ny, nx) with the active mask (same shape, 0/1).
 
     The network sees the input on the active functions only (zero elsewhere).
@@ -107,7 +108,7 @@ def forward(w, r_grid, mask, bf16: bool = True):
     Ws = split_weights(w)
     rnd = round_bf16 if bf16 else (lambda v: v)
     Ws = [rnd(W) for W in Ws]
-    r_grid = np.asarray(r_grid, dtype=np.float64) * mask
+    r_grid = np.asarray(r_grid, dtype=np.float64) * in_scale * mask
     x = (to_input(r_grid) if bf16 else r_grid)[None]
     a1 = rnd(np.maximum(conv3d(x, Ws[0]), 0.0))
     a2 = rnd(np.maximum(conv3d(a1, Ws[1]), 0.0))
@@ -115,13 +116,13 @@ def forward(w, r_grid, mask, bf16: bool = True):
     return out, (x, a1, a2)
 
 
-def loss_and_grads(w, r_grid, e_grid, mask, scale: float, bf16: bool = True):
-    """Loss scale * sum_v m_v (N(r)_v - e_v)^2 and its gradient with respect to the
-    (FP32 master) weights, by reverse mode through the stored activations."""
+def loss_and_grads(w, r_grid, e_grid, mask, scale: float, bf16: bool = True, in_scale: float = 1.0):
+    """Loss scale * sum_v m_v (N(in_scale r)_v - e_v)^2 and its gradient with respect to
+    the (FP32 master) weights, by reverse mode through the stored activations."""
     Ws = split_weights(w)
     rnd = round_bf16 if bf16 else (lambda v: v)
     Wq = [rnd(W) for W in Ws]
-    out, (x, a1, a2) = forward(w, r_grid, mask, bf16)
+    out, (x, a1, a2) = forward(w, r_grid, mask, bf16, in_scale)
     diff = (out - e_grid) * mask
     loss = scale * float(np.sum(diff * diff))
     d3 = (2.0 * diff * scale)[None]
@@ -151,10 +152,16 @@ class Adam:
 
 def training_pair(A, precondition, e0):
     """One V-cycle's residual/error pair from a random error e0 (active functions):
-    e1 = e0 - B A e0, r1 = A e1, each divided by its own root mean square."""
+    e1 = e0 - B A e0, r1 = A e1, both divided by the root mean square of e1."""
     e1 = e0 - precondition(A @ e0)
     r1 = A @ e1
-    return r1 / np.sqrt(np.mean(r1 * r1)), e1 / np.sqrt(np.mean(e1 * e1))
+    s = np.sqrt(np.mean(e1 * e1))
+    return r1 / s, e1 / s
+
+
+def input_scale(pairs):
+    """The training set's input scale: 1 / mean over its pairs of rms(r1)."""
+    return 1.0 / float(np.mean([np.sqrt(np.mean(r * r)) for r, _ in pairs]))
 
 
 def stage(A, r, z, net):

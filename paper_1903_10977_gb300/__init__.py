@@ -88,11 +88,11 @@ _SIGS = {
     "imgm_net_get_grads": (_I, [_P, _P]),
     "imgm_net_forward": (_I, [_P, _I, _I, _I, _P, _P, _P, _P]),
     "imgm_net_zero_grad": (_I, [_P, _P]),
-    "imgm_net_accumulate": (_I, [_P, _I, _I, _I, _P, _P, _P, _D, _P, _P]),
+    "imgm_net_accumulate": (_I, [_P, _I, _I, _I, _P, _P, _P, _D, _D, _P, _P]),
     "imgm_net_adam_step": (_I, [_P, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, _P]),
     "imgm_set_net": (_I, [_H, _P]),
     "imgm_learned_stage": (_I, [_H, _P, _P, _P, _P]),
-    "imgm_learned_pair": (_I, [_H, _P, _P, _P, _P]),
+    "imgm_learned_pair": (_I, [_H, _P, _P, _P, _P, _P]),
 }
 NET_WEIGHTS = 7776
 for _name, (_res, _args) in _SIGS.items():
@@ -262,12 +262,14 @@ class Solver:
                                             _stream(stream)))
         return z
 
-    def learned_pair(self, e0, r1=None, e1=None, stream=None):
-        """Training pair of the V-cycle: e1 = e0 - B A e0, r1 = A e1, each divided by its own rms."""
+    def learned_pair(self, e0, r1=None, e1=None, r_rms=None, stream=None):
+        """Training pair of the V-cycle: e1 = e0 - B A e0, r1 = A e1, both divided by rms(e1);
+        r_rms (optional one-element float64 CUDA tensor) receives rms(r1) afterwards."""
         import torch
         r1 = torch.empty_like(e0) if r1 is None else r1
         e1 = torch.empty_like(e0) if e1 is None else e1
-        self._check(_lib.imgm_learned_pair(self._h, _ptr(e0), _ptr(r1), _ptr(e1), _stream(stream)))
+        self._check(_lib.imgm_learned_pair(self._h, _ptr(e0), _ptr(r1), _ptr(e1),
+                                           _ptr(r_rms) if r_rms is not None else None, _stream(stream)))
         return r1, e1
 
     def residual_norm2(self, b, x, out=None, stream=None):
@@ -456,22 +458,24 @@ class Net:
     def zero_grad(self, stream=None):
         self._check(_lib.imgm_net_zero_grad(self._n, _stream(stream)))
 
-    def accumulate(self, x, target, shape, loss, mask=None, scale=1.0, stream=None):
-        """Adds the gradient of scale * sum m (N(x) - target)^2; adds the loss to loss[0]."""
+    def accumulate(self, x, target, shape, loss, mask=None, scale=1.0, in_scale=1.0, stream=None):
+        """Adds the gradient of scale * sum m (N(in_scale x) - target)^2; adds the loss to loss[0]."""
         nz, ny, nx = shape
-        self._check(_lib.imgm_net_accumulate(self._n, nx, ny, nz, _ptr(x), _ptr(target), _mask_ptr(mask), scale,
-                                             _ptr(loss), _stream(stream)))
+        self._check(_lib.imgm_net_accumulate(self._n, nx, ny, nz, _ptr(x), _ptr(target), _mask_ptr(mask), in_scale,
+                                             scale, _ptr(loss), _stream(stream)))
 
     def adam_step(self, lr, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
         self._check(_lib.imgm_net_adam_step(self._n, lr, beta1, beta2, eps, _stream(stream)))
 
 
-def train_net(net: Net, pairs, shape, steps: int, lr: float = 1e-3, batch: int = 1, stream=None):
+def train_net(net: Net, pairs, shape, steps: int, lr: float = 1e-3, batch: int = 1, in_scale: float = 1.0,
+              stream=None):
     """Adam on the V-cycle's residual/error pairs [(r1, e1, mask), ...] on grids of one
     shape (nz, ny, nx) (mask: uint8 CUDA vector of the pair's active functions): each step
     accumulates the gradient of `batch` pairs, taken in turn, and applies one update.  The
-    loss of a pair is scaled by 1 / (batch * its number of active functions).  Returns
-    the per-step losses (device tensor)."""
+    loss of a pair is scaled by 1 / (batch * its number of active functions); every input
+    is multiplied by in_scale (the set's 1 / mean rms(r1), see Solver.learned_pair).
+    Returns the per-step losses (device tensor)."""
     import torch
     losses = torch.zeros(steps, dtype=torch.float64, device="cuda")
     scales = [1.0 / (batch * max(int(m.sum().item()), 1)) for _, _, m in pairs]
@@ -480,7 +484,8 @@ def train_net(net: Net, pairs, shape, steps: int, lr: float = 1e-3, batch: int =
         net.zero_grad(stream)
         for _ in range(batch):
             r1, e1, mask = pairs[k % len(pairs)]
-            net.accumulate(r1, e1, shape, losses[it:it + 1], mask=mask, scale=scales[k % len(pairs)], stream=stream)
+            net.accumulate(r1, e1, shape, losses[it:it + 1], mask=mask, scale=scales[k % len(pairs)],
+                           in_scale=in_scale, stream=stream)
             k += 1
         net.adam_step(lr, stream=stream)
     return losses

@@ -401,7 +401,8 @@ cudaError_t enqueue_learned(imgm_handle* h, const double* r, double* z, double* 
     cudaError_t e;
     if ((e = imgm::launch_apply<double>(F.d, imgm::RESID, z, r, h->l_r1, nullptr, h->gamma, nullptr, s)) != cudaSuccess)
         return e;
-    if ((e = imgm::net_forward(h->net->wb, h->lws, h->l_r1, h->l_mask, h->l_c, nullptr, s)) != cudaSuccess) return e;
+    if ((e = imgm::net_forward(h->net->wb, h->lws, h->l_r1, h->l_mask, 1.0, h->l_c, nullptr, s)) != cudaSuccess)
+        return e;
     if ((e = imgm::launch_apply<double>(F.d, imgm::APPLY, h->l_c, nullptr, h->l_q, nullptr, 0.0, nullptr, s)) !=
         cudaSuccess)
         return e;
@@ -1685,7 +1686,7 @@ int imgm_net_forward(imgm_net* net, int nx, int ny, int nz, const double* dev_in
     cudaStream_t s = (cudaStream_t)stream;
     if ((int64_t)nx * ny * nz > net->ws.cap) NCK(cudaStreamSynchronize(s), "sync");
     NCK(net->ws.ensure(nx, ny, nz, net->ws.train), "activations");
-    NCK(imgm::net_forward(net->wb, net->ws, dev_in, dev_mask, dev_out, nullptr, s), "forward");
+    NCK(imgm::net_forward(net->wb, net->ws, dev_in, dev_mask, 1.0, dev_out, nullptr, s), "forward");
     return IMGM_OK;
 }
 
@@ -1696,15 +1697,16 @@ int imgm_net_zero_grad(imgm_net* net, void* stream) {
 }
 
 int imgm_net_accumulate(imgm_net* net, int nx, int ny, int nz, const double* dev_in, const double* dev_target,
-                        const uint8_t* dev_mask, double scale, double* dev_loss, void* stream) {
+                        const uint8_t* dev_mask, double in_scale, double scale, double* dev_loss, void* stream) {
     if (!net || !dev_in || !dev_target || !dev_loss) return net_fail(IMGM_ERR_INVALID, "null pointer");
     if (!net_dims_ok(nx, ny, nz)) return net_fail(IMGM_ERR_INVALID, "bad grid size");
     if (!(scale >= 0.0) || !std::isfinite(scale)) return net_fail(IMGM_ERR_INVALID, "bad loss scale");
+    if (!(in_scale > 0.0) || !std::isfinite(in_scale)) return net_fail(IMGM_ERR_INVALID, "bad input scale");
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t nvox = (int64_t)nx * ny * nz;
     if (nvox > net->ws.cap || !net->ws.train) NCK(cudaStreamSynchronize(s), "sync");
     NCK(net->ws.ensure(nx, ny, nz, true), "activations");
-    NCK(imgm::net_forward(net->wb, net->ws, dev_in, dev_mask, nullptr, net->ws.o, s), "forward");
+    NCK(imgm::net_forward(net->wb, net->ws, dev_in, dev_mask, in_scale, nullptr, net->ws.o, s), "forward");
     NCK(imgm::net_backward(net->wbt, net->ws, dev_target, dev_mask, scale, net->g, dev_loss, s), "backward");
     return IMGM_OK;
 }
@@ -1748,7 +1750,8 @@ int imgm_learned_stage(imgm_handle* h, const double* dev_r, double* dev_z, doubl
     return IMGM_OK;
 }
 
-int imgm_learned_pair(imgm_handle* h, const double* dev_e0, double* dev_r1, double* dev_e1, void* stream) {
+int imgm_learned_pair(imgm_handle* h, const double* dev_e0, double* dev_r1, double* dev_e1, double* dev_r_rms,
+                      void* stream) {
     int c = check_level(h, h ? h->L : 0, 1);
     if (c) return c;
     if (!dev_e0 || !dev_r1 || !dev_e1 || dev_e0 == dev_r1 || dev_e0 == dev_e1 || dev_r1 == dev_e1)
@@ -1761,6 +1764,6 @@ int imgm_learned_pair(imgm_handle* h, const double* dev_e0, double* dev_r1, doub
     CK(enqueue_precondition(h, h->l_r1, h->l_c, s), "vcycle");
     CK(imgm::pair_error(N, dev_e0, h->l_c, dev_e1, s), "e1");
     CK(imgm::launch_apply<double>(F.d, imgm::APPLY, dev_e1, nullptr, dev_r1, nullptr, 0.0, nullptr, s), "A e1");
-    CK(imgm::pair_normalise(N, dev_r1, dev_e1, (double)F.info.n_active, h->lws.partial, s), "normalise");
+    CK(imgm::pair_normalise(N, dev_r1, dev_e1, (double)F.info.n_active, h->lws.partial, dev_r_rms, s), "normalise");
     return IMGM_OK;
 }

@@ -203,9 +203,9 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
 }
 
 __global__ void __launch_bounds__(RTPB) k_pack(int64_t n, const double* __restrict__ in, const uint8_t* __restrict__ mask,
-                                               uint16_t* __restrict__ a0) {
+                                               double in_scale, uint16_t* __restrict__ a0) {
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
-        a0[v] = (!mask || mask[v]) ? (uint16_t)bf_bits((float)in[v]) : (uint16_t)0;
+        a0[v] = (!mask || mask[v]) ? (uint16_t)bf_bits((float)(in[v] * in_scale)) : (uint16_t)0;
 }
 
 __global__ void __launch_bounds__(RTPB) k_loss(int64_t n, const float* __restrict__ o, const double* __restrict__ t,
@@ -316,15 +316,17 @@ __global__ void __launch_bounds__(RTPB) k_sub(int64_t n, const double* __restric
         out[i] = a[i] - b[i];
 }
 
-__global__ void __launch_bounds__(RTPB) k_scale2(int64_t n, double* __restrict__ a, double* __restrict__ b, double count,
-                                                 const double* __restrict__ partial) {
-    double sa, sb;
-    sum_partials(partial, &sa, &sb);
-    const double ka = (sa > 0.0 && count > 0.0) ? 1.0 / sqrt(sa / count) : 1.0;
-    const double kb = (sb > 0.0 && count > 0.0) ? 1.0 / sqrt(sb / count) : 1.0;
+// partials hold (sum r^2, sum e^2): r, e *= k = 1 / rms(e); r_rms_out = rms(r) afterwards
+__global__ void __launch_bounds__(RTPB) k_pair_scale(int64_t n, double* __restrict__ r, double* __restrict__ e,
+                                                     double count, const double* __restrict__ partial,
+                                                     double* r_rms_out) {
+    double sr, se;
+    sum_partials(partial, &sr, &se);
+    const double k = (se > 0.0 && count > 0.0) ? 1.0 / sqrt(se / count) : 1.0;
+    if (r_rms_out && blockIdx.x == 0 && threadIdx.x == 0) r_rms_out[0] = count > 0.0 ? k * sqrt(sr / count) : 0.0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        a[i] *= ka;
-        b[i] *= kb;
+        r[i] *= k;
+        e[i] *= k;
     }
 }
 
@@ -389,12 +391,12 @@ cudaError_t net_convert(const float* w, uint16_t* wb, uint16_t* wbt, cudaStream_
     return cudaGetLastError();
 }
 
-cudaError_t net_forward(const uint16_t* wb, NetWorkspace& ws, const double* in, const uint8_t* mask, double* out64,
-                        float* out32, cudaStream_t s) {
+cudaError_t net_forward(const uint16_t* wb, NetWorkspace& ws, const double* in, const uint8_t* mask, double in_scale,
+                        double* out64, float* out32, cudaStream_t s) {
     const int64_t nvox = (int64_t)ws.nx * ws.ny * ws.nz;
     if (nvox == 0) return cudaSuccess;
     const int gc = grid_for(nvox, CTPB, 16);
-    k_pack<<<elementwise_grid(nvox), RTPB, 0, s>>>(nvox, in, mask, ws.a0);
+    k_pack<<<elementwise_grid(nvox), RTPB, 0, s>>>(nvox, in, mask, in_scale, ws.a0);
     k_conv<1, NET_C, uint16_t, EPI_RELU><<<gc, CTPB, 0, s>>>(ws.a0, wb, nullptr, nullptr, ws.a1, nullptr, nullptr,
                                                              ws.nx, ws.ny, ws.nz);
     k_conv<NET_C, NET_C, uint16_t, EPI_RELU><<<gc, CTPB, 0, s>>>(ws.a1, wb + NET_OFF2, nullptr, nullptr, ws.a2, nullptr,
@@ -448,9 +450,10 @@ cudaError_t pair_error(int64_t n, const double* e0, const double* z, double* e1,
     return cudaGetLastError();
 }
 
-cudaError_t pair_normalise(int64_t n, double* a, double* b, double count, double* partial, cudaStream_t s) {
-    k_dots<<<NET_PARTIALS, RTPB, 0, s>>>(n, a, a, b, b, partial);
-    k_scale2<<<elementwise_grid(n), RTPB, 0, s>>>(n, a, b, count, partial);
+cudaError_t pair_normalise(int64_t n, double* r, double* e, double count, double* partial, double* r_rms,
+                           cudaStream_t s) {
+    k_dots<<<NET_PARTIALS, RTPB, 0, s>>>(n, r, r, e, e, partial);
+    k_pair_scale<<<elementwise_grid(n), RTPB, 0, s>>>(n, r, e, count, partial, r_rms);
     add_launches(2);
     return cudaGetLastError();
 }

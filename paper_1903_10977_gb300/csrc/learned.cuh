@@ -43,10 +43,10 @@ struct NetWorkspace {
 // weights ([26 - tap][in][out]) that turn the input gradient into a forward convolution.
 cudaError_t net_convert(const float* w, uint16_t* wb, uint16_t* wbt, cudaStream_t s);
 
-// N(in) on the grid of ws: a0 = bf16(float(in)) on the mask (mask null: every voxel),
-// a1, a2 stored; the output goes to out64 (FP64, zero off the mask) and/or out32.
-cudaError_t net_forward(const uint16_t* wb, NetWorkspace& ws, const double* in, const uint8_t* mask, double* out64,
-                        float* out32, cudaStream_t s);
+// N(in_scale in) on the grid of ws: a0 = bf16(float(in_scale in)) on the mask (mask null:
+// every voxel), a1, a2 stored; the output goes to out64 (FP64, zero off the mask) and/or out32.
+cudaError_t net_forward(const uint16_t* wb, NetWorkspace& ws, const double* in, const uint8_t* mask, double in_scale,
+                        double* out64, float* out32, cudaStream_t s);
 
 // After net_forward(..., out32 = ws.o): grad += dL/dw of L = scale sum_v m_v (o_v - t_v)^2
 // and loss[0] += L (device double).
@@ -65,7 +65,8 @@ cudaError_t stage_update(int64_t n, const double* r1, const double* c, const dou
 
 // e1 = e0 - z (e1 may alias neither input)
 cudaError_t pair_error(int64_t n, const double* e0, const double* z, double* e1, cudaStream_t s);
-// a /= sqrt(sum(a^2) / count), b /= sqrt(sum(b^2) / count)
-cudaError_t pair_normalise(int64_t n, double* a, double* b, double count, double* partial, cudaStream_t s);
+// r, e /= sqrt(sum(e^2) / count); r_rms (device, may be null) = sqrt(sum(r^2) / count) afterwards
+cudaError_t pair_normalise(int64_t n, double* r, double* e, double count, double* partial, double* r_rms,
+                           cudaStream_t s);
 
 }  // namespace imgm

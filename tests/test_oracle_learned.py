@@ -85,6 +85,19 @@ def test_loss_gradient_matches_finite_differences():
         assert abs(fd - g[k]) <= 1e-6 * max(abs(g).max(), 1e-12), (k, fd, g[k])
 
 
+def test_input_scale_is_homogeneous():
+    """No biases and ReLU: N(a r) = a N(r) for a > 0 (exact forward), so the stage's step
+    omega makes any input scale irrelevant."""
+    rng = np.random.default_rng(12)
+    shape = (4, 5, 6)
+    mask = (rng.random(shape) < 0.7).astype(float)
+    r = rng.standard_normal(shape)
+    w = initial_weights(13)
+    a, _ = NL.forward(w, r, mask, bf16=False, in_scale=8.0)
+    b, _ = NL.forward(w, r, mask, bf16=False)
+    assert np.allclose(a, 8.0 * b, rtol=1e-12, atol=1e-14)
+
+
 def test_forward_bf16_rounds_only_where_stored():
     """With weights and data exactly representable in bfloat16 and small enough that no
     sum needs more than 8 bits, the bf16 and the exact forward agree exactly."""
@@ -163,8 +176,10 @@ def test_training_pair_is_vcycle_error_propagation():
     e0 = np.random.default_rng(11).standard_normal(n)
     r1, e1 = NL.training_pair(A, H.precondition, e0)
     e_ref = e0 - B @ (A @ e0)
-    r_ref = A @ e_ref
-    assert np.allclose(e1, e_ref / np.sqrt(np.mean(e_ref ** 2)), rtol=1e-10, atol=1e-12)
-    assert np.allclose(r1, r_ref / np.sqrt(np.mean(r_ref ** 2)), rtol=1e-10, atol=1e-10)
+    s = np.sqrt(np.mean(e_ref ** 2))
+    assert np.allclose(e1, e_ref / s, rtol=1e-10, atol=1e-12)
+    assert np.allclose(r1, (A @ e_ref) / s, rtol=1e-10, atol=1e-10)
+    # the set's input scale is the reciprocal of the mean rms of its residuals
+    assert abs(NL.input_scale([(r1, e1), (2 * r1, e1)]) - 1.0 / (1.5 * np.sqrt(np.mean(r1 ** 2)))) < 1e-12
     # the V-cycle is a contraction in the A-norm: the pair's error is smaller than e0's
     assert e_ref @ (A @ e_ref) < e0 @ (A @ e0)
