@@ -26,7 +26,9 @@ of the published methods it uses:
 * gradients by the chain rule (reverse mode), Adam (Kingma and Ba, 2015, Algorithm 1)
   with bias correction on FP32 master weights;
 * flexible CG with the Polak-Ribiere beta (z_{k+1} . (r_{k+1} - r_k)) / (z_k . r_k),
-  as the stage makes the preconditioner vary from step to step (Notay, 2000).
+  as the stage makes the preconditioner vary from step to step (Notay, 2000), and its
+  truncated form FCG(m), which A-orthogonalises each new direction against the last m
+  directions instead of one (Notay, 2000): FCG(1) is the Polak-Ribiere form.
 """
 from __future__ import annotations
 
@@ -196,4 +198,29 @@ def flexible_pcg(A, b, precond, rtol: float = 1e-8, maxit: int = 1000):
         rz = float(z @ r_new)
         p = z + beta * p
         r = r_new
+    return x, maxit, hist
+
+
+def fcg(A, b, precond, m: int, rtol: float = 1e-8, maxit: int = 1000):
+    """Truncated flexible CG, FCG(m): p_k = z_k minus its A-projections on the last m
+    directions, alpha_k = (r_k . p_k) / (p_k . A p_k).  Returns (x, iterations, history)."""
+    x = np.zeros_like(b)
+    r = b.copy()
+    bnorm = np.linalg.norm(b)
+    hist = [np.linalg.norm(r) / bnorm]
+    dirs = []                             # (p_j, A p_j, p_j . A p_j) of the last m steps
+    for k in range(1, maxit + 1):
+        z = precond(r)
+        p = z.copy()
+        for pj, qj, pqj in dirs:
+            p = p - (float(z @ qj) / pqj) * pj
+        q = A @ p
+        pq = float(p @ q)
+        alpha = float(r @ p) / pq
+        x = x + alpha * p
+        r = r - alpha * q
+        hist.append(np.linalg.norm(r) / bnorm)
+        if hist[-1] <= rtol:
+            return x, k, hist
+        dirs = (dirs + [(p, q, pq)])[-m:]
     return x, maxit, hist

@@ -11,6 +11,8 @@ invariants (no GPU).
   never a larger A-norm error than the V-cycle alone;
 * flexible CG with a fixed SPD preconditioner takes the iterations of standard PCG
   (Polak-Ribiere = Fletcher-Reeves beta in exact arithmetic) and reaches the dense solve;
+  FCG(m) for any m gives the PCG iterates then (the directions are A-conjugate already),
+  and it converges with a preconditioner that varies from step to step;
 * training pairs: e1 = (I - B A) e0 with B assembled column by column from the V-cycle.
 """
 import numpy as np
@@ -183,3 +185,23 @@ def test_training_pair_is_vcycle_error_propagation():
     assert abs(NL.input_scale([(r1, e1), (2 * r1, e1)]) - 1.0 / (1.5 * np.sqrt(np.mean(r1 ** 2)))) < 1e-12
     # the V-cycle is a contraction in the A-norm: the pair's error is smaller than e0's
     assert e_ref @ (A @ e_ref) < e0 @ (A @ e0)
+
+
+def test_fcg_reduces_to_pcg_and_keeps_m_directions_conjugate():
+    from oracle.multigrid import pcg
+    A = _spd(60, 14)
+    D = sp.diags(1.0 / A.diagonal())
+    b = np.random.default_rng(15).standard_normal(60)
+    x2, k2, h2 = pcg(A, b, lambda r: D @ r, rtol=1e-10)
+    for m in (1, 3, 8):
+        x1, k1, h1 = NL.fcg(A, b, lambda r: D @ r, m, rtol=1e-10)
+        assert k1 == k2 and np.allclose(h1, h2, rtol=1e-6, atol=1e-14)
+    x1, _, _ = NL.flexible_pcg(A, b, lambda r: D @ r, rtol=1e-10)
+    assert np.allclose(NL.fcg(A, b, lambda r: D @ r, 1, rtol=1e-10)[0], x1, rtol=1e-8, atol=1e-12)
+    # a preconditioner that changes every step: FCG(3) still converges
+    rng = np.random.default_rng(16)
+
+    def varying(r):
+        return (1.0 + 0.5 * rng.random()) * (D @ r) + 0.1 * (D @ (D @ r))
+    x, k, _ = NL.fcg(A, b, varying, 3, rtol=1e-10, maxit=500)
+    assert np.linalg.norm(b - A @ x) <= 1e-9 * np.linalg.norm(b)
