@@ -477,7 +477,7 @@ def train_net(net: Net, pairs, shape, steps: int, lr: float = 1e-3, batch: int =
     is multiplied by in_scale (the set's 1 / mean rms(r1), see Solver.learned_pair).
     Returns the per-step losses (device tensor)."""
     import torch
-    losses = torch.zeros(steps, dtype=torch.float64, device="cuda")
+    losses = torch.zeros(steps, dtype=torch.float64, device=pairs[0][0].device)
     scales = [1.0 / (batch * max(int(m.sum().item()), 1)) for _, _, m in pairs]
     k = 0
     for it in range(steps):

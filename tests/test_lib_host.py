@@ -156,3 +156,54 @@ def test_box_without_holes():
     S = lib.Solver(2, np.zeros((0, 2)), np.zeros(0), 16, 2, 3, 0, 1, host_only=True)
     info = S.level_info(3)
     assert info["n_active"] == (16 + 2 - 2) ** 2 and info["n_band"] == 0
+
+
+def test_learned_stage_arguments_checked_before_the_gpu():
+    """The network and stage entry points reject bad arguments on the host, before any
+    CUDA call (so these run without a GPU)."""
+    import ctypes
+    L = lib._lib
+    out = ctypes.c_void_p()
+    assert L.imgm_net_create(None, ctypes.byref(out)) == -1
+    w = np.zeros(lib.NET_WEIGHTS, dtype=np.float32)
+    assert L.imgm_net_create(w.ctypes.data_as(ctypes.c_void_p), None) == -1
+    assert L.imgm_net_forward(None, 4, 4, 4, None, None, None, None) == -1
+    assert L.imgm_net_accumulate(None, 4, 4, 4, None, None, None, 1.0, 1.0, None, None) == -1
+    assert L.imgm_net_adam_step(None, 1e-3, 0.9, 0.999, 1e-8, None) == -1
+    assert L.imgm_net_zero_grad(None, None) == -1
+    assert L.imgm_net_get_weights(None, None) == -1
+    pr, lay, _, _ = oracle_for("disc1_32_p2")
+    S = solver_for(lib, pr, lay, host_only=True)
+    for rc in (L.imgm_set_net(S._h, None), L.imgm_learned_stage(S._h, None, None, None, None),
+               L.imgm_learned_pair(S._h, None, None, None, None, None)):
+        assert rc == -1                                  # a host-only handle has no device data
+    S.close()
+
+
+def test_train_net_schedule():
+    """train_net: one zero_grad and one Adam step per step, `batch` accumulations taken in
+    turn over the pairs, each pair's loss scaled by 1 / (batch * its active count), the set's
+    input scale passed through."""
+    torch = pytest.importorskip("torch")
+    calls = []
+
+    class FakeNet:
+        def zero_grad(self, stream=None):
+            calls.append(("zero",))
+
+        def accumulate(self, x, target, shape, loss, mask=None, scale=1.0, in_scale=1.0, stream=None):
+            calls.append(("acc", int(x[0].item()), scale, in_scale, shape))
+            loss += 1.0
+
+        def adam_step(self, lr, stream=None):
+            calls.append(("adam", lr))
+
+    pairs = [(torch.full((4,), float(k)), torch.zeros(4), torch.tensor([1, 1, 0, k % 2], dtype=torch.uint8))
+             for k in range(3)]
+    losses = lib.train_net(FakeNet(), pairs, (1, 2, 2), steps=2, lr=0.01, batch=2, in_scale=7.0)
+    assert [c[0] for c in calls] == ["zero", "acc", "acc", "adam", "zero", "acc", "acc", "adam"]
+    accs = [c for c in calls if c[0] == "acc"]
+    assert [a[1] for a in accs] == [0, 1, 2, 0]
+    assert [a[2] for a in accs] == [1 / (2 * 2), 1 / (2 * 3), 1 / (2 * 2), 1 / (2 * 2)]
+    assert all(a[3] == 7.0 and a[4] == (1, 2, 2) for a in accs)
+    assert losses.tolist() == [2.0, 2.0]
