@@ -223,7 +223,11 @@ void imgm_batch_destroy(imgm_batch* b);
  * Weights: IMGM_NET_WEIGHTS floats, layer by layer, each layer [tap][out][in] with
  * tap = 9 (dz + 1) + 3 (dy + 1) + (dx + 1); a grid vector of nx * ny * nz entries is
  * indexed x + nx (y + ny z) (a finest-level vector of a 3-D problem: nx = ny = nz = m).
- * Network calls report errors through imgm_last_error(NULL). */
+ * Network calls report errors through imgm_last_error(NULL): IMGM_ERR_INVALID for a null
+ * pointer, an empty grid or a bad scale or Adam parameter (checked before any CUDA call),
+ * IMGM_ERR_CUDA when an allocation or launch fails.  Device vectors passed in stay owned
+ * by the caller; the library keeps no pointer to them after a call returns (a network
+ * owns its weights, Adam state and activation buffers; a handle owns its stage vectors). */
 #define IMGM_NET_WEIGHTS 7776
 
 typedef struct imgm_net imgm_net;
