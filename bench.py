@@ -1,18 +1,21 @@
 """Benchmark: DOF/s of the multigrid-preconditioned CG solve to relative residual 1e-8.
 
 Workload (one "step" = one whole solve from x0 = 0, every hot-path step included):
-2-D Poisson on [0,1]^2 minus 10 seeded discs (r ~ U(0.03, 0.1)), 512 x 512 background
-grid, quadratic open B-splines, 6 levels, depth-0 cut cells, symmetric Nitsche on the
-immersed boundary, additive Schwarz smoothing.  The timed solves run the V-cycle in FP32
-on Jacobi-scaled data inside the FP64 CG (--precision mixed, default); the plain FP64
-path is timed the same way beside it ("fp64" in the JSON line, "speedup_vs_fp64").
+3-D Poisson on the unit cube minus 20 seeded spheres (r ~ U(0.05, 0.15)), 128^3 background
+grid, quadratic open B-splines (1,965,303 active functions), 5 levels, depth-2 octree cut-cell
+quadrature, symmetric Nitsche on the immersed boundary, additive Schwarz smoothing.  The
+headline value is the plain FP64 V-cycle solve (--precision fp64, default); the FP32
+V-cycle inside the FP64 flexible CG ("mixed") and the FP64-finest hybrid are timed beside
+it on the same problem, with their speed-up at the same 1e-8 residual.  The 512x512 2-D
+workload, the batched solves and the learned stage are reported as sub-objects.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 Prints one JSON line (rank 0).  With N > 1 (torchrun) every rank solves its own seeded
 geometry (independent problems, no collective on the data path: weak scaling); the
 timed region is bracketed by barriers and the maximum over ranks is taken.
-The reference arm times the FP64 CPU oracle (the only other place this script runs it).
+The CPU legs (cpu_baseline, and the reference arm) time the FP64 CPU oracle, the only
+other place this script runs it, on a 32^3 instance of the same 20-sphere geometry.
 """
 from __future__ import annotations
 
@@ -30,29 +33,35 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "DOF/s to rel. residual 1e-8 (PCG+MG) vs plain FP64 GPU; HBM GB/s of roofline"
-# DRAM bytes of one finest-level FP64 apply launch on this workload, from one ncu capture
-# (dram__bytes_read.sum 4.908 MB + dram__bytes_write.sum 0); null it when the kernel changes
-APPLY_TRAFFIC_BYTES = 4.908032e6
-WORKLOAD = "poisson2d-512x512-10discs-bspline-p2-6levels-nitsche"
-PRESET = "discs10_512_p2"
-WORKLOADS = ("discs10_512_p2", "discs10_512_p1", "discs10_512_p3", "spheres20_128_p2", "disc1_32_p2", "box_256_p2")
+PRESET = "spheres20_128_p2"
+WORKLOADS = ("spheres20_128_p2", "discs10_512_p2", "discs10_512_p1", "discs10_512_p3", "disc1_32_p2", "box_256_p2")
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one finest-level FP64 apply
+# launch with p^T A p, per workload, from one ncu capture of the current kernel (null when
+# none has been taken since the kernel last changed)
+APPLY_TRAFFIC_BYTES = {}
+APPLY_TRAFFIC_SOURCE = {}
 
 
 def workload_name(pr) -> str:
-    if pr.name == PRESET:
-        return WORKLOAD
     holes = {"disc1": "1disc", "discs10": "10discs", "spheres20": "20spheres", "none3": "noholes"}[pr.layout]
     size = "x".join([str(pr.n)] * pr.dim)
     basis = "bspline" if pr.basis == 0 else "lagrange"
     return f"poisson{pr.dim}d-{size}-{holes}-{basis}-p{pr.degree}-{pr.levels}levels-depth{pr.depth}-nitsche"
+
+
 RTOL = 1e-8
-# learned stage (--learned): training geometries of the workload's hole layout at
-# LEARN_N^3, pairs per geometry, Adam steps, pairs per step, step size
+# learned stage: training geometries of the workload's hole layout at LEARN_N^3, pairs per
+# geometry, Adam steps, pairs per step, step size
 LEARN_GEOMS, LEARN_N, LEARN_PAIRS, LEARN_STEPS, LEARN_BATCH, LEARN_LR = 4, 64, 8, 800, 4, 1e-3
 FP32_PEAK_NOTE = "152 SMs x 128 FP32 FMA/clk x 2 flop x 2070 MHz"
 MAXIT = 2000
 FP64_PEAK_NOTE = "152 SMs x 2 FP64 FMA/clk x 2 flop x 2070 MHz"
-CPU_SAMPLE_N, CPU_SAMPLE_LEVELS = 128, 4
+# CPU oracle sample: the workload's geometry (same hole layout and seed) on a 32^3 grid
+# with 4 levels (coarsest 4^3, as the workload's 8^3 at 128^3 with 5 levels is one level
+# below 16^3); depth-0 cut-cell quadrature, since the oracle's depth-2 assembly of that
+# grid alone takes ~20 min (the solve phase, which is what is timed, does not depend on
+# the quadrature depth: same rows, blocks and levels)
+CPU_SAMPLE = {"n": 32, "levels": 4, "depth": 0}
 
 
 def fp64_peak_tflops(sm_mhz: float = 2070.0) -> float:
@@ -66,44 +75,98 @@ def measured_peaks():
         return {}
 
 
-# ------------------------------------------------------------------ CPU oracle leg
-_ORACLE_SCRIPT = r"""
-import json, sys, time
+# ------------------------------------------------------------------ CPU oracle legs
+# Build once (one process, single-threaded), pickle the assembled system and hierarchy,
+# then time solves in fresh processes: one alone (single thread) and one per host core
+# at the same time (each an independent copy of the same solve: the oracle's sparse
+# products are single-threaded, so the machine's throughput is that of parallel solves).
+_ORACLE_BUILD = r"""
+import pickle, sys, time
 sys.path.insert(0, {root!r})
 from oracle import discretize as D, geometry as G, multigrid as MG
 from synthetic import config_layout, preset
-pr = preset({preset!r}, n={n}, levels={levels})
+pr = preset({preset!r}, n={n}, levels={levels}, depth={depth})
 lay = config_layout(pr.layout, {seed})
+t0 = time.perf_counter()
 d = D.Discretization(G.Balls(lay.centers, lay.radii), pr.basis, pr.degree, pr.n, pr.depth, pr.bc)
 H = MG.Hierarchy(d, pr.levels)
+with open({path!r}, "wb") as f:
+    pickle.dump({{"A": d.A, "b": d.b, "H": H, "n_active": int(d.n_active),
+                 "build_s": time.perf_counter() - t0}}, f)
+"""
+
+_ORACLE_SOLVE = r"""
+import json, pickle, sys, time
+sys.path.insert(0, {root!r})
+from oracle import multigrid as MG
+o = pickle.load(open({path!r}, "rb"))
+while time.time() < {start}:
+    time.sleep(0.01)
 times, its = [], []
 for k in range({reps}):
     t0 = time.perf_counter()
-    x, it, hist = MG.pcg(d.A, d.b, H.precondition, rtol={rtol}, maxit={maxit})
+    x, it, hist = MG.pcg(o["A"], o["b"], o["H"].precondition, rtol={rtol}, maxit={maxit})
     times.append(time.perf_counter() - t0)
     its.append(it)
-print(json.dumps({{"n_active": int(d.n_active), "times": times, "iterations": its, "rel": hist[-1]}}))
+print(json.dumps({{"n_active": o["n_active"], "times": times, "iterations": its, "rel": hist[-1],
+                  "build_s": o["build_s"]}}))
 """
 
-
-def run_oracle(reps: int, seed: int = 0):
-    """Oracle CG solve (setup excluded) on the 128 x 128 instance of the workload, single thread."""
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    code = _ORACLE_SCRIPT.format(root=ROOT, preset=PRESET, n=CPU_SAMPLE_N, levels=CPU_SAMPLE_LEVELS, seed=seed,
-                                 reps=reps, rtol=RTOL, maxit=MAXIT)
-    r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=1800)
-    if r.returncode != 0:
-        raise RuntimeError("oracle run failed: " + r.stderr[-2000:])
-    return json.loads(r.stdout.strip().splitlines()[-1])
+_ONE_THREAD = dict(OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
 
 
-def cpu_baseline_entry(o):
-    t = statistics.median(o["times"])
-    return {"value": o["n_active"] / t, "unit": "DOF/s", "cores": 1, "kind": "oracle",
-            "sample": (f"FP64 CPU oracle (numpy/scipy, 1 thread) CG solve to 1e-8 of the {CPU_SAMPLE_N}x{CPU_SAMPLE_N} "
-                       f"instance of the same geometry ({CPU_SAMPLE_LEVELS} levels, {o['n_active']} DOFs, "
-                       f"{o['iterations'][0]} iterations), setup excluded; median of {len(o['times'])} solves"),
-            "host_cpus": os.cpu_count()}
+def oracle_build_start(seed: int = 0):
+    """Starts the oracle's assembly of the CPU sample in the background; returns (process, path)."""
+    path = os.path.join(tempfile.mkdtemp(prefix="imgm_oracle_"), "system.pkl")
+    code = _ORACLE_BUILD.format(root=ROOT, preset=PRESET, seed=seed, path=path, **CPU_SAMPLE)
+    proc = subprocess.Popen([sys.executable, "-c", code], env=dict(os.environ, **_ONE_THREAD),
+                            stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True)
+    return proc, path
+
+
+def oracle_build_wait(proc, path):
+    _, err = proc.communicate(timeout=3600)
+    if proc.returncode != 0:
+        raise RuntimeError("oracle build failed: " + err[-2000:])
+    return path
+
+
+def oracle_solves(path: str, procs: int, reps: int):
+    """Runs `procs` single-threaded solve processes at once, each timing `reps` solves of the
+    pickled system; returns their JSON results."""
+    start = time.time() + 2.0 + 0.05 * procs          # all start together after loading
+    code = _ORACLE_SOLVE.format(root=ROOT, path=path, start=start, reps=reps, rtol=RTOL, maxit=MAXIT)
+    ps = [subprocess.Popen([sys.executable, "-c", code], env=dict(os.environ, **_ONE_THREAD),
+                           stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True) for _ in range(procs)]
+    out = []
+    for p in ps:
+        o, e = p.communicate(timeout=3600)
+        if p.returncode != 0:
+            raise RuntimeError("oracle solve failed: " + e[-2000:])
+        out.append(json.loads(o.strip().splitlines()[-1]))
+    return out
+
+
+def sample_text(o, procs: int, reps: int) -> str:
+    return (f"FP64 CPU oracle (numpy/scipy) CG solve to 1e-8 of the 20-sphere workload geometry at "
+            f"{CPU_SAMPLE['n']}^3 ({CPU_SAMPLE['levels']} levels, depth-{CPU_SAMPLE['depth']} cut-cell "
+            f"quadrature, {o['n_active']} DOFs, {o['iterations'][0]} iterations), setup excluded; "
+            f"{procs} single-threaded process{'es' if procs > 1 else ''} at once, {reps} solves each")
+
+
+def cpu_baseline_entry(path: str, reps: int = 3):
+    """Single-thread and all-cores throughput of the oracle solve on the CPU sample."""
+    one = oracle_solves(path, 1, reps)[0]
+    t1 = statistics.median(one["times"])
+    ncpu = os.cpu_count() or 1
+    many = oracle_solves(path, ncpu, reps)
+    t_all = max(sum(o["times"]) for o in many)
+    value_all = ncpu * reps * many[0]["n_active"] / t_all
+    return {"value": value_all, "unit": "DOF/s", "cores": ncpu, "kind": "oracle",
+            "sample": sample_text(many[0], ncpu, reps), "host_cpus": ncpu,
+            "single_thread": {"value": one["n_active"] / t1, "unit": "DOF/s", "cores": 1,
+                              "median_s": t1, "times_s": one["times"]},
+            "oracle_build_s": one["build_s"]}
 
 
 # ------------------------------------------------------------------ clocks
@@ -353,12 +416,15 @@ def run_learned(args, lib, torch, pr, S64, timed_solves, total_units, t64, res64
 
 
 def run_ours(args, rank, world, local_rank):
-    import numpy as np
     import torch
 
     import paper_1903_10977_gb300 as lib
     from synthetic import config_layout, preset
 
+    # the oracle's CPU sample is assembled on one host core while the GPU legs run
+    oracle = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        oracle = oracle_build_start(args.seed)
     torch.cuda.set_device(local_rank)
     dist = None
     if world > 1:
@@ -373,14 +439,15 @@ def run_ours(args, rank, world, local_rank):
     pr = preset(args.workload)
     lay = config_layout(pr.layout, args.seed + rank)
     code = {"fp64": 0, "mixed": 1, "hybrid": 2}[args.precision]
-    mixed = code != 0            # an FP32 V-cycle (all levels, or below an FP64 finest level)
     headline = args.workload == PRESET
+
+    def make(precision, smoother=0, p=pr, l=lay):
+        return lib.Solver(p.dim, l.centers, l.radii, p.n, p.degree, p.levels, p.depth, p.bc, basis=p.basis,
+                          lo=l.lo, hi=l.hi, precision=precision, smoother=smoother)
+
     t0 = time.perf_counter()
-    S = lib.Solver(pr.dim, lay.centers, lay.radii, pr.n, pr.degree, pr.levels, pr.depth, pr.bc, basis=pr.basis,
-                   precision=code)
+    S = make(code)
     setup_s = time.perf_counter() - t0
-    S64 = S if not mixed else lib.Solver(pr.dim, lay.centers, lay.radii, pr.n, pr.degree, pr.levels, pr.depth,
-                                         pr.bc, basis=pr.basis, precision=0)
     info = S.level_info(S.L)
     n_active, n_grid = info["n_active"], info["n_grid"]
     b = S.rhs()
@@ -388,43 +455,56 @@ def run_ours(args, rank, world, local_rank):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")   # > 129 MB L2
     stream = torch.cuda.current_stream()
 
-    def timed_solves(solver, steps, warmup, label):
+    def timed_solves(solver, steps, warmup, label, rhs=None):
         """Device time of `steps` whole solves, each after an L2 flush (flush outside the events).
         The timed solves sit in the NVTX range `label` (lets ncu select their launches)."""
+        bb = b if rhs is None else rhs
+        xx = x if rhs is None else torch.zeros_like(rhs)
         for _ in range(warmup):
-            x.zero_()
-            solver.pcg_solve(b, x, rtol=RTOL, maxit=MAXIT)
+            xx.zero_()
+            solver.pcg_solve(bb, xx, rtol=RTOL, maxit=MAXIT)
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
         res = []
         barrier()
         torch.cuda.nvtx.range_push(label)
         for k in range(steps):
             flush.fill_(float(k))
-            x.zero_()
+            xx.zero_()
             ev[k][0].record(stream)
-            _, r, _ = solver.pcg_solve(b, x, rtol=RTOL, maxit=MAXIT)
+            _, r, _ = solver.pcg_solve(bb, xx, rtol=RTOL, maxit=MAXIT)
             ev[k][1].record(stream)
             res.append(r)
         torch.cuda.nvtx.range_pop()
         barrier()
         return sum(a.elapsed_time(c) for a, c in ev) / 1e3, res
 
+    def form(t, res, units, t_ref=None):
+        out = {"value": units / t, "unit": "DOF/s", "ms_per_step": 1e3 * t / len(res),
+               "iterations": res[0]["iterations"], "true_rel_residual": max(r["true_rel_residual"] for r in res),
+               "gpu_launches_per_solve": int(res[0]["kernel_launches"])}
+        if t_ref is not None:
+            out["speedup_vs_fp64"] = t_ref / t
+        return out
+
     with ClockSampler(local_rank) as clk:
         t_dev, results = timed_solves(S, args.steps, args.warmup, f"solve_{args.precision}")
     clocks = clk.summary()
-    t64, res64 = (t_dev, results) if not mixed else timed_solves(S64, args.steps, args.warmup, "solve_fp64")
-    # the same solve with coloured multiplicative Schwarz (Sec. 3.4), and the batch, beside
-    # the headline workload (other workloads: the two precisions only)
-    t_mult, res_mult, batched = None, None, None
-    if headline:
-        SM = lib.Solver(pr.dim, lay.centers, lay.radii, pr.n, pr.degree, pr.levels, pr.depth, pr.bc,
-                        basis=pr.basis, precision=1 if mixed else 0, smoother=1)
-        t_mult, res_mult = timed_solves(SM, args.steps, args.warmup, "solve_multiplicative")
-        SM.close()
-        batched = run_batched(lib, torch, mixed, max(1, args.steps // 2), 1)
+    units = n_active * args.steps
+    # the other V-cycle precisions on the same problem, each against the FP64 solve
+    t64, res64, S64 = (t_dev, results, S) if code == 0 else (None, None, None)
+    forms = {}
+    wanted = [f for f in ("fp64", "mixed", "hybrid") if f != args.precision and (f == "fp64" or not args.quick)]
+    for f in wanted:
+        Sf = make({"fp64": 0, "mixed": 1, "hybrid": 2}[f])
+        tf, rf = timed_solves(Sf, args.steps, args.warmup, f"solve_{f}")
+        if f == "fp64":
+            t64, res64, S64 = tf, rf, Sf
+        else:
+            forms[f] = (tf, rf)
+            Sf.close()
     learned = None
-    if args.learned and pr.dim == 3:
-        learned = run_learned(args, lib, torch, pr, S64, timed_solves, n_active * args.steps, t64, res64)
+    if pr.dim == 3 and not args.no_learned:
+        learned = run_learned(args, lib, torch, pr, S64, timed_solves, units, t64, res64)
 
     # end to end: host (pinned) b in, host x out, through the C-ABI
     bh = torch.empty(n_grid, dtype=torch.float64, pin_memory=True)
@@ -441,71 +521,46 @@ def run_ours(args, rank, world, local_rank):
     barrier()
     t_e2e = time.perf_counter() - e0
 
-    # FP64 finest-level operator apply (run once per CG iteration in both paths), timed alone
-    xs = torch.randn(n_grid, dtype=torch.float64, device="cuda") * torch.as_tensor(
-        S.active_mask(), dtype=torch.float64, device="cuda")
-    ys = torch.empty_like(xs)
-    for _ in range(5):
-        S.apply_operator(xs, ys)
-    reps = 200
-    k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    # the 200 launches replayed from a CUDA graph, so that host launch gaps do not enter the
-    # per-launch time (stream launches as the fallback)
-    apply_graph = None
-    try:
-        apply_graph = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(apply_graph):
-            for _ in range(reps):
-                S.apply_operator(xs, ys)
-        apply_graph.replay()
-        torch.cuda.synchronize()
-    except Exception:
-        apply_graph = None
-    torch.cuda.nvtx.range_push("finest_apply_timing")      # lets ncu select these launches
-    k0.record(stream)
-    if apply_graph is not None:
-        apply_graph.replay()
-    else:
-        for _ in range(reps):
-            S.apply_operator(xs, ys)
-    k1.record(stream)
-    torch.cuda.synchronize()
-    torch.cuda.nvtx.range_pop()
-    apply_ms = k0.elapsed_time(k1) / reps
-
+    apply_ms, apply_graph = time_finest_apply(S, torch, stream, n_grid)
     vcycle = vcycle_bandwidth(S, torch, stream, code == 1)
-    (t_dev, t64, t_e2e), total_units = reduce_replicas(dist, "cuda", [t_dev, t64, t_e2e], n_active * args.steps)
+    # the 2-D 512x512 workload and the batch beside the 3-D headline
+    poisson2d = run_2d(args, lib, torch, timed_solves) if headline and not args.quick else None
+    batched = run_batched(lib, torch, code != 0, max(1, args.steps // 2), 1) if headline and not args.quick else None
+
+    times = [t_dev, t64, t_e2e] + [forms[f][0] for f in sorted(forms)]
+    times, total_units = reduce_replicas(dist, "cuda", times, units)
+    t_dev, t64, t_e2e = times[:3]
     if dist is not None:
         dist.destroy_process_group()
     if rank != 0:
         return None
     value = total_units / t_dev
-    value64 = total_units / t64
-    its = [r["iterations"] for r in results]
     flops = apply_flops(S)
     achieved = flops / (apply_ms * 1e-3) / 1e12
     peak = fp64_peak_tflops()
+    wl = workload_name(pr)
     line = {
         "metric": METRIC, "value": value, "unit": "DOF/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * t_dev / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32" if mixed else "f64", "data": "synthetic",
-        "config": {"workload": workload_name(pr), "dim": pr.dim, "n": pr.n,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if code == 0 else "f64+f32", "data": "synthetic",
+        "config": {"workload": wl, "dim": pr.dim, "n": pr.n,
                    "basis": "bspline" if pr.basis == 0 else "lagrange", "degree": pr.degree,
                    "levels": pr.levels, "holes": lay.n_holes, "depth": pr.depth, "bc": "nitsche", "rtol": RTOL,
                    "n_active": n_active, "n_grid": n_grid, "seed": args.seed, "parallelism": f"replicas{world}",
                    "vcycle": {0: "fp64", 1: "fp32 (Jacobi-scaled) in fp64 flexible CG",
                               2: "fp64 finest level, fp32 (Jacobi-scaled) below, in fp64 flexible CG"}[code],
+                   "smoother": "additive Schwarz",
                    "l2": "flushed (256 MiB write) before every timed solve, flush outside the events",
-                   "iterations": its[0], "true_rel_residual": results[-1]["true_rel_residual"],
-                   "setup_s": setup_s},
-        "fp64": {"value": value64, "unit": "DOF/s", "ms_per_step": 1e3 * t64 / args.steps,
-                 "iterations": res64[0]["iterations"], "true_rel_residual": res64[-1]["true_rel_residual"]},
-        "speedup_vs_fp64": value / value64,
-        "multiplicative": None if t_mult is None else {
-            "value": total_units / t_mult, "unit": "DOF/s", "ms_per_step": 1e3 * t_mult / args.steps,
-            "iterations": res_mult[0]["iterations"], "true_rel_residual": res_mult[-1]["true_rel_residual"],
-            "gpu_launches_per_solve": int(res_mult[0]["kernel_launches"]),
-            "smoother": "coloured multiplicative Schwarz, same precision as the headline"},
+                   "iterations": results[0]["iterations"],
+                   "true_rel_residual": max(r["true_rel_residual"] for r in results), "setup_s": setup_s},
+    }
+    if code != 0:
+        line["fp64"] = form(t64, res64, total_units)
+        line["speedup_vs_fp64"] = t64 / t_dev
+    for k, f in enumerate(sorted(forms)):
+        line[f] = form(times[3 + k], forms[f][1], total_units, t64)
+    line.update({
+        "poisson2d_512": poisson2d,
         "batched": batched,
         "learned": learned,
         "vcycle": vcycle,
@@ -513,44 +568,110 @@ def run_ours(args, rank, world, local_rank):
                 "d2h_bytes_per_step": 8 * n_grid},
         "gpu_launches": sum(int(r["kernel_launches"]) for r in results),
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                     "traffic": APPLY_TRAFFIC_BYTES if headline else None,
-                     "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of this kernel on this "
-                                       "workload (profiles/k_apply_fp64_poisson2d_512_p2.md)",
+                     "traffic": APPLY_TRAFFIC_BYTES.get(wl),
+                     "traffic_source": APPLY_TRAFFIC_SOURCE.get(wl, "no capture of the current kernel"),
                      "kernel": ("k_apply_tile2d<double>" if pr.dim == 2 else "k_apply_tile3d<double>")
-                               + " (finest-level operator apply, FP64)",
+                               + " (finest-level FP64 operator apply, imgm_apply_operator)",
                      "peak_source": "derived: " + FP64_PEAK_NOTE, "flops_per_launch": flops,
                      "launch_ms": apply_ms,
-                     "timing": "200 launches replayed from a CUDA graph" if apply_graph is not None
+                     "timing": "200 launches replayed from a CUDA graph" if apply_graph
                                else "200 stream launches"},
         "clocks": clocks,
-    }
-    if not args.no_cpu_baseline:
+    })
+    if oracle is not None:
         try:
-            line["cpu_baseline"] = cpu_baseline_entry(run_oracle(reps=1, seed=args.seed))
+            line["cpu_baseline"] = cpu_baseline_entry(oracle_build_wait(*oracle))
         except Exception as e:  # the GPU number stands without it
             line["cpu_baseline"] = {"error": str(e)[:200]}
-    if not headline:
-        line["cpu_baseline_note"] = "cpu_baseline is measured on the headline workload's 128x128 sample"
-    if S64 is not S:
+        if not headline:
+            line["cpu_baseline_note"] = "cpu_baseline is measured on the 3-D 20-sphere workload's 32^3 sample"
+    if S64 is not S and S64 is not None:
         S64.close()
     S.close()
     return line
 
 
+def time_finest_apply(S, torch, stream, n_grid):
+    """Per-launch time of the finest-level FP64 operator apply (run once per CG iteration in
+    every form and three times per FP64 iteration), 200 launches replayed from a captured
+    CUDA graph so that host launch gaps do not enter (stream launches as the fallback)."""
+    xs = torch.randn(n_grid, dtype=torch.float64, device="cuda") * torch.as_tensor(
+        S.active_mask(), dtype=torch.float64, device="cuda")
+    ys = torch.empty_like(xs)
+    for _ in range(5):
+        S.apply_operator(xs, ys)
+    reps = 200
+    k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    graph = None
+    try:
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            for _ in range(reps):
+                S.apply_operator(xs, ys)
+        graph.replay()
+        torch.cuda.synchronize()
+    except Exception:
+        graph = None
+    torch.cuda.nvtx.range_push("finest_apply_timing")      # lets ncu select these launches
+    k0.record(stream)
+    if graph is not None:
+        graph.replay()
+    else:
+        for _ in range(reps):
+            S.apply_operator(xs, ys)
+    k1.record(stream)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
+    return k0.elapsed_time(k1) / reps, graph is not None
+
+
+def run_2d(args, lib, torch, timed_solves):
+    """The 2-D 512x512 quadratic B-spline workload (10 discs, 6 levels): FP64, mixed and the
+    coloured multiplicative smoother (same precision as the mixed form)."""
+    from synthetic import config_layout, preset
+    pr = preset("discs10_512_p2")
+    lay = config_layout(pr.layout, args.seed)
+    out = {"workload": workload_name(pr)}
+    t64 = None
+    for name, prec, sm in (("fp64", 0, 0), ("mixed", 1, 0), ("multiplicative_mixed", 1, 1)):
+        S = lib.Solver(pr.dim, lay.centers, lay.radii, pr.n, pr.degree, pr.levels, pr.depth, pr.bc,
+                       basis=pr.basis, lo=lay.lo, hi=lay.hi, precision=prec, smoother=sm)
+        units = S.level_info(S.L)["n_active"] * args.steps
+        t, res = timed_solves(S, args.steps, args.warmup, f"solve2d_{name}", rhs=S.rhs())
+        t64 = t if name == "fp64" else t64
+        out[name] = {"value": units / t, "unit": "DOF/s", "ms_per_step": 1e3 * t / args.steps,
+                     "iterations": res[0]["iterations"],
+                     "true_rel_residual": max(r["true_rel_residual"] for r in res),
+                     "gpu_launches_per_solve": int(res[0]["kernel_launches"]), "speedup_vs_fp64": t64 / t}
+        out["n_active"] = S.level_info(S.L)["n_active"]
+        S.close()
+    return out
+
+
 def run_reference(args, rank):
+    """The oracle on the CPU sample: one single-threaded solve process per host core, each
+    doing warmup + steps solves; value = DOFs of the timed solves of all processes over the
+    longest process's timed span."""
     if rank != 0:
         return None
-    o = run_oracle(reps=args.warmup + args.steps, seed=args.seed)
-    times = o["times"][args.warmup:]
-    value = o["n_active"] * len(times) / sum(times)
-    cb = cpu_baseline_entry({**o, "times": times})
-    cb["value"] = value
+    path = oracle_build_wait(*oracle_build_start(args.seed))
+    ncpu = os.cpu_count() or 1
+    outs = oracle_solves(path, ncpu, args.warmup + args.steps)
+    t = max(sum(o["times"][args.warmup:]) for o in outs)
+    n_act = outs[0]["n_active"]
+    value = ncpu * args.steps * n_act / t
+    from synthetic import preset
+    pr = preset(PRESET)
     return {"metric": METRIC, "value": value, "unit": "DOF/s", "n_gpus": args.gpus, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": WORKLOAD, "cpu_sample": f"{CPU_SAMPLE_N}x{CPU_SAMPLE_N} instance, "
-                       f"{CPU_SAMPLE_LEVELS} levels", "rtol": RTOL, "n_active": o["n_active"]},
-            "cpu_baseline": cb,
+            "config": {"workload": workload_name(pr), "cpu_sample": f"{CPU_SAMPLE['n']}^3 instance of the same "
+                       f"geometry, {CPU_SAMPLE['levels']} levels, depth {CPU_SAMPLE['depth']}", "rtol": RTOL,
+                       "n_active": n_act, "iterations": outs[0]["iterations"][0]},
+            "cpu_baseline": {"value": value, "unit": "DOF/s", "cores": ncpu, "kind": "oracle",
+                             "sample": sample_text(outs[0], ncpu, args.warmup + args.steps)
+                                       + f" (the first {args.warmup} of each untimed)",
+                             "host_cpus": ncpu, "oracle_build_s": outs[0]["build_s"]},
             "e2e": {"value": value, "unit": "DOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
@@ -563,12 +684,14 @@ def main():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default=PRESET, choices=WORKLOADS,
-                    help="the headline is the 512x512 quadratic B-spline workload; the others are the other "
-                         "configurations of the same study")
-    ap.add_argument("--learned", action="store_true",
-                    help="3-D workloads: also train the learned stage and time the FP64 solve with it")
-    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64", "hybrid"],
-                    help="V-cycle arithmetic of the timed solves (the FP64 path is timed beside it)")
+                    help="the headline is the 3-D 128^3 20-sphere quadratic B-spline workload; the others are "
+                         "the other configurations of the same study")
+    ap.add_argument("--no-learned", action="store_true",
+                    help="3-D workloads: skip training the learned stage and timing the FP64 solve with it")
+    ap.add_argument("--quick", action="store_true",
+                    help="time the chosen precision (and FP64) only: no other forms, 2-D workload or batch")
+    ap.add_argument("--precision", default="fp64", choices=["mixed", "fp64", "hybrid"],
+                    help="V-cycle arithmetic of the headline solves (the others are timed beside it)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -40,6 +40,9 @@ extern "C" {
 #define IMGM_ERR_NOT_SPD (-4)      /* a factorisation met a non-positive pivot */
 #define IMGM_ERR_BREAKDOWN (-5)    /* CG: p^T A p <= 0 or not finite */
 #define IMGM_MAX_ITER 1            /* CG stopped at maxit before reaching rtol (warning) */
+/* There is no timeout code: no kernel of this library waits on another grid, a flag set
+ * by the host or another device, so every launch ends by itself; a solve that does not
+ * converge ends at maxit with IMGM_MAX_ITER. */
 
 typedef struct imgm_handle imgm_handle;
 
@@ -99,7 +102,10 @@ typedef struct {
  * coarse rows R A R^T, Schwarz blocks with encapsulating supports and the Remark 3.3
  * rule, coarsest-level inverse) and uploads it to the current CUDA device.
  * Sec. 2 (discretisation), Sec. 3.3 (Eq. coarsening, Remark 3.1), Sec. 3.4 (blocks,
- * Remark 3.3).  Synchronous.  On success *out receives a new handle. */
+ * Remark 3.3).  Synchronous: it takes no stream, builds everything on the host (OpenMP),
+ * uploads it and times the setup-time autotuner's candidates on a stream of its own, and
+ * returns after the device has finished; the handle's tables are then read-only.  On
+ * success *out receives a new handle. */
 int imgm_setup(const imgm_geometry* geom, const imgm_config* cfg, imgm_handle** out);
 
 /* Frees everything the handle owns (device and host).  Waits for the device. */
@@ -234,8 +240,14 @@ typedef struct imgm_net imgm_net;
 
 /* A network with the given FP32 weights (host array, copied) and zero Adam state. */
 int imgm_net_create(const float* host_weights, imgm_net** out);
-/* Frees the network (waits for the device).  Detach it from every handle first. */
-void imgm_net_destroy(imgm_net* net);
+/* Frees the network (waits for the device) and returns IMGM_OK; NULL is a no-op.
+ * A network counts its attachments: every handle it is attached to (imgm_set_net) and
+ * every batch created while one of its handles held it (the batch's recorded solves read
+ * its weights, whatever imgm_set_net does to the handle afterwards).  While that count is
+ * above zero the call frees nothing and returns IMGM_ERR_INVALID (message in
+ * imgm_last_error(NULL)): detach it from its handles (or destroy them) and destroy those
+ * batches first. */
+int imgm_net_destroy(imgm_net* net);
 /* Copies the FP32 master weights / the gradient accumulator to the host (waits). */
 int imgm_net_get_weights(const imgm_net* net, float* host_weights);
 int imgm_net_get_grads(const imgm_net* net, float* host_grads);
@@ -260,7 +272,10 @@ int imgm_net_adam_step(imgm_net* net, float lr, float beta1, float beta2, float 
 /* Attaches net to h's solves (NULL detaches): imgm_pcg_solve then runs the stage after
  * every V-cycle.  The network must outlive the attachment.  IMGM_ERR_UNSUPPORTED for a
  * 2-D problem or precision 1 (the stage follows an FP64 V-cycle output).  Rebuilds the
- * solve graph on the next solve; batches created earlier keep the plain V-cycle. */
+ * solve graph on the next solve.  A batch keeps the stage as it was when the batch was
+ * created: batches created before the call keep their V-cycle (with or without a
+ * network), and a batch created while a network was attached runs that network until
+ * it is destroyed (and holds one attachment of it; see imgm_net_destroy). */
 int imgm_set_net(imgm_handle* h, imgm_net* net);
 
 /* One stage with the attached network: dev_z (in: B dev_r, out: the corrected value);

@@ -334,3 +334,77 @@ class Discretization:
             e0 += np.sum(vw * (u(vp) - uh) ** 2)
             e1 += np.sum(vw * np.sum((grad_u(vp) - guh) ** 2, axis=1))
         return math.sqrt(e0), math.sqrt(e1)
+
+
+class LocalRows(Discretization):
+    """Rows of the immersed system assembled from their own support elements only, for
+    grids too large for the global assembly above (test infrastructure, like the rest of
+    this package).
+
+    Same discretisation as Discretization (Sec. 2: the element systems, the activity rule
+    and the box-face condition are those methods, unchanged); what differs is that cut
+    elements are integrated on demand.  No global cut-volume pass is made, so a row's
+    activity and its entries come from the elements of its own support:
+
+    * row I is active iff it is not a box-face function (when the box faces carry u = 0)
+      and some element of its support has positive measure in Omega_h;
+    * a column J enters through an element K of supp(I) with positive measure; an
+      inactive J (all of its support elements of zero measure) never meets such a K, so
+      its entry is not formed at all, as in the global assembly, except for box-face
+      functions, which are excluded explicitly.
+    """
+
+    def __init__(self, geom, basis_kind: int, p: int, n: int, depth: int, bc: int = NITSCHE,
+                 problem=Manufactured):
+        self.geom, self.dim = geom, geom.dim
+        self.kind, self.p, self.n, self.depth, self.bc = int(basis_kind), int(p), int(n), int(depth), int(bc)
+        self.problem = problem
+        self.tb = TensorBasis(make_basis(basis_kind, n, p, geom.lo, geom.hi), geom.dim)
+        self.h = self.tb.h
+        self.beta_penalty = 2.0 / self.h
+        self._batch = 8192
+        self._classify()
+        self._cut_cache = {}
+
+    def on_box(self, J: int) -> bool:
+        if not self.geom.box_dirichlet:
+            return False
+        multi = np.unravel_index(int(J), (self.tb.m,) * self.dim, order="F")
+        return any(k == 0 or k == self.tb.m - 1 for k in multi)
+
+    def element_active(self, E: int) -> bool:
+        c = self.elem_class[E]
+        if c == FULL:
+            return True
+        if c == EMPTY:
+            return False
+        return self.cut_rule(int(E))[1].sum() > 0
+
+    def row_active(self, I: int) -> bool:
+        return (not self.on_box(I)) and any(self.element_active(E) for E in self.tb.support_elems(int(I)))
+
+    def assemble_rows(self, rows_full: np.ndarray):
+        """Rows of A (full-grid column indexing) and entries of b: row -> (cols, vals, b_row);
+        an inactive row comes back empty."""
+        out = {}
+        cache = {}
+        for I in rows_full:
+            I = int(I)
+            acc: dict[int, float] = {}
+            bI = 0.0
+            if self.row_active(I):
+                for E in self.tb.support_elems(I):
+                    if not self.element_active(E):
+                        continue
+                    if E not in cache:
+                        cache[E] = self.element_system(E)[:2]
+                    AK, bK = cache[E]
+                    dofs = self.tb.elem_dofs(E)
+                    a = int(np.flatnonzero(dofs == I)[0])
+                    bI += bK[a]
+                    for bi, J in enumerate(dofs):
+                        if not self.on_box(int(J)):
+                            acc[int(J)] = acc.get(int(J), 0.0) + AK[a, bi]
+            cols = np.array(sorted(acc), dtype=np.int64)
+            out[I] = (cols, np.array([acc[j] for j in cols]), bI)
+        return out

@@ -83,7 +83,7 @@ _SIGS = {
     "imgm_batch_solve": (_I, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), _D, _I, ctypes.POINTER(Result), _P]),
     "imgm_batch_destroy": (None, [_P]),
     "imgm_net_create": (_I, [_P, ctypes.POINTER(_P)]),
-    "imgm_net_destroy": (None, [_P]),
+    "imgm_net_destroy": (ctypes.c_int, [_P]),
     "imgm_net_get_weights": (_I, [_P, _P]),
     "imgm_net_get_grads": (_I, [_P, _P]),
     "imgm_net_forward": (_I, [_P, _I, _I, _I, _P, _P, _P, _P]),
@@ -427,8 +427,9 @@ class Net:
         return rc
 
     def close(self):
+        """Frees the network; raises ImgmError while a handle or a batch still holds it."""
         if getattr(self, "_n", None):
-            _lib.imgm_net_destroy(self._n)
+            self._check(_lib.imgm_net_destroy(self._n))
             self._n = None
 
     def __del__(self):

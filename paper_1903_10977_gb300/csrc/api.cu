@@ -90,6 +90,7 @@ struct imgm_net {
     float *w = nullptr, *g = nullptr, *m = nullptr, *v = nullptr;
     uint16_t *wb = nullptr, *wbt = nullptr;
     int64_t t = 0;                 // Adam steps taken
+    int attached = 0;              // handles holding it plus batches whose graph recorded it
     imgm::NetWorkspace ws;
     ~imgm_net() {
         for (void* p : {(void*)w, (void*)g, (void*)m, (void*)v, (void*)wb, (void*)wbt})
@@ -165,6 +166,7 @@ struct imgm_handle {
         return cudaMemcpy(*p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice);
     }
     ~imgm_handle() {
+        if (net) net->attached -= 1;
         if (exec) cudaGraphExecDestroy(exec);
         if (capture) cudaStreamDestroy(capture);
         if (graph) cudaGraphDestroy(graph);
@@ -1479,8 +1481,10 @@ struct imgm_batch {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     std::vector<int64_t> kernels;        // per solve: start, body, finish kernel counts
+    std::vector<imgm_net*> nets;         // networks the recorded solves run (one count each)
     std::string err;
     ~imgm_batch() {
+        for (imgm_net* n : nets) n->attached -= 1;
         if (exec) cudaGraphExecDestroy(exec);
         if (graph) cudaGraphDestroy(graph);
         for (cudaEvent_t e : events) cudaEventDestroy(e);
@@ -1545,6 +1549,13 @@ int imgm_batch_create(imgm_handle* const* hs, int n, imgm_batch** out) {
         return batch_fail(nullptr, IMGM_ERR_CUDA, std::string("batch graph: ") + cudaGetErrorString(e));
     }
     b->graph = g;
+    // the recorded solves read the attached networks' weights: each counts as an attachment
+    // until the batch is destroyed, so such a network cannot be freed under the graph
+    for (int k = 0; k < n; ++k)
+        if (hs[k]->net) {
+            hs[k]->net->attached += 1;
+            b->nets.push_back(hs[k]->net);
+        }
     *out = b.release();
     return IMGM_OK;
 }
@@ -1659,10 +1670,13 @@ int imgm_net_create(const float* host_weights, imgm_net** out) {
     return IMGM_OK;
 }
 
-void imgm_net_destroy(imgm_net* net) {
-    if (!net) return;
+int imgm_net_destroy(imgm_net* net) {
+    if (!net) return IMGM_OK;
+    if (net->attached > 0)
+        return net_fail(IMGM_ERR_INVALID, "the network is still attached to a handle or recorded in a batch");
     cudaDeviceSynchronize();
     delete net;
+    return IMGM_OK;
 }
 
 int imgm_net_get_weights(const imgm_net* net, float* host_weights) {
@@ -1737,6 +1751,8 @@ int imgm_set_net(imgm_handle* h, imgm_net* net) {
     h->exec = nullptr;
     h->graph = nullptr;
     h->graph_failed = false;
+    if (h->net) h->net->attached -= 1;
+    if (net) net->attached += 1;
     h->net = net;
     return IMGM_OK;
 }

@@ -280,3 +280,25 @@ def test_set_net_rejects_2d_and_fp32_vcycle():
     S2.close()
     S3.close()
     net.close()
+
+
+def test_net_destroy_waits_for_handles_and_batches(problem):
+    """A network cannot be freed while a handle holds it or a batch recorded it: the
+    batch's graph keeps running the stage with the weights it captured, so the order
+    set_net -> batch -> set_net(None) -> destroy is refused until the batch is gone."""
+    pr, lay, d, H, S = problem
+    net = lib.Net(initial_weights(3))
+    S.set_net(net)
+    with pytest.raises(lib.ImgmError):
+        net.close()                      # attached to S
+    batch = lib.Batch([S])               # records S's solve with the stage
+    S.set_net(None)
+    with pytest.raises(lib.ImgmError):
+        net.close()                      # still recorded in the batch
+    b = S.rhs()
+    x = torch.zeros_like(b)
+    _, res = batch.solve([b], [x], rtol=1e-8, maxit=1000)
+    assert res[0]["status"] == lib.IMGM_OK
+    batch.close()
+    net.close()
+    assert net._n is None

@@ -178,3 +178,32 @@ def test_row_assembly_matches_global_assembly():
         scale = np.abs(ref).max()
         assert np.abs(row - ref).max() <= 1e-13 * scale
         assert abs(bI - d.b[pos[I]]) <= 1e-13 * np.abs(d.b).max()
+
+
+@pytest.mark.parametrize("name,ov", [("disc1_32_p2", {}), ("spheres20_128_p2", dict(n=8, levels=2, depth=1))])
+def test_local_rows_equal_global_assembly(name, ov):
+    """LocalRows (cut elements integrated on demand, activity from each row's own support)
+    gives exactly the rows and right-hand side entries of the global assembly, including
+    inactive rows (empty) and box-face rows (excluded)."""
+    from oracle.discretize import LocalRows
+    from parity_utils import layout_for
+    pr, lay = layout_for(name, **ov)
+    geom = G.Balls(lay.centers, lay.radii, lay.lo, lay.hi)
+    d = Discretization(geom, pr.basis, pr.degree, pr.n, pr.depth, pr.bc)
+    loc = LocalRows(geom, pr.basis, pr.degree, pr.n, pr.depth, pr.bc)
+    rng = np.random.default_rng(5)
+    rows = np.unique(np.concatenate([rng.choice(d.tb.n_funcs, 60, replace=False),
+                                     d.active[rng.choice(d.n_active, 60, replace=False)]]))
+    got = loc.assemble_rows(rows)
+    Af = d.A.tocsr()
+    for I in rows:
+        cols, vals, bI = got[int(I)]
+        a = d.full_to_active[I]
+        if a < 0:
+            assert cols.size == 0 and bI == 0.0
+            continue
+        ref = Af[a]
+        np.testing.assert_array_equal(cols, np.sort(d.active[ref.indices]))
+        order = np.argsort(d.active[ref.indices])
+        np.testing.assert_allclose(vals, ref.data[order], rtol=0, atol=1e-14 * np.abs(ref.data).max())
+        assert abs(bI - d.b[a]) <= 1e-14 * np.abs(d.b).max()
