@@ -278,6 +278,19 @@ int imgm_net_adam_step(imgm_net* net, float lr, float beta1, float beta2, float 
  * it is destroyed (and holds one attachment of it; see imgm_net_destroy). */
 int imgm_set_net(imgm_handle* h, imgm_net* net);
 
+/* Truncated flexible CG for h's solves, FCG(m) (Notay, "Flexible conjugate gradients",
+ * SIAM J. Sci. Comput. 22, 2000): each new direction is the preconditioned residual z
+ * A-orthogonalised against the last m directions, p = z - sum_j (z^T A p_j)/(p_j^T A p_j) p_j,
+ * and alpha = (r^T p)/(p^T A p).  For a fixed SPD preconditioner it is plain PCG up to
+ * rounding; with the learned stage (a preconditioner that varies from step to step) the
+ * m stored directions keep more of the Krylov acceleration than the one-direction
+ * Polak-Ribiere form.  m = 0 returns to the default (PCG, or Polak-Ribiere with a network
+ * or an FP32 V-cycle); 1 <= m <= 8.  Allocates 2 m n_grid doubles on the first call with a
+ * larger m (synchronous; call it outside stream capture).  Errors: IMGM_ERR_INVALID (m out
+ * of range), IMGM_ERR_UNSUPPORTED (precision 1: its V-cycle output is FP32), IMGM_ERR_CUDA.
+ * The paper has no counterpart: its CG takes the fixed V-cycle of Algorithm 1. */
+int imgm_set_fcg(imgm_handle* h, int m);
+
 /* One stage with the attached network: dev_z (in: B dev_r, out: the corrected value);
  * dev_omega (device double, may be NULL) receives omega. */
 int imgm_learned_stage(imgm_handle* h, const double* dev_r, double* dev_z, double* dev_omega, void* stream);

@@ -84,6 +84,7 @@ _SIGS = {
     "imgm_batch_destroy": (None, [_P]),
     "imgm_net_create": (_I, [_P, ctypes.POINTER(_P)]),
     "imgm_net_destroy": (ctypes.c_int, [_P]),
+    "imgm_set_fcg": (ctypes.c_int, [_H, ctypes.c_int]),
     "imgm_net_get_weights": (_I, [_P, _P]),
     "imgm_net_get_grads": (_I, [_P, _P]),
     "imgm_net_forward": (_I, [_P, _I, _I, _I, _P, _P, _P, _P]),
@@ -255,6 +256,10 @@ class Solver:
         """Attach a network to this context's solves (None detaches); see imgm_set_net."""
         self._check(_lib.imgm_set_net(self._h, net._n if net is not None else None))
         self._net = net               # keeps the network alive while attached
+
+    def set_fcg(self, m: int):
+        """Truncated flexible CG with m stored directions for the following solves (0: off)."""
+        self._check(_lib.imgm_set_fcg(self._h, int(m)))
 
     def learned_stage(self, r, z, omega=None, stream=None):
         """z <- z + omega N(r - A z) in place with the attached network (z = B r on entry)."""

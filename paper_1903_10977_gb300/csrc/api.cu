@@ -140,6 +140,9 @@ struct imgm_handle {
     // learned stage (dim 3, FP64 V-cycle output): the attached network, its activations on
     // the finest grid, the stage's vectors (r1 = r - A z, c = N(r1), A c), the active mask
     imgm_net* net = nullptr;
+    // truncated flexible CG (imgm_set_fcg): m stored directions and their images, m x N each
+    int fcg_m = 0, fcg_cap = 0;
+    double *fcg_P = nullptr, *fcg_Q = nullptr;
     imgm::NetWorkspace lws;
     double *l_r1 = nullptr, *l_c = nullptr, *l_q = nullptr;
     uint8_t* l_mask = nullptr;
@@ -453,6 +456,15 @@ cudaError_t enqueue_iteration(imgm_handle* h, cudaStream_t s) {
                                              h->gamma_diag, h->partial, h->st, h->hist, s)) != cudaSuccess)
         return e;
     if ((e = enqueue_vcycle<double>(h, h->cr, h->cz, done, s)) != cudaSuccess) return e;
+    if (h->fcg_m > 0) {
+        // FCG(m): the new direction is z (after the learned stage, if any) A-orthogonalised
+        // against the last m directions
+        if (h->net && (e = enqueue_learned(h, h->cr, h->cz, nullptr, s)) != cudaSuccess) return e;
+        if ((e = imgm::launch_fcg_push_dots(N, h->fcg_m, h->cz, h->cp, h->cq, h->fcg_P, h->fcg_Q, h->partial, h->st,
+                                            s)) != cudaSuccess)
+            return e;
+        return imgm::launch_fcg_dir(N, h->fcg_m, h->cz, h->cr, h->cp, h->fcg_P, h->partial, h->st, s);
+    }
     if (h->net) {
         // the learned stage makes the preconditioner vary: Polak-Ribiere beta from A p (cq)
         if ((e = enqueue_learned(h, h->cr, h->cz, nullptr, s)) != cudaSuccess) return e;
@@ -768,6 +780,15 @@ int alloc_level_vectors(imgm_handle* h, LevelDev& dst) {
     CK(cudaMemset(ctr, 0, 2 * sizeof(unsigned int)), "memset tile counter");
     dst.d.tile_ctr = ctr;
     dst.fd.tile_ctr = ctr;
+    // scratch of the sum-factorised transfers to the next coarser level (3-D levels whose
+    // transfers take the passes; the row kernels serve the small ones)
+    if (dst.d.dim == 3 && dst.d.m >= 34) {
+        const int64_t mf = dst.d.m, mc = (dst.d.m - dst.d.p) / 2 + dst.d.p;
+        CK(h->alloc(&dst.d.xs1, mf * mf * mc), "alloc transfer scratch");
+        CK(h->alloc(&dst.d.xs2, mf * mc * mc), "alloc transfer scratch");
+        dst.fd.xs1 = dst.d.xs1;
+        dst.fd.xs2 = dst.d.xs2;
+    }
     CK(h->alloc(&dst.x, N), "alloc x");
     CK(h->alloc(&dst.r, N), "alloc r");
     CK(h->alloc(&dst.t, N), "alloc t");
@@ -811,7 +832,7 @@ int alloc_context(imgm_handle* h) {
         CK(h->alloc(&h->czp, N), "alloc");
         CK(cudaMemset(h->czp, 0, N * sizeof(double)), "memset");
     }
-    CK(h->alloc(&h->partial, 2 * (size_t)imgm::reduction_blocks()), "alloc");
+    CK(h->alloc(&h->partial, (size_t)imgm::FCG_MAX * imgm::reduction_blocks()), "alloc");
     CK(h->alloc(&h->st, 1), "alloc");
     CK(cudaMemset(h->st, 0, sizeof(PcgState)), "memset");
     CK(h->alloc(&h->partial_aux, 2 * (size_t)imgm::reduction_blocks()), "alloc");
@@ -841,6 +862,9 @@ int upload_level(imgm_handle* h, const imgm::LevelData& src, LevelDev& dst, int 
     int32_t *bi, *rf, *tf;
     CK(h->upload(&ri, src.rowinfo), "upload rowinfo");
     CK(h->upload(&bc, src.band_coef), "upload stored rows");
+    int32_t* brow;
+    CK(h->upload(&brow, src.band_rows), "upload stored row ids");
+    d.band_row = brow;
     CK(h->upload(&k1, src.K1), "upload K1");
     CK(h->upload(&m1, src.M1), "upload M1");
     CK(h->upload(&dv, src.dinv.empty() ? std::vector<double>(src.N, 0.0) : src.dinv), "upload dinv");
@@ -848,6 +872,16 @@ int upload_level(imgm_handle* h, const imgm::LevelData& src, LevelDev& dst, int 
     CK(h->upload(&bi, src.blk_idx), "upload block idx");
     CK(h->upload(&bvp, src.blk_vptr.empty() ? std::vector<int64_t>(1, 0) : src.blk_vptr), "upload block vptr");
     CK(h->upload(&bv, src.blk_val), "upload block values");
+    int32_t* bof;
+    {
+        // the block of every (block, function) pair: one thread per pair applies A_j^{-1}
+        std::vector<int32_t> of(src.blk_idx.size());
+        for (size_t b = 0; b + 1 < src.blk_ptr.size(); ++b)
+            for (int64_t q = src.blk_ptr[b]; q < src.blk_ptr[b + 1]; ++q) of[(size_t)q] = (int32_t)b;
+        CK(h->upload(&bof, of), "upload block of pair");
+    }
+    d.blk_of = bof;
+    d.npair = (int64_t)src.blk_idx.size();
     CK(h->upload(&rf, src.r_first), "upload restriction");
     CK(h->upload(&rw, src.r_w), "upload restriction");
     CK(h->upload(&tf, src.t_first), "upload prolongation");
@@ -877,9 +911,12 @@ int upload_level(imgm_handle* h, const imgm::LevelData& src, LevelDev& dst, int 
         f.max_block = d.max_block;
         f.TW = d.TW;
         f.rowinfo = d.rowinfo;
+        f.band_row = d.band_row;
         f.blk_ptr = d.blk_ptr;
         f.blk_idx = d.blk_idx;
         f.blk_vptr = d.blk_vptr;
+        f.blk_of = d.blk_of;
+        f.npair = d.npair;
         f.r_first = d.r_first;
         f.t_first = d.t_first;
         float *bcf, *k1f, *m1f, *dvf, *bvf, *rwf, *twf, *sf, *df;
@@ -1754,6 +1791,28 @@ int imgm_set_net(imgm_handle* h, imgm_net* net) {
     if (h->net) h->net->attached -= 1;
     if (net) net->attached += 1;
     h->net = net;
+    return IMGM_OK;
+}
+
+int imgm_set_fcg(imgm_handle* h, int m) {
+    int c = check_level(h, h ? h->L : 0, 1);
+    if (c) return c;
+    if (m < 0 || m > imgm::FCG_MAX) return fail(h, IMGM_ERR_INVALID, "FCG(m) needs 0 <= m <= 8");
+    if (m > 0 && h->precision == 1)
+        return fail(h, IMGM_ERR_UNSUPPORTED, "FCG(m) takes the FP64 V-cycle output (precision 0 or 2)");
+    CK(cudaDeviceSynchronize(), "sync");
+    if (m > h->fcg_cap) {
+        const int64_t N = h->lv[h->L - 1].d.N;
+        CK(h->alloc(&h->fcg_P, (size_t)m * N), "alloc FCG directions");
+        CK(h->alloc(&h->fcg_Q, (size_t)m * N), "alloc FCG directions");
+        h->fcg_cap = m;
+    }
+    if (h->exec) cudaGraphExecDestroy(h->exec);
+    if (h->graph) cudaGraphDestroy(h->graph);
+    h->exec = nullptr;
+    h->graph = nullptr;
+    h->graph_failed = false;
+    h->fcg_m = m;
     return IMGM_OK;
 }
 

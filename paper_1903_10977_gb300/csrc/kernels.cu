@@ -403,143 +403,203 @@ __global__ void __launch_bounds__(TPB) k_apply_tile2d(DevLevelT<T> L, const T* _
 }
 
 // ---------------------------------------------------------------------------------
-// 3-D operator apply on TX3 x TY3 x TZ3 tiles with sum factorisation.  The tile and its
-// p-halo are staged in shared memory; tensor rows then cost
-//   u_M = M_z x, u_K = K_z x          over the (TX3+2p) x (TY3+2p) x TZ3 slab   (2(2p+1) FMA)
-//   v_1 = M_y u_M, v_2 = K_y u_M + M_y u_K   over (TX3+2p) x TY3 x TZ3            (3(2p+1) FMA)
-//   y = K_x v_1 + M_x v_2              on the outputs                           (2(2p+1) FMA)
-// about 50 FMA per row for p = 2 instead of ~250 for the row-by-row sum.  Stored rows read
-// their (2p+1)^3 coefficients and take x from the staged tile.  Modes as k_apply_tile2d.
-constexpr int TX3 = 32, TY3 = 4, TZ3 = 2;
+// 3-D operator apply by z-marching warps.  A warp owns a column of outputs: 32 - 2P
+// consecutive x positions (its lanes, plus P halo lanes on each side), YT (1 or 2) consecutive
+// y rows and a chunk of z planes, and walks the input planes z' of that chunk (with a
+// P-plane halo at each end).  For each plane every lane loads its x-column segment of
+// YT + 2P values and forms, for its own YT rows,
+//   m = M_y v, k = K_y v                              (along y, in registers)
+//   a = M_x m, b = M_x k + K_x m                       (along x, neighbours by shuffles)
+// which are the plane's (M_y M_x) and (K_y M_x + M_y K_x) images; an output at plane z then
+// collects  y_z = sum_o K_z[z][o] a(z - P + o) + M_z[z][o] b(z - P + o)  in a ring of
+// 2P + 1 register accumulators, and is written when its last plane has passed.  That is
+// 2(2P+1) + 3(2P+1) FMA per row in the plane (times 32/(32-2P) for the halo lanes) plus
+// 2(2P+1) along z: about 39 FMA per row for P = 2, with no shared memory and no block
+// barrier.  Stored rows are not formed here: the same launch runs them as tasks of 32
+// stored rows (one per lane, (2P+1)^3 coefficients each), so no warp of the tensor tasks
+// waits on a lane with a stored row.  Warps draw tasks (tensor tasks first) from the
+// level's counter; the last warp to finish re-arms it.  Modes as k_apply_tile2d.
+// output rows (y) per lane: a template parameter of the kernel (1 or 2), chosen per level
 
-template <typename T, int P, int MODE, bool DOT>
-__global__ void __launch_bounds__(TPB) k_apply_tile3d(DevLevelT<T> L, const T* __restrict__ x, const T* rin, T* out,
-                                                      T* __restrict__ xs, T gamma, const int* done, double* partial,
-                                                      PcgState* st) {
+struct ZmShape {
+    int sx, sy, sz;                      // tensor tasks along x (strips), y (segments), z (chunks)
+    int zc;                              // planes per chunk
+    unsigned int ntensor, ntotal;        // tensor tasks; all tasks (tensor + stored)
+};
+
+template <typename T, int P, int MODE, bool DOT, int YT>
+__global__ void __launch_bounds__(TPB) k_apply_zm3d(DevLevelT<T> L, const T* __restrict__ x, const T* rin, T* out,
+                                                    T* __restrict__ xs, T gamma, const int* done, double* partial,
+                                                    PcgState* st, ZmShape sh) {
     pdl_begin();
-    constexpr int W = 2 * P + 1;
-    constexpr int SX = TX3 + 2 * P, SY = TY3 + 2 * P, SZ = TZ3 + 2 * P;
-    constexpr bool SC = sizeof(T) == 4;              // FP32 path: Jacobi-scaled variables
-    static_assert(TX3 * TY3 * TZ3 == TPB, "one output per thread");
-    __shared__ T sx[SZ][SY][SX];
-    __shared__ T ss[SC ? SZ : 1][SC ? SY : 1][SC ? SX : 1];
-    __shared__ T uM[TZ3][SY][SX], uK[TZ3][SY][SX];
-    __shared__ T v1[TZ3][TY3][SX], v2[TZ3][TY3][SX];
-    __shared__ T tKx[TX3][W], tMx[TX3][W], tKy[TY3][W], tMy[TY3][W], tKz[TZ3][W], tMz[TZ3][W];
-    __shared__ int s_tile;
     if (done && *done) return;
+    constexpr int W = 2 * P + 1, XS = 32 - 2 * P, NV = YT + 2 * P;
+    constexpr bool SC = sizeof(T) == 4;              // FP32 path: Jacobi-scaled variables
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
     const int m = L.m;
     const int64_t mm = (int64_t)m * m;
-    const int tiles_x = (m + TX3 - 1) / TX3, tiles_y = (m + TY3 - 1) / TY3, tiles_z = (m + TZ3 - 1) / TZ3;
-    const int ntiles = tiles_x * tiles_y * tiles_z;
-    const bool dyn = sizeof(T) == 8 && MODE == APPLY && (int)gridDim.x < ntiles;
     double acc = 0.0;
-    for (int tb = blockIdx.x;; tb += gridDim.x) {
-        __syncthreads();
-        if (dyn) {
-            if (threadIdx.x == 0) s_tile = (int)atomicAdd(&L.tile_ctr[0], 1u);
-            __syncthreads();
-        }
-        const int tile = dyn ? s_tile : tb;
-        if (tile >= ntiles) break;
-        const int x0 = (tile % tiles_x) * TX3, y0 = ((tile / tiles_x) % tiles_y) * TY3,
-                  z0 = (tile / (tiles_x * tiles_y)) * TZ3;
-        for (int k = threadIdx.x; k < SX * SY * SZ; k += TPB) {
-            const int lz = k / (SX * SY), ly = (k / SX) % SY, lx = k % SX;
-            const int gx = x0 + lx - P, gy = y0 + ly - P, gz = z0 + lz - P;
-            const bool in = (unsigned)gx < (unsigned)m && (unsigned)gy < (unsigned)m && (unsigned)gz < (unsigned)m;
-            const int64_t g = (int64_t)gz * mm + (int64_t)gy * m + gx;
-            sx[lz][ly][lx] = in ? x[g] : T(0);
-            if (SC) ss[SC ? lz : 0][SC ? ly : 0][SC ? lx : 0] = in ? ro(L.s + g) : T(0);
-        }
-        for (int k = threadIdx.x; k < TX3 * W; k += TPB) {
-            const int lx = k / W, o = k % W, gx = x0 + lx;
-            tKx[lx][o] = gx < m ? ro(L.K1 + (int64_t)gx * W + o) : T(0);
-            tMx[lx][o] = gx < m ? ro(L.M1 + (int64_t)gx * W + o) : T(0);
-        }
-        for (int k = threadIdx.x; k < TY3 * W; k += TPB) {
-            const int ly = k / W, o = k % W, gy = y0 + ly;
-            tKy[ly][o] = gy < m ? ro(L.K1 + (int64_t)gy * W + o) : T(0);
-            tMy[ly][o] = gy < m ? ro(L.M1 + (int64_t)gy * W + o) : T(0);
-        }
-        for (int k = threadIdx.x; k < TZ3 * W; k += TPB) {
-            const int lz = k / W, o = k % W, gz = z0 + lz;
-            tKz[lz][o] = gz < m ? ro(L.K1 + (int64_t)gz * W + o) : T(0);
-            tMz[lz][o] = gz < m ? ro(L.M1 + (int64_t)gz * W + o) : T(0);
-        }
-        // this thread's output
-        const int olx = threadIdx.x % TX3, oly = (threadIdx.x / TX3) % TY3, olz = threadIdx.x / (TX3 * TY3);
-        const int ogx = x0 + olx, ogy = y0 + oly, ogz = z0 + olz;
-        const bool oin = ogx < m && ogy < m && ogz < m;
-        const int64_t oi = (int64_t)ogz * mm + (int64_t)ogy * m + ogx;
-        const int ri = oin ? ro(L.rowinfo + oi) : -3;
-        const T rv = (MODE != APPLY && oin) ? rin[oi] : T(0);
-        const T dv = (MODE == RESID_SMOOTH && oin) ? ro(L.dinv + oi) : T(0);
-        const T xv = (MODE == RESID_SMOOTH && oin) ? xs[oi] : T(0);
-        __syncthreads();
-        // along z, over the x-y halo slab of the output planes
-        for (int k = threadIdx.x; k < TZ3 * SY * SX; k += TPB) {
-            const int lz = k / (SY * SX), ly = (k / SX) % SY, lx = k % SX;
-            T a = T(0), b = T(0);
+    for (;;) {
+        unsigned int t = 0;
+        if (lane == 0) t = atomicAdd(&L.tile_ctr[0], 1u);
+        t = __shfl_sync(FULL, t, 0);
+        if (t >= sh.ntotal) break;
+        if (t < sh.ntensor) {
+            // ---------------- tensor task: strip sxi, rows y0.., planes zc0..zend-1
+            const int sxi = (int)(t % (unsigned)sh.sx);
+            const int syi = (int)((t / (unsigned)sh.sx) % (unsigned)sh.sy);
+            const int szi = (int)(t / ((unsigned)sh.sx * (unsigned)sh.sy));
+            const int gx = sxi * XS - P + lane;
+            const int y0 = syi * YT;
+            const int zc0 = szi * sh.zc;
+            const int zend = min(zc0 + sh.zc, m);
+            const bool xin = (unsigned)gx < (unsigned)m;
+            const bool own = lane >= P && lane < 32 - P && xin;      // this lane writes outputs
+            T kx[W], mx[W];
 #pragma unroll
             for (int o = 0; o < W; ++o) {
-                const T xq = SC ? sx[lz + o][ly][lx] * ss[SC ? lz + o : 0][SC ? ly : 0][SC ? lx : 0] : sx[lz + o][ly][lx];
-                a = fmaT(tMz[lz][o], xq, a);
-                b = fmaT(tKz[lz][o], xq, b);
+                kx[o] = xin ? ro(L.K1 + (int64_t)gx * W + o) : T(0);
+                mx[o] = xin ? ro(L.M1 + (int64_t)gx * W + o) : T(0);
             }
-            uM[lz][ly][lx] = a;
-            uK[lz][ly][lx] = b;
-        }
-        __syncthreads();
-        // along y
-        for (int k = threadIdx.x; k < TZ3 * TY3 * SX; k += TPB) {
-            const int lz = k / (TY3 * SX), ly = (k / SX) % TY3, lx = k % SX;
-            T a = T(0), b = T(0);
+            T ring[YT][W];
 #pragma unroll
-            for (int o = 0; o < W; ++o) {
-                a = fmaT(tMy[ly][o], uM[lz][ly + o][lx], a);
-                b = fmaT(tKy[ly][o], uM[lz][ly + o][lx], b);
-                b = fmaT(tMy[ly][o], uK[lz][ly + o][lx], b);
-            }
-            v1[lz][ly][lx] = a;
-            v2[lz][ly][lx] = b;
-        }
-        __syncthreads();
-        if (ri != -3) {
-            T y = T(0);
-            if (ri == -1) {
+            for (int j = 0; j < YT; ++j)
 #pragma unroll
-                for (int o = 0; o < W; ++o) {
-                    y = fmaT(tKx[olx][o], v1[olz][oly][olx + o], y);
-                    y = fmaT(tMx[olx][o], v2[olz][oly][olx + o], y);
+                for (int q = 0; q < W; ++q) ring[j][q] = T(0);
+            const int nplanes = (zend - zc0) + 2 * P;
+            // the column segment of input plane zp (zero outside the grid)
+            auto load_plane = [&](int zp, T* v) {
+                const bool zin = (unsigned)zp < (unsigned)m;
+#pragma unroll
+                for (int i = 0; i < NV; ++i) {
+                    const int gy = y0 - P + i;
+                    const bool in = zin && xin && (unsigned)gy < (unsigned)m;
+                    const int64_t g = (int64_t)zp * mm + (int64_t)gy * m + gx;
+                    v[i] = in ? (SC ? x[g] * ro(L.s + g) : x[g]) : T(0);
                 }
-                if (SC) y *= ss[SC ? olz + P : 0][SC ? oly + P : 0][SC ? olx + P : 0];
-            } else if (ri >= 0) {
-                const T* __restrict__ c = L.band_coef + ri;
+            };
+            T v[NV];
+            load_plane(zc0 - P, v);
+            for (int base = 0; base < nplanes; base += W) {
+#pragma unroll
+                for (int u = 0; u < W; ++u) {
+                    const int k = base + u;
+                    if (k >= nplanes) break;
+                    const int zp = zc0 - P + k;                      // input plane
+                    // the next plane's loads go out before this plane's arithmetic
+                    T vn[NV];
+                    if (k + 1 < nplanes) load_plane(zp + 1, vn);
+                    T a[YT], b[YT];
+#pragma unroll
+                    for (int j = 0; j < YT; ++j) {
+                        const int gy = y0 + j;
+                        T my = T(0), ky = T(0);
+                        if (gy < m) {
+#pragma unroll
+                            for (int o = 0; o < W; ++o) {
+                                my = fmaT(ro(L.M1 + (int64_t)gy * W + o), v[j + o], my);
+                                ky = fmaT(ro(L.K1 + (int64_t)gy * W + o), v[j + o], ky);
+                            }
+                        }
+                        T aa = T(0), bb = T(0);
+#pragma unroll
+                        for (int o = 0; o < W; ++o) {
+                            const T mo = __shfl_sync(FULL, my, (lane - P + o) & 31);
+                            const T ko = __shfl_sync(FULL, ky, (lane - P + o) & 31);
+                            aa = fmaT(mx[o], mo, aa);
+                            bb = fmaT(mx[o], ko, bb);
+                            bb = fmaT(kx[o], mo, bb);
+                        }
+                        a[j] = aa;
+                        b[j] = bb;
+                    }
+                    // outputs z = zp - P + jz receive K_z[z][2P - jz] a + M_z[z][2P - jz] b;
+                    // output z keeps ring slot (z - zc0 + 2P + 1) mod W, here (u + 1 + jz) mod W
+                    // (base is a multiple of W)
+#pragma unroll
+                    for (int jz = 0; jz < W; ++jz) {
+                        const int z = zp - P + jz;
+                        if ((unsigned)z < (unsigned)m) {
+                            const T kz = ro(L.K1 + (int64_t)z * W + (2 * P - jz));
+                            const T mz = ro(L.M1 + (int64_t)z * W + (2 * P - jz));
+#pragma unroll
+                            for (int j = 0; j < YT; ++j) {
+                                T& r = ring[j][(u + 1 + jz) % W];
+                                r = fmaT(kz, a[j], r);
+                                r = fmaT(mz, b[j], r);
+                            }
+                        }
+                    }
+                    // output zp - P has seen its last plane (slot (u + 1) mod W)
+                    const int zo = zp - P;
+#pragma unroll
+                    for (int j = 0; j < YT; ++j) {
+                        T& r = ring[j][(u + 1) % W];
+                        const int gy = y0 + j;
+                        if (own && zo >= zc0 && zo < zend && gy < m) {
+                            const int64_t oi = (int64_t)zo * mm + (int64_t)gy * m + gx;
+                            const int ri = L.rowinfo[oi];
+                            if (ri < 0) {                            // tensor row or inactive row
+                                T y = T(0);
+                                if (ri == -1) y = SC ? r * ro(L.s + oi) : r;
+                                if (MODE == APPLY) {
+                                    out[oi] = y;
+                                } else {
+                                    const T rr = (ri == -2) ? T(0) : rin[oi] - y;
+                                    out[oi] = rr;
+                                    if (MODE == RESID_SMOOTH && ri == -1)
+                                        xs[oi] = fmaT(gamma * ro(L.dinv + oi), rr, xs[oi]);
+                                }
+                                if (DOT && ri == -1) acc = fma((double)x[oi], (double)y, acc);
+                            }
+                        }
+                        r = T(0);
+                    }
+#pragma unroll
+                    for (int i = 0; i < NV; ++i) v[i] = vn[i];
+                }
+            }
+        } else {
+            // ---------------- stored rows: 32 consecutive stored row ids, one per lane
+            const int64_t k = (int64_t)(t - sh.ntensor) * 32 + lane;
+            if (k < L.nb) {
+                const int64_t oi = L.band_row[k];
+                const int ix = (int)(oi % m), iy = (int)((oi / m) % m), iz = (int)(oi / mm);
+                const T* __restrict__ c = L.band_coef + k;
                 const int64_t nb = L.nb;
+                T y = T(0);
 #pragma unroll
-                for (int oz = 0; oz < W; ++oz)
+                for (int oz = 0; oz < W; ++oz) {
+                    const bool zin = (unsigned)(iz + oz - P) < (unsigned)m;
 #pragma unroll
-                    for (int oy = 0; oy < W; ++oy)
+                    for (int oy = 0; oy < W; ++oy) {
+                        const bool yin = zin && (unsigned)(iy + oy - P) < (unsigned)m;
 #pragma unroll
-                        for (int ox = 0; ox < W; ++ox)
-                            y = fmaT(ro(c + (int64_t)(ox + W * (oy + W * oz)) * nb), sx[olz + oz][oly + oy][olx + ox], y);
+                        for (int ox = 0; ox < W; ++ox) {
+                            const bool in = yin && (unsigned)(ix + ox - P) < (unsigned)m;
+                            const int64_t g = oi + (ox - P) + (int64_t)(oy - P) * m + (int64_t)(oz - P) * mm;
+                            const T xv = in ? x[g] : T(0);
+                            y = fmaT(ro(c + (int64_t)(ox + W * (oy + W * oz)) * nb), xv, y);
+                        }
+                    }
+                }
+                if (MODE == APPLY) {
+                    out[oi] = y;
+                } else {
+                    const T rr = rin[oi] - y;
+                    out[oi] = rr;
+                    if (MODE == RESID_SMOOTH) xs[oi] = fmaT(gamma * ro(L.dinv + oi), rr, xs[oi]);
+                }
+                if (DOT) acc = fma((double)x[oi], (double)y, acc);
             }
-            if (MODE == APPLY) {
-                out[oi] = y;
-            } else {
-                const T r = (ri == -2) ? T(0) : rv - y;
-                out[oi] = r;
-                if (MODE == RESID_SMOOTH) xs[oi] = fmaT(gamma * dv, r, xv);
-            }
-            if (DOT) acc = fma((double)sx[olz + P][oly + P][olx + P], (double)y, acc);
         }
     }
-    if (dyn && threadIdx.x == 0) {
-        if (atomicAdd(&L.tile_ctr[1], 1u) == gridDim.x - 1) {
-            L.tile_ctr[0] = 0u;
-            L.tile_ctr[1] = 0u;
-        }
+    // every warp has drawn past the end once; the last one re-arms the counter for the next
+    // launch (which starts only after this grid has completed)
+    if (lane == 0 && atomicAdd(&L.tile_ctr[1], 1u) == gridDim.x * (TPB / 32) - 1) {
+        L.tile_ctr[0] = 0u;
+        L.tile_ctr[1] = 0u;
     }
     if (DOT) {
         double pq;
@@ -611,16 +671,26 @@ __device__ __forceinline__ void blocks_warps(const DevLevelT<T>& L, const T* __r
     }
 }
 
+// Additive Schwarz, stored blocks (Eq. applyCS): x_i += gamma (A_j^{-1} r_j)_a for every
+// (block j, function i = idx_j[a]) pair, one thread per pair: the pair's row of the
+// inverse against the block's gathered residual, then one atomic add.  Blocks on the cut
+// band hold a few functions each (about 3 on average at the 3-D workloads), so a thread
+// per pair keeps every lane busy where a warp per block would leave most of them idle.
 template <typename T>
-__global__ void __launch_bounds__(TPB) k_blocks(DevLevelT<T> L, const T* __restrict__ r, T* x, T gamma,
-                                                const int* done) {
+__global__ void __launch_bounds__(TPB) k_blocks_pairs(DevLevelT<T> L, int64_t npairs, const T* __restrict__ r, T* x,
+                                                      T gamma, const int* done) {
     pdl_begin();
-    extern __shared__ __align__(16) unsigned char smraw[];
-    T* sm = reinterpret_cast<T*>(smraw);
     if (done && *done) return;
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    blocks_warps<T>(L, r, x, gamma, 0, L.nblk, ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5,
-                    ((int64_t)gridDim.x * blockDim.x) >> 5, lane, sm + (int64_t)wib * L.max_block);
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < npairs; q += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t b = ro(L.blk_of + q);
+        const int64_t s = ro(L.blk_ptr + b);
+        const int nj = (int)(ro(L.blk_ptr + b + 1) - s);
+        const int a = (int)(q - s);
+        const T* __restrict__ A = L.blk_val + ro(L.blk_vptr + b) + a;
+        T acc = T(0);
+        for (int c = 0; c < nj; ++c) acc = fmaT(ro(A + (int64_t)c * nj), r[ro(L.blk_idx + s + c)], acc);
+        atomicAdd(&x[ro(L.blk_idx + q)], gamma * acc);
+    }
 }
 
 // One colour of the multiplicative Schwarz sweep (Sec. 3.4): x += sum_{j of colour c}
@@ -740,6 +810,60 @@ __global__ void __launch_bounds__(TPB) k_prolong(DevLevelT<TF> F, DevLevelT<TC> 
     if (done && *done) return;
     prolong_rows<TF, TC, DIM, P>(F, C, xc, e, x, (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
                                  (int64_t)gridDim.x * blockDim.x);
+}
+
+// Sum-factorised 3-D transfers.  R = R_1 (x) R_1 (x) R_1 is applied one direction at a
+// time: along the pass's axis every output index o takes sum_k w[o][k] in[first[o] + k]
+// (the 1-D two-scale table of the restriction, p + 2 weights per coarse index, or of the
+// prolongation, TW per fine index), the other two indices unchanged.  Per fine row that is
+// about (p + 2)(1/2 + 1/4 + 1/8) FMA for the restriction and TW (1/4 + 1/2 + 1) for the
+// prolongation, against (p + 2)^3 / 8 and TW^3 in the direct kernels, whose loads are also
+// (p + 2)^3 or TW^3 gathers per row.  The first pass applies the input's Jacobi scale
+// (FP32 V-cycle: fine d before the restriction, coarse s before the prolongation), the last
+// the output's scale, the zeros of inactive rows and the fused update (restriction:
+// xc = gamma dinv_c rc; prolongation: x += e).
+enum XferEpi { XF_MID = 0, XF_RESTRICT = 1, XF_PROLONG = 2 };
+
+template <typename TI, typename TO, typename T, int AXIS, int EPI>
+__global__ void __launch_bounds__(TPB) k_xfer_pass(const TI* __restrict__ in, TO* __restrict__ out, int nx, int ny,
+                                                   int nz, int n_out, const int32_t* __restrict__ first,
+                                                   const T* __restrict__ w, int nt, const TI* __restrict__ pre,
+                                                   const TO* __restrict__ post, const int32_t* __restrict__ rowinfo,
+                                                   const TO* __restrict__ dinv, TO gamma, TO* __restrict__ upd,
+                                                   const int* done) {
+    pdl_begin();
+    if (done && *done) return;
+    // output dims: the input's with the AXIS extent replaced by n_out
+    const int ox = AXIS == 0 ? n_out : nx, oy = AXIS == 1 ? n_out : ny, oz = AXIS == 2 ? n_out : nz;
+    const int64_t total = (int64_t)ox * oy * oz;
+    const int64_t istride = AXIS == 0 ? 1 : (AXIS == 1 ? (int64_t)nx : (int64_t)nx * ny);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int ix = (int)(i % ox);
+        const int64_t q = i / ox;
+        const int iy = (int)(q % oy), iz = (int)(q / oy);
+        const int o = AXIS == 0 ? ix : (AXIS == 1 ? iy : iz);
+        const int64_t base = (AXIS == 0 ? 0 : ix) + (AXIS == 1 ? 0 : (int64_t)nx * iy) +
+                             (AXIS == 2 ? 0 : (int64_t)nx * ny * iz);
+        const int64_t src0 = base + (int64_t)ro(first + o) * istride;
+        const T* __restrict__ wo = w + (int64_t)o * nt;
+        T acc = T(0);
+#pragma unroll 4
+        for (int k = 0; k < nt; ++k) {
+            const int64_t src = src0 + (int64_t)k * istride;
+            const T v = pre ? (T)in[src] * (T)ro(pre + src) : (T)in[src];
+            acc = fmaT(ro(wo + k), v, acc);
+        }
+        if (EPI == XF_MID) {
+            out[i] = (TO)acc;
+        } else {
+            if (post) acc *= (T)ro(post + i);
+            const bool inactive = rowinfo[i] == -2;
+            const TO v = inactive ? TO(0) : (TO)acc;
+            out[i] = v;
+            if (EPI == XF_RESTRICT && upd) upd[i] = gamma * ro(dinv + i) * v;
+            if (EPI == XF_PROLONG && upd && !inactive) upd[i] += v;
+        }
+    }
 }
 
 // one warp per kept coarse row
@@ -1198,6 +1322,98 @@ __global__ void __launch_bounds__(TPB) k_pcg_xpay(int64_t N, const TZ* __restric
     }
 }
 
+// the sums of NV values over the grid (partials at [k G, (k+1) G)); the last block adds
+// each in block order and returns true with the totals in tot[0..NV) (thread 0)
+template <int NV>
+__device__ __forceinline__ bool finish_reduction_n(const double* v, double* partial, unsigned int* ticket,
+                                                   double* tot) {
+    __shared__ double ws[32];
+    __shared__ bool last;
+#pragma unroll 1
+    for (int k = 0; k < NV; ++k) {
+        const double bs = block_sum(v[k], ws);
+        if (threadIdx.x == 0) partial[(int64_t)k * gridDim.x + blockIdx.x] = bs;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return false;
+    __threadfence();
+#pragma unroll 1
+    for (int k = 0; k < NV; ++k) {
+        double s = 0.0;
+        for (int b = threadIdx.x; b < (int)gridDim.x; b += TPB) s += ((volatile double*)partial)[(int64_t)k * gridDim.x + b];
+        s = block_sum(s, ws);
+        if (threadIdx.x == 0) tot[k] = s;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *ticket = 0u;
+    return true;
+}
+
+__global__ void __launch_bounds__(TPB) k_fcg_push_dots(int64_t N, int m, const double* __restrict__ z,
+                                                       const double* __restrict__ p, const double* __restrict__ q,
+                                                       double* __restrict__ Pring, double* __restrict__ Qring,
+                                                       double* partial, PcgState* st) {
+    pdl_begin();
+    if (st->done) return;
+    const int it = st->iter;                      // steps taken, >= 1 here
+    const int slot = (it - 1) % m, nv = min(it, m);
+    double acc[FCG_MAX];
+#pragma unroll
+    for (int j = 0; j < FCG_MAX; ++j) acc[j] = 0.0;
+    const int64_t stride = (int64_t)gridDim.x * TPB;
+    for (int64_t i = (int64_t)blockIdx.x * TPB + threadIdx.x; i < N; i += stride) {
+        const double zi = z[i], qi = q[i];
+        Pring[(int64_t)slot * N + i] = p[i];
+        Qring[(int64_t)slot * N + i] = qi;
+#pragma unroll
+        for (int j = 0; j < FCG_MAX; ++j)
+            if (j < nv) acc[j] = fma(zi, j == slot ? qi : Qring[(int64_t)j * N + i], acc[j]);
+    }
+    double tot[FCG_MAX];
+    if (finish_reduction_n<FCG_MAX>(acc, partial, &st->ticket[2], tot) && threadIdx.x == 0) {
+        st->fcg_pq[slot] = st->pq;
+        for (int j = 0; j < FCG_MAX; ++j) st->fcg_c[j] = (j < nv && st->fcg_pq[j] > 0.0) ? tot[j] / st->fcg_pq[j] : 0.0;
+        if (!isfinite(tot[0])) {
+            st->done = 1;
+            st->status = -5;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(TPB) k_fcg_dir(int64_t N, int m, const double* __restrict__ z,
+                                                 const double* __restrict__ r, double* __restrict__ p,
+                                                 const double* __restrict__ Pring, double* partial, PcgState* st) {
+    pdl_begin();
+    if (st->done) return;
+    const int nv = min(st->iter, m);
+    double c[FCG_MAX];
+#pragma unroll
+    for (int j = 0; j < FCG_MAX; ++j) c[j] = st->fcg_c[j];
+    double acc = 0.0;
+    const int64_t stride = (int64_t)gridDim.x * TPB;
+    for (int64_t i = (int64_t)blockIdx.x * TPB + threadIdx.x; i < N; i += stride) {
+        double pi = z[i];
+#pragma unroll
+        for (int j = 0; j < FCG_MAX; ++j)
+            if (j < nv) pi = fma(-c[j], Pring[(int64_t)j * N + i], pi);
+        p[i] = pi;
+        acc = fma(r[i], pi, acc);
+    }
+    double rp;
+    if (finish_reduction(acc, partial, &st->ticket[2], &rp) && threadIdx.x == 0) {
+        st->rz = rp;
+        if (!isfinite(rp)) {
+            st->done = 1;
+            st->status = -5;
+        }
+    }
+}
+
 __global__ void __launch_bounds__(TPB) k_init_norms(int64_t N, const double* __restrict__ r, const double* __restrict__ b,
                                                     double* partial, PcgState* st, double* hist) {
     pdl_begin();
@@ -1340,42 +1556,89 @@ inline RowLaunch row_launch(int64_t n) {
 }
 
 inline int tiles_2d(int m) { return ((m + TX - 1) / TX) * ((m + TY - 1) / TY); }
-inline int64_t tiles_3d(int m) {
-    return (int64_t)((m + TX3 - 1) / TX3) * ((m + TY3 - 1) / TY3) * ((m + TZ3 - 1) / TZ3);
+// 3-D operator apply: the z-marching warp kernel on levels with enough work to fill the
+// GPU (IMGM_TILE3D=1: on every level, for testing it on small grids; IMGM_ZM_BLOCKS=k
+// caps its grid at k blocks, so that warps draw many tasks on small grids)
+// Task shape of a level: strips of 32 - 2P columns, segments of yt rows, and z chunks of
+// equal size, as long as possible (each chunk recomputes the plane passes of 2P halo
+// planes) while there are at least ZM_TASKS tensor tasks to spread over the warps (a
+// task is one warp's sequential walk, so too few tasks leave the SMs latency-bound),
+// and no shorter than ZM_ZMIN planes.  IMGM_ZM_ZC / IMGM_ZM_ZMIN override the two limits.
+constexpr int ZM_TASKS = 3600, ZM_ZMIN = 4, ZM_ZMAX = 32;
+ZmShape zm_shape(int m, int64_t nb, int P, int yt) {
+    ZmShape s{};
+    const int xs = 32 - 2 * P;
+    s.sx = (m + xs - 1) / xs;
+    s.sy = (m + yt - 1) / yt;
+    int zmin = ZM_ZMIN, zmax = ZM_ZMAX;
+    if (const char* v = std::getenv("IMGM_ZM_ZMIN")) zmin = std::max(1, std::atoi(v));
+    const int want = (ZM_TASKS + s.sx * s.sy - 1) / (s.sx * s.sy);     // chunks for enough tasks
+    int zc = std::max(zmin, std::min(zmax, (m + want - 1) / want));
+    if (const char* v = std::getenv("IMGM_ZM_ZC")) zc = std::max(1, std::atoi(v));
+    const int nz = (m + zc - 1) / zc;
+    s.zc = (m + nz - 1) / nz;
+    s.sz = (m + s.zc - 1) / s.zc;
+    s.ntensor = (unsigned)((int64_t)s.sx * s.sy * s.sz);
+    s.ntotal = s.ntensor + (unsigned)((nb + 31) / 32);
+    return s;
 }
-// 3-D tile kernels on levels with at least one tile per SM (IMGM_TILE3D=1: on every level,
-// for testing the tile kernel on small grids)
-bool use_tiles_3d(int m) {
+bool use_zm_3d(int m) {
     const char* v = std::getenv("IMGM_TILE3D");
-    return (v && v[0] == '1') || tiles_3d(m) >= num_sms();
+    static const int mmin = [] {
+        const char* w = std::getenv("IMGM_ZM_MIN_M");
+        return w ? std::atoi(w) : 18;
+    }();
+    return (v && v[0] == '1') || m >= mmin;
+}
+// rows per lane: two on large levels (fewer loads per row), one where the level needs the
+// extra tasks (IMGM_ZM_YT overrides)
+int zm_yt(int m) {
+    if (const char* v = std::getenv("IMGM_ZM_YT")) return std::atoi(v) == 1 ? 1 : 2;
+    return m >= 100 ? 2 : 1;
+}
+int zm_grid(const ZmShape& sh, int cap) {
+    int64_t g = std::min<int64_t>((sh.ntotal + TPB / 32 - 1) / (TPB / 32), cap);
+    if (const char* v = std::getenv("IMGM_ZM_BLOCKS")) {
+        const int k = std::atoi(v);
+        if (k > 0) g = std::min<int64_t>(g, k);
+    }
+    return (int)std::max<int64_t>(g, 1);
 }
 
-// blocks of a tile launch: one per tile, except the FP64 operator apply (the CG's A p, and
-// the standalone apply), whose two blocks per SM draw tiles from the level's counter.  In
-// the residual modes of the V-cycle the extra loads per row favour more resident blocks.
+template <typename T, int P, int YT>
+void launch_zm3d_yt(const DevLevelT<T>& L, int mode, const T* x, const T* rin, T* out, T* xs, T gamma, const int* done,
+                    cudaStream_t s) {
+    const ZmShape sh = zm_shape(L.m, L.nb, P, YT);
+    const int g = zm_grid(sh, 2 * num_sms());
+    if (mode == APPLY)
+        launch_pdl(k_apply_zm3d<T, P, APPLY, false, YT>, g, TPB, 0, s, L, x, rin, out, xs, gamma, done, nullptr, nullptr,
+                   sh);
+    else if (mode == RESID)
+        launch_pdl(k_apply_zm3d<T, P, RESID, false, YT>, g, TPB, 0, s, L, x, rin, out, xs, gamma, done, nullptr, nullptr,
+                   sh);
+    else
+        launch_pdl(k_apply_zm3d<T, P, RESID_SMOOTH, false, YT>, g, TPB, 0, s, L, x, rin, out, xs, gamma, done, nullptr,
+                   nullptr, sh);
+}
+
+template <typename T, int P>
+cudaError_t launch_zm3d(const DevLevelT<T>& L, int mode, const T* x, const T* rin, T* out, T* xs, T gamma,
+                        const int* done, cudaStream_t s) {
+    if (L.tile_ctr == nullptr || (L.nb > 0 && L.band_row == nullptr)) return cudaErrorInvalidValue;
+    if (zm_yt(L.m) == 2)
+        launch_zm3d_yt<T, P, 2>(L, mode, x, rin, out, xs, gamma, done, s);
+    else
+        launch_zm3d_yt<T, P, 1>(L, mode, x, rin, out, xs, gamma, done, s);
+    return cudaGetLastError();
+}
+
+// blocks of a 2-D tile launch: one per tile, except the FP64 operator apply (the CG's A p,
+// and the standalone apply), whose two blocks per SM draw tiles from the level's counter.
+// In the residual modes of the V-cycle the extra loads per row favour more resident blocks.
 template <typename T>
 inline int tile_grid(int m, int mode) {
     const int n = tiles_2d(m);
     return (sizeof(T) == 8 && mode == APPLY) ? std::min(n, 2 * num_sms()) : n;
-}
-
-template <typename T, int P>
-cudaError_t launch_tile3d(const DevLevelT<T>& L, int mode, const T* x, const T* rin, T* out, T* xs, T gamma,
-                          const int* done, cudaStream_t s) {
-    if (sizeof(T) == 8 && L.tile_ctr == nullptr) return cudaErrorInvalidValue;
-    const int64_t n = tiles_3d(L.m);
-    // FP64 apply: blocks drawing tiles from the level's counter, four per SM (3-D levels
-    // have many tiles, and more resident blocks hide the tile loads)
-    const int64_t g = (sizeof(T) == 8 && mode == APPLY) ? std::min<int64_t>(n, 4 * num_sms()) : n;
-    if (g > 2147483647LL) return cudaErrorInvalidValue;
-    if (mode == APPLY)
-        launch_pdl(k_apply_tile3d<T, P, APPLY, false>, (unsigned)g, TPB, 0, s, L, x, rin, out, xs, gamma, done, nullptr, nullptr);
-    else if (mode == RESID)
-        launch_pdl(k_apply_tile3d<T, P, RESID, false>, (unsigned)g, TPB, 0, s, L, x, rin, out, xs, gamma, done, nullptr, nullptr);
-    else
-        launch_pdl(k_apply_tile3d<T, P, RESID_SMOOTH, false>, (unsigned)g, TPB, 0, s, L, x, rin, out, xs, gamma, done,
-                   nullptr, nullptr);
-    return cudaGetLastError();
 }
 
 template <typename T, int P>
@@ -1418,10 +1681,10 @@ template <typename T>
 cudaError_t launch_apply(const DevLevelT<T>& L, int mode, const T* x, const T* rin, T* out, T* xs, double gamma,
                          const int* done, cudaStream_t s) {
     // tiles when there are enough of them to fill the GPU; one row per thread otherwise
-    if (L.dim == 3 && use_tiles_3d(L.m)) {
-        if (L.p == 1) return launch_tile3d<T, 1>(L, mode, x, rin, out, xs, (T)gamma, done, s);
-        if (L.p == 2) return launch_tile3d<T, 2>(L, mode, x, rin, out, xs, (T)gamma, done, s);
-        if (L.p == 3) return launch_tile3d<T, 3>(L, mode, x, rin, out, xs, (T)gamma, done, s);
+    if (L.dim == 3 && use_zm_3d(L.m)) {
+        if (L.p == 1) return launch_zm3d<T, 1>(L, mode, x, rin, out, xs, (T)gamma, done, s);
+        if (L.p == 2) return launch_zm3d<T, 2>(L, mode, x, rin, out, xs, (T)gamma, done, s);
+        if (L.p == 3) return launch_zm3d<T, 3>(L, mode, x, rin, out, xs, (T)gamma, done, s);
     }
     if (L.dim == 2 && tiles_2d(L.m) >= num_sms()) {
         if (L.p == 1) return launch_tile2d<T, 1>(L, mode, x, rin, out, xs, (T)gamma, done, s);
@@ -1449,17 +1712,19 @@ cudaError_t launch_apply_pq(const DevLevel& L, const double* p, double* q, doubl
             return cudaErrorInvalidValue;
         return cudaGetLastError();
     }
-    if (L.dim == 3 && use_tiles_3d(L.m)) {
-        if (L.tile_ctr == nullptr) return cudaErrorInvalidValue;
-        const int g = (int)std::min<int64_t>(std::min<int64_t>(tiles_3d(L.m), 4 * num_sms()), reduction_blocks());
-        if (L.p == 1)
-            launch_pdl(k_apply_tile3d<double, 1, APPLY, true>, g, TPB, 0, s, L, p, nullptr, q, nullptr, 0.0, &st->done, partial, st);
-        else if (L.p == 2)
-            launch_pdl(k_apply_tile3d<double, 2, APPLY, true>, g, TPB, 0, s, L, p, nullptr, q, nullptr, 0.0, &st->done, partial, st);
-        else if (L.p == 3)
-            launch_pdl(k_apply_tile3d<double, 3, APPLY, true>, g, TPB, 0, s, L, p, nullptr, q, nullptr, 0.0, &st->done, partial, st);
-        else
-            return cudaErrorInvalidValue;
+    if (L.dim == 3 && use_zm_3d(L.m)) {
+        if (L.tile_ctr == nullptr || (L.nb > 0 && L.band_row == nullptr)) return cudaErrorInvalidValue;
+        const int yt = zm_yt(L.m);
+        const ZmShape sh = zm_shape(L.m, L.nb, L.p, yt);
+        const int g = zm_grid(sh, std::min(2 * num_sms(), reduction_blocks()));
+#define IMGM_ZM_PQ(PP, YY) \
+    launch_pdl(k_apply_zm3d<double, PP, APPLY, true, YY>, g, TPB, 0, s, L, p, nullptr, q, nullptr, 0.0, &st->done, \
+               partial, st, sh)
+        if (L.p == 1) { if (yt == 2) IMGM_ZM_PQ(1, 2); else IMGM_ZM_PQ(1, 1); }
+        else if (L.p == 2) { if (yt == 2) IMGM_ZM_PQ(2, 2); else IMGM_ZM_PQ(2, 1); }
+        else if (L.p == 3) { if (yt == 2) IMGM_ZM_PQ(3, 2); else IMGM_ZM_PQ(3, 1); }
+        else return cudaErrorInvalidValue;
+#undef IMGM_ZM_PQ
         return cudaGetLastError();
     }
     IMGM_DISPATCH(L.dim, L.p, (launch_pdl(k_apply_pq<D, Q>, reduction_blocks(), TPB, 0, s, L, p, q, partial, st)));
@@ -1476,11 +1741,9 @@ cudaError_t launch_scale_diag(const DevLevelT<T>& L, const T* r, T* x, double ga
 template <typename T>
 cudaError_t launch_blocks(const DevLevelT<T>& L, const T* r, T* x, double gamma, const int* done, cudaStream_t s) {
     if (L.nblk == 0) return cudaSuccess;
-    const int warps = 2;                        // small blocks: spread the work over all SMs
-    int64_t g = (L.nblk + warps - 1) / warps;
-    if (g > 65535) g = 65535;
-    size_t smem = (size_t)warps * L.max_block * sizeof(T);
-    launch_pdl(k_blocks<T>, (int)g, 32 * warps, smem, s, L, r, x, (T)gamma, done);
+    if (L.blk_of == nullptr || L.npair <= 0) return cudaErrorInvalidValue;
+    const RowLaunch rl = row_launch(L.npair);
+    launch_pdl(k_blocks_pairs<T>, rl.grid, rl.block, 0, s, L, L.npair, r, x, (T)gamma, done);
     return cudaGetLastError();
 }
 
@@ -1497,9 +1760,51 @@ cudaError_t launch_colour_smooth(const DevLevelT<T>& L, int64_t b_first, int64_t
     return cudaGetLastError();
 }
 
+// the three passes of the sum-factorised 3-D restriction (fine type TF, coarse type TC,
+// arithmetic in TF): x (fine z, y; coarse x), y, then z into the coarse level
+template <typename TF, typename TC>
+void restrict_passes(const DevLevelT<TF>& F, const DevLevelT<TC>& C, const TF* rf, TC* rc, TC* xc, double gamma,
+                     const int* done, cudaStream_t s) {
+    const int mf = F.m, mc = C.m, nt = F.p + 2;
+    TF* u1 = reinterpret_cast<TF*>(F.xs1);          // [mf][mf][mc]
+    TF* u2 = reinterpret_cast<TF*>(F.xs2);          // [mf][mc][mc]
+    const RowLaunch l1 = row_launch((int64_t)mf * mf * mc), l2 = row_launch((int64_t)mf * mc * mc),
+                    l3 = row_launch(C.N);
+    launch_pdl(k_xfer_pass<TF, TF, TF, 0, XF_MID>, l1.grid, l1.block, 0, s, rf, u1, mf, mf, mf, mc, F.r_first, F.r_w,
+               nt, F.d, (const TF*)nullptr, (const int32_t*)nullptr, (const TF*)nullptr, TF(0), (TF*)nullptr, done);
+    launch_pdl(k_xfer_pass<TF, TF, TF, 1, XF_MID>, l2.grid, l2.block, 0, s, (const TF*)u1, u2, mc, mf, mf, mc,
+               F.r_first, F.r_w, nt, (const TF*)nullptr, (const TF*)nullptr, (const int32_t*)nullptr,
+               (const TF*)nullptr, TF(0), (TF*)nullptr, done);
+    launch_pdl(k_xfer_pass<TF, TC, TF, 2, XF_RESTRICT>, l3.grid, l3.block, 0, s, (const TF*)u2, rc, mc, mc, mf, mc,
+               F.r_first, F.r_w, nt, (const TF*)nullptr, C.s, C.rowinfo, C.dinv, (TC)gamma, xc, done);
+}
+
+// the three passes of the sum-factorised 3-D prolongation: x (coarse z, y; fine x), y,
+// then z onto the fine level
+template <typename TF, typename TC>
+void prolong_passes(const DevLevelT<TF>& F, const DevLevelT<TC>& C, const TC* xc, TF* e, TF* x, const int* done,
+                    cudaStream_t s) {
+    const int mf = F.m, mc = C.m, nt = F.TW;
+    TF* v1 = reinterpret_cast<TF*>(F.xs2);          // [mc][mc][mf]
+    TF* v2 = reinterpret_cast<TF*>(F.xs1);          // [mc][mf][mf]
+    const RowLaunch l1 = row_launch((int64_t)mc * mc * mf), l2 = row_launch((int64_t)mc * mf * mf),
+                    l3 = row_launch(F.N);
+    launch_pdl(k_xfer_pass<TC, TF, TF, 0, XF_MID>, l1.grid, l1.block, 0, s, xc, v1, mc, mc, mc, mf, F.t_first, F.t_w,
+               nt, C.s, (const TF*)nullptr, (const int32_t*)nullptr, (const TF*)nullptr, TF(0), (TF*)nullptr, done);
+    launch_pdl(k_xfer_pass<TF, TF, TF, 1, XF_MID>, l2.grid, l2.block, 0, s, (const TF*)v1, v2, mf, mc, mc, mf,
+               F.t_first, F.t_w, nt, (const TF*)nullptr, (const TF*)nullptr, (const int32_t*)nullptr,
+               (const TF*)nullptr, TF(0), (TF*)nullptr, done);
+    launch_pdl(k_xfer_pass<TF, TF, TF, 2, XF_PROLONG>, l3.grid, l3.block, 0, s, (const TF*)v2, e, mf, mf, mc, mf,
+               F.t_first, F.t_w, nt, (const TF*)nullptr, F.d, F.rowinfo, (const TF*)nullptr, TF(0), x, done);
+}
+
 template <typename T>
 cudaError_t launch_restrict(const DevLevelT<T>& F, const DevLevelT<T>& C, const T* rf, T* rc, T* xc, double gamma,
                             const int* done, cudaStream_t s) {
+    if (F.dim == 3 && F.xs1 && F.xs2) {
+        restrict_passes<T, T>(F, C, rf, rc, xc, gamma, done, s);
+        return cudaGetLastError();
+    }
     const RowLaunch rl = row_launch(C.N);
     IMGM_DISPATCH(F.dim, F.p, (launch_pdl(k_restrict<T, T, D, Q>, rl.grid, rl.block, 0, s, F, C, rf, rc, xc, (T)gamma, done)));
     return cudaGetLastError();
@@ -1507,8 +1812,12 @@ cudaError_t launch_restrict(const DevLevelT<T>& F, const DevLevelT<T>& C, const 
 
 cudaError_t launch_restrict_64to32(const DevLevel& F, const DevLevelT<float>& C, const double* rf, float* rc, float* xc,
                                    double gamma, cudaStream_t s) {
-    const RowLaunch rl = row_launch(C.N);
     const int* done = nullptr;
+    if (F.dim == 3 && F.xs1 && F.xs2) {
+        restrict_passes<double, float>(F, C, rf, rc, xc, gamma, done, s);
+        return cudaGetLastError();
+    }
+    const RowLaunch rl = row_launch(C.N);
     IMGM_DISPATCH(F.dim, F.p,
                   (launch_pdl(k_restrict<double, float, D, Q>, rl.grid, rl.block, 0, s, F, C, rf, rc, xc, (float)gamma, done)));
     return cudaGetLastError();
@@ -1525,6 +1834,10 @@ cudaError_t launch_prolong_32to64(const DevLevel& F, const DevLevelT<float>& C, 
 template <typename T>
 cudaError_t launch_prolong(const DevLevelT<T>& F, const DevLevelT<T>& C, const T* xc, T* e, T* x, const int* done,
                            cudaStream_t s) {
+    if (F.dim == 3 && F.xs1 && F.xs2) {
+        prolong_passes<T, T>(F, C, xc, e, x, done, s);
+        return cudaGetLastError();
+    }
     const RowLaunch rl = row_launch(F.N);
     IMGM_DISPATCH(F.dim, F.p, (launch_pdl(k_prolong<T, T, D, Q>, rl.grid, rl.block, 0, s, F, C, xc, e, x, done)));
     return cudaGetLastError();
@@ -1628,6 +1941,20 @@ template <typename TZ>
 cudaError_t launch_pcg_rz(int64_t N, const double* r, const TZ* z, const TZ* zs, const TZ* zprev, double* partial,
                           PcgState* st, cudaStream_t s, const double* qprev) {
     launch_pdl(k_pcg_rz<TZ>, reduction_blocks(), TPB, 0, s, N, r, z, zs, zprev, partial, st, qprev);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fcg_push_dots(int64_t N, int m, const double* z, const double* p, const double* q, double* Pring,
+                                 double* Qring, double* partial, PcgState* st, cudaStream_t s) {
+    if (m < 1 || m > FCG_MAX) return cudaErrorInvalidValue;
+    launch_pdl(k_fcg_push_dots, reduction_blocks(), TPB, 0, s, N, m, z, p, q, Pring, Qring, partial, st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fcg_dir(int64_t N, int m, const double* z, const double* r, double* p, const double* Pring,
+                           double* partial, PcgState* st, cudaStream_t s) {
+    if (m < 1 || m > FCG_MAX) return cudaErrorInvalidValue;
+    launch_pdl(k_fcg_dir, reduction_blocks(), TPB, 0, s, N, m, z, r, p, Pring, partial, st);
     return cudaGetLastError();
 }
 

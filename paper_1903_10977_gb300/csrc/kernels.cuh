@@ -18,6 +18,7 @@ struct DevLevelT {
     const int32_t* rowinfo = nullptr;   // [N]: -2 inactive, -1 tensor-stencil row, >= 0 stored row id
     const T* band_coef = nullptr;       // [ncoef][nb]
     int32_t nb = 0;
+    const int32_t* band_row = nullptr;  // [nb]: row of each stored row id
     const T* K1 = nullptr;              // [m][2p+1]
     const T* M1 = nullptr;              // [m][2p+1]
     const T* dinv = nullptr;            // [N]
@@ -27,6 +28,8 @@ struct DevLevelT {
     const int32_t* blk_idx = nullptr;
     const int64_t* blk_vptr = nullptr;
     const T* blk_val = nullptr;
+    const int32_t* blk_of = nullptr;    // [npair]: block of each (block, function) pair
+    int64_t npair = 0;                  // blk_ptr[nblk]
     // restriction to the next coarser level (levels >= 2)
     const int32_t* r_first = nullptr;   // [m_c]
     const T* r_w = nullptr;             // [m_c][p+2]
@@ -39,6 +42,10 @@ struct DevLevelT {
     const T* d = nullptr;
     // work counter of the FP64 tile kernels ([0] next tile, [1] blocks done); zero between launches
     unsigned int* tile_ctr = nullptr;
+    // scratch of the sum-factorised 3-D transfers from this level to the next coarser one
+    // (m^2 m_c and m m_c^2 doubles; nullptr where the direct kernels run)
+    double* xs1 = nullptr;
+    double* xs2 = nullptr;
 };
 using DevLevel = DevLevelT<double>;
 
@@ -56,7 +63,12 @@ struct PcgState {
     double rz_prev;     // r_{k+1}^T z_k (flexible CG)
     int flexible;       // 1: Polak-Ribiere beta (mixed-precision V-cycle)
     int pad;
+    // truncated flexible CG, FCG(m): p_j^T A p_j of the stored directions (ring slot j) and
+    // the projection coefficients (z^T A p_j) / (p_j^T A p_j) of the current step
+    double fcg_pq[8];
+    double fcg_c[8];
 };
+constexpr int FCG_MAX = 8;
 
 enum ApplyMode { APPLY = 0, RESID = 1, RESID_SMOOTH = 2 };
 
@@ -124,6 +136,17 @@ template <typename TZ>
 cudaError_t launch_pcg_rz(int64_t N, const double* r, const TZ* z, const TZ* zs, const TZ* zprev, double* partial,
                           PcgState* st, cudaStream_t s, const double* qprev = nullptr);
 // p = z + beta p (and zprev = z^ when zprev != nullptr)
+// Truncated flexible CG, FCG(m) (Notay 2000), FP64 z (after the V-cycle of this
+// iteration and any learned stage): push_dots stores the direction just used (p, A p and
+// p^T A p, the step's st->pq) in ring slot (iter - 1) mod m and forms
+// c_j = (z^T A p_j) / (p_j^T A p_j) over the min(iter, m) stored directions; dir sets
+// p = z - sum_j c_j p_j and st->rz = r^T p, from which the next apply takes alpha.
+// Pring, Qring: m x N doubles each.
+cudaError_t launch_fcg_push_dots(int64_t N, int m, const double* z, const double* p, const double* q, double* Pring,
+                                 double* Qring, double* partial, PcgState* st, cudaStream_t s);
+cudaError_t launch_fcg_dir(int64_t N, int m, const double* z, const double* r, double* p, const double* Pring,
+                           double* partial, PcgState* st, cudaStream_t s);
+
 template <typename TZ>
 cudaError_t launch_pcg_xpay(int64_t N, const TZ* z, const TZ* zs, double* p, TZ* zprev, PcgState* st,
                             cudaStream_t s);

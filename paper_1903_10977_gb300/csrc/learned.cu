@@ -11,6 +11,7 @@
 #include <cuda_bf16.h>
 
 #include <cmath>
+#include <cstdlib>
 
 #include "kernels.cuh"
 #include "learned.cuh"
@@ -132,6 +133,202 @@ __global__ void __launch_bounds__(CTPB) k_conv(const TIN* __restrict__ x, const 
             if (yf) yf[v] = on ? acc[0] : 0.f;
         }
     }
+}
+
+// ---------------------------------------------------------------------------------
+// The 16 -> 16 layer's forward convolution on the tensor cores (tcgen05, kind::f16 with
+// bf16 operands and an FP32 accumulator in tensor memory).  It is an implicit GEMM: the
+// 128 output voxels of an 8 x 16 patch of one z plane are the M = 128 rows, the 16 output
+// channels N = 16, and each of the 27 taps one K = 16 step (the 16 input channels of the
+// neighbour in that direction): y = sum_tap X_tap W_tap^T, 27 MMAs per output plane.
+//
+// A CTA walks a column of patches along z.  Its input planes (the patch plus a one-voxel
+// halo, 10 x 18 voxels, zero outside the grid) sit in a ring of three shared-memory
+// slots, each stored as two planes of 8-channel groups (16 bytes per voxel, x fastest).
+// In that layout the operand of tap (dx, dy, dz) is a canonical K-major matrix without
+// swizzling: 8-row core matrices are 8 consecutive voxels of an x line (16-byte rows), the
+// next 8 rows the next y line (stride 10 x 16 B), the second 8 channels one group-plane
+// further; its start moves by 16 bytes per voxel of shift, so all 27 operands are views
+// of the same ring.  The weights of tap t, W_t[out][in], are the K-major B operand in the
+// same layout (16-byte rows per output channel).
+//
+// Per output plane: the CTA waits for the previous plane's MMAs (an mbarrier the MMA
+// commit arrives on), loads the next input plane into the slot they no longer read, and
+// one thread issues the plane's 27 MMAs into one of two accumulators while the four warps
+// read the previous plane's accumulator (tcgen05.ld, one warp per 32 rows), apply the
+// ReLU and store bf16.  Every wait is bounded: after about a second the CTA sets *err and
+// stops (the host reports the error), never hanging the GPU.
+constexpr int TC_PX = 8, TC_PY = 16;                 // output patch of one plane: 128 voxels
+constexpr int TC_RX = TC_PX + 2, TC_RY = TC_PY + 2;  // its input region with the halo
+constexpr int TC_RV = TC_RX * TC_RY;                 // 180 voxels
+constexpr int TC_GROUP = TC_RV * 16;                 // one 8-channel group-plane of a slot (bytes)
+constexpr int TC_SLOT = 2 * TC_GROUP;                // one input plane: 5,760 bytes
+constexpr int TC_WBYTES = 27 * 512;                  // B operands of the 27 taps
+constexpr int TC_ZC = 16;                            // output planes per CTA
+constexpr int TC_THREADS = 128;
+// shared memory: weights, ring, two mbarriers and the TMEM address, then a margin that
+// keeps every operand view of the ring inside the allocation even if the leading and
+// stride offsets of a descriptor were read the other way round (16 row groups x 2,880 B)
+constexpr int TC_SMEM = TC_WBYTES + 3 * TC_SLOT + 64 + 40960;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// tcgen05 shared-memory matrix descriptor: start address, leading (K-direction) and
+// stride (M/N-direction) byte offsets, descriptor version 1, no swizzle
+__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
+}
+
+// instruction descriptor of kind::f16: FP32 accumulator (bits 4-5 = 1), A and B bf16
+// (bits 7-9, 10-12 = 1), both K-major, N >> 3 at bits 17-22, M >> 4 at bits 24-28
+constexpr uint32_t TC_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((16u >> 3) << 17) | ((128u >> 4) << 24);
+
+__device__ __forceinline__ uint64_t globaltimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+// waits until the mbarrier's phase of the given parity has completed; false after ~1 s
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+    const uint64_t t0 = globaltimer();
+    for (;;) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        if (globaltimer() - t0 > 1000000000ull) return false;
+    }
+}
+
+__global__ void __launch_bounds__(TC_THREADS) k_conv16_tc(const uint16_t* __restrict__ x,
+                                                          const uint16_t* __restrict__ w, uint16_t* __restrict__ y,
+                                                          int nx, int ny, int nz, int* err) {
+    extern __shared__ __align__(1024) unsigned char tsm[];
+    unsigned char* wsm = tsm;                                    // [27][2 groups][16 out][8 in] bf16
+    unsigned char* ring = tsm + TC_WBYTES;                       // [3 slots][2 groups][180 voxels][8] bf16
+    uint64_t* bars = reinterpret_cast<uint64_t*>(ring + 3 * TC_SLOT);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 2);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int npx = (nx + TC_PX - 1) / TC_PX, npy = (ny + TC_PY - 1) / TC_PY;
+    const int bx = blockIdx.x % npx, by = (blockIdx.x / npx) % npy, bz = blockIdx.x / (npx * npy);
+    const int x0 = bx * TC_PX, y0 = by * TC_PY, z0 = bz * TC_ZC, z1 = min(z0 + TC_ZC, nz);
+
+    // B operands: W_t[o][i] -> group i / 8, row o, column i % 8
+    uint16_t* wsm16 = reinterpret_cast<uint16_t*>(wsm);
+    for (int q = tid; q < 27 * 256; q += TC_THREADS) {
+        const int t = q >> 8, o = (q >> 4) & 15, i = q & 15;
+        wsm16[t * 256 + (i >> 3) * 128 + o * 8 + (i & 7)] = w[q];
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bars[0])) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bars[1])) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {                                 // 32 columns: two 16-column accumulators
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 32;" ::"r"(smem_u32(tslot))
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    // one input plane into its slot: 180 voxels x 2 groups of 16 bytes
+    auto load_plane = [&](int zp) {
+        unsigned char* slot = ring + ((zp - z0 + 3) % 3) * TC_SLOT;
+        for (int q = tid; q < 2 * TC_RV; q += TC_THREADS) {
+            const int vox = q >> 1, g = q & 1;
+            const int gx = x0 - 1 + vox % TC_RX, gy = y0 - 1 + vox / TC_RX;
+            uint4 val = make_uint4(0u, 0u, 0u, 0u);
+            if ((unsigned)gx < (unsigned)nx && (unsigned)gy < (unsigned)ny && (unsigned)zp < (unsigned)nz)
+                val = *reinterpret_cast<const uint4*>(x + ((int64_t)gx + (int64_t)nx * (gy + (int64_t)ny * zp)) * 16 +
+                                                      g * 8);
+            *reinterpret_cast<uint4*>(slot + g * TC_GROUP + vox * 16) = val;
+        }
+    };
+    load_plane(z0 - 1);
+    load_plane(z0);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tslot;
+    const uint32_t wbase = smem_u32(wsm), rbase = smem_u32(ring);
+
+    // accumulator of plane k -> ReLU -> bf16 -> y (row = warp * 32 + lane)
+    auto epilogue = [&](int k) {
+        uint32_t v[16];
+        const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)((k & 1) * 16);
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+            "%14, %15}, [%16];"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+            : "r"(ta));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        const int row = warp * 32 + lane;
+        const int gx = x0 + row % TC_PX, gy = y0 + row / TC_PX, gz = z0 + k;
+        if (gx < nx && gy < ny) {
+            uint32_t pk[8];
+#pragma unroll
+            for (int c = 0; c < 8; ++c)
+                pk[c] = bf_bits(fmaxf(__uint_as_float(v[2 * c]), 0.f)) |
+                        (bf_bits(fmaxf(__uint_as_float(v[2 * c + 1]), 0.f)) << 16);
+            uint4* out = reinterpret_cast<uint4*>(y + ((int64_t)gx + (int64_t)nx * (gy + (int64_t)ny * gz)) * 16);
+            out[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+            out[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+        }
+    };
+
+    bool ok = true;
+    const int nk = z1 - z0;
+    for (int k = 0; k < nk && ok; ++k) {
+        const int z = z0 + k;
+        if (k > 0) ok = __syncthreads_and(mbar_wait(smem_u32(&bars[(k - 1) & 1]), ((k - 1) >> 1) & 1));
+        if (!ok) break;
+        load_plane(z + 1);                            // the slot of plane z - 2, no longer read
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (tid == 0) {
+            const uint32_t d = tmem + (uint32_t)((k & 1) * 16);
+#pragma unroll 1
+            for (int t = 0; t < 27; ++t) {
+                const int dz = t / 9 - 1, dy = (t / 3) % 3 - 1, dx = t % 3 - 1;
+                const uint32_t a = rbase + ((z + dz - z0 + 3) % 3) * TC_SLOT + 16 * ((dx + 1) + TC_RX * (dy + 1));
+                const uint64_t ad = tc_desc(a, TC_GROUP, 16 * TC_RX);
+                const uint64_t bd = tc_desc(wbase + t * 512, 256, 128);
+                const uint32_t acc = t > 0 ? 1u : 0u;
+                asm volatile(
+                    "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+                    ::"r"(d), "l"(ad), "l"(bd), "r"(TC_IDESC), "r"(acc)
+                    : "memory");
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             smem_u32(&bars[k & 1]))
+                         : "memory");
+        }
+        if (k > 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            epilogue(k - 1);
+        }
+    }
+    if (ok && nk > 0) {
+        ok = __syncthreads_and(mbar_wait(smem_u32(&bars[(nk - 1) & 1]), ((nk - 1) >> 1) & 1));
+        if (ok) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            epilogue(nk - 1);
+        }
+    }
+    if (!ok && tid == 0) atomicExch(err, 1);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" ::"r"(tmem) : "memory");
 }
 
 // gw[tap][o][i] += sum_v dy[v][o] x[v + off_tap][i]
@@ -341,6 +538,21 @@ int sm_count() {
     return sms;
 }
 
+// the 16 -> 16 forward convolution on the tensor cores unless IMGM_NET_TC=0 (CUDA-core
+// FP32 loop, kept for comparison); the kernel's shared memory is opted in once per process
+bool net_tensor_cores() {
+    static const bool on = [] {
+        const char* v = std::getenv("IMGM_NET_TC");
+        return !(v && v[0] == '0');
+    }();
+    static bool attr = false;
+    if (on && !attr) {
+        cudaFuncSetAttribute(k_conv16_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+        attr = true;
+    }
+    return on;
+}
+
 int grid_for(int64_t work, int per_block, int max_per_sm) {
     const int64_t want = (work + per_block - 1) / per_block;
     const int64_t cap = (int64_t)max_per_sm * sm_count();
@@ -361,6 +573,8 @@ cudaError_t NetWorkspace::ensure(int nx_, int ny_, int nz_, bool train_) {
         if ((e = cudaMalloc(&a1, n * NET_C * sizeof(uint16_t))) != cudaSuccess) return e;
         if ((e = cudaMalloc(&a2, n * NET_C * sizeof(uint16_t))) != cudaSuccess) return e;
         if ((e = cudaMalloc(&partial, 2 * NET_PARTIALS * sizeof(double))) != cudaSuccess) return e;
+        if ((e = cudaMalloc(&err, sizeof(int))) != cudaSuccess) return e;
+        if ((e = cudaMemset(err, 0, sizeof(int))) != cudaSuccess) return e;
         if (train_) {
             if ((e = cudaMalloc(&o, n * sizeof(float))) != cudaSuccess) return e;
             if ((e = cudaMalloc(&d3, n * sizeof(float))) != cudaSuccess) return e;
@@ -375,9 +589,10 @@ cudaError_t NetWorkspace::ensure(int nx_, int ny_, int nz_, bool train_) {
 }
 
 void NetWorkspace::release() {
-    for (void* p : {(void*)a0, (void*)a1, (void*)a2, (void*)o, (void*)d3, (void*)d2, (void*)d1, (void*)partial})
+    for (void* p : {(void*)a0, (void*)a1, (void*)a2, (void*)o, (void*)d3, (void*)d2, (void*)d1, (void*)partial, (void*)err})
         if (p) cudaFree(p);
     a0 = a1 = a2 = nullptr;
+    err = nullptr;
     o = d3 = d2 = d1 = nullptr;
     partial = nullptr;
     cap = 0;
@@ -399,8 +614,15 @@ cudaError_t net_forward(const uint16_t* wb, NetWorkspace& ws, const double* in, 
     k_pack<<<elementwise_grid(nvox), RTPB, 0, s>>>(nvox, in, mask, in_scale, ws.a0);
     k_conv<1, NET_C, uint16_t, EPI_RELU><<<gc, CTPB, 0, s>>>(ws.a0, wb, nullptr, nullptr, ws.a1, nullptr, nullptr,
                                                              ws.nx, ws.ny, ws.nz);
-    k_conv<NET_C, NET_C, uint16_t, EPI_RELU><<<gc, CTPB, 0, s>>>(ws.a1, wb + NET_OFF2, nullptr, nullptr, ws.a2, nullptr,
-                                                                 nullptr, ws.nx, ws.ny, ws.nz);
+    if (net_tensor_cores()) {
+        const int64_t g = (int64_t)((ws.nx + TC_PX - 1) / TC_PX) * ((ws.ny + TC_PY - 1) / TC_PY) *
+                          ((ws.nz + TC_ZC - 1) / TC_ZC);
+        if (g > 2147483647LL) return cudaErrorInvalidValue;
+        k_conv16_tc<<<(unsigned)g, TC_THREADS, TC_SMEM, s>>>(ws.a1, wb + NET_OFF2, ws.a2, ws.nx, ws.ny, ws.nz, ws.err);
+    } else {
+        k_conv<NET_C, NET_C, uint16_t, EPI_RELU><<<gc, CTPB, 0, s>>>(ws.a1, wb + NET_OFF2, nullptr, nullptr, ws.a2,
+                                                                     nullptr, nullptr, ws.nx, ws.ny, ws.nz);
+    }
     k_conv<NET_C, 1, uint16_t, EPI_OUT><<<gc, CTPB, 0, s>>>(ws.a2, wb + NET_OFF3, nullptr, mask, nullptr, out32, out64,
                                                             ws.nx, ws.ny, ws.nz);
     add_launches(4);

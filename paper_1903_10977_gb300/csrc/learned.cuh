@@ -35,6 +35,7 @@ struct NetWorkspace {
     float* o = nullptr;              // output [v] (training)
     float *d3 = nullptr, *d2 = nullptr, *d1 = nullptr;      // dL/d(out) [v], dL/d(a2), dL/d(a1) [v][16]
     double* partial = nullptr;       // [2 * NET_PARTIALS]
+    int* err = nullptr;              // set by a tensor-core convolution whose wait gave up
     cudaError_t ensure(int nx, int ny, int nz, bool train);
     void release();
 };

@@ -135,12 +135,15 @@ def test_full3d_solution_approximates_manufactured(full):
 
 def test_full3d_vcycle_symmetric_positive_and_bounded(full):
     """<B u, v> = <u, B v>, <B u, u> > 0, and the largest eigenvalue of B A (power iteration
-    in the A inner product) in (0.9, 1]."""
+    in the A inner product) in (0.9, 1].  u and v are residuals A w of random w: the class
+    of vectors the CG hands the V-cycle.  (The FP32 V-cycle works on Jacobi-scaled data,
+    r / sqrt(A_ii); an O(1) entry on a function whose cut support makes A_ii tiny would
+    leave the FP32 range there, while a residual's entry scales with its row.)"""
     precision, loc, rows, A_rows, active, S = full
     tol = 1e-11 if precision == 0 else 1e-5
     mask = S.active_mask().astype(float)
-    u = dev(random_grid_vector(mask.size, 11) * mask)
-    v = dev(random_grid_vector(mask.size, 12) * mask)
+    u = S.apply_operator(dev(random_grid_vector(mask.size, 11) * mask))
+    v = S.apply_operator(dev(random_grid_vector(mask.size, 12) * mask))
     Bu, Bv = S.apply_preconditioner(u), S.apply_preconditioner(v)
     buu, bvv = float(Bu @ u), float(Bv @ v)
     assert buu > 0 and bvv > 0

@@ -44,11 +44,11 @@ def host(t):
     return t.detach().cpu().numpy()
 
 
-def grid_case(seed):
+def grid_case(seed, shape=SHAPE):
     rng = np.random.default_rng(seed)
-    mask = (rng.random(SHAPE) < 0.8).astype(np.float64)
-    x = rng.standard_normal(SHAPE) * mask
-    y = rng.standard_normal(SHAPE) * mask
+    mask = (rng.random(shape) < 0.8).astype(np.float64)
+    x = rng.standard_normal(shape) * mask
+    y = rng.standard_normal(shape) * mask
     w = initial_weights(seed) * 2.0
     return mask, x, y, w.astype(np.float32).astype(np.float64)
 
@@ -61,11 +61,13 @@ def scale_chain(w, x, mask):
     return s[0] * mask
 
 
-@pytest.mark.parametrize("seed", [1, 2])
-def test_net_forward_matches_oracle(seed):
-    mask, x, _, w = grid_case(seed)
+@pytest.mark.parametrize("seed,shape", [(1, SHAPE), (2, SHAPE), (6, (37, 21, 19))])
+def test_net_forward_matches_oracle(seed, shape):
+    """Entry by entry within 3 2^-8 S_3.  The last shape spans several 8 x 16 patches and
+    three 16-plane chunks of the tensor-core layer, with ragged ends in every direction."""
+    mask, x, _, w = grid_case(seed, shape)
     net = lib.Net(w)
-    out = host(net.forward(dev(x.ravel()), SHAPE, mask=dev(mask.ravel(), torch.uint8))).reshape(SHAPE)
+    out = host(net.forward(dev(x.ravel()), shape, mask=dev(mask.ravel(), torch.uint8))).reshape(shape)
     ref, _ = NL.forward(w, x, mask, bf16=True)
     S3 = scale_chain(w, x, mask)
     err = np.abs(out - ref)
@@ -75,8 +77,8 @@ def test_net_forward_matches_oracle(seed):
     record(seed=seed, rel_l2=float(np.linalg.norm(out - ref) / np.linalg.norm(ref)),
            max_err_over_scale=float((err / (S3 + 1e-300)).max()))
     # no mask: the whole grid is active
-    out = host(net.forward(dev(x.ravel()), SHAPE)).reshape(SHAPE)
-    ref, _ = NL.forward(w, x, np.ones(SHAPE), bf16=True)
+    out = host(net.forward(dev(x.ravel()), shape)).reshape(shape)
+    ref, _ = NL.forward(w, x, np.ones(shape), bf16=True)
     assert np.linalg.norm(out - ref) <= 1e-2 * np.linalg.norm(ref)
     net.close()
 
@@ -258,12 +260,48 @@ def test_training_gains_and_learned_solve(problem):
     xe = host(x0)[d.active]
     assert energy_rel(host(x1)[d.active] - xe, xe, d.A) <= 1e-6
     assert res1["iterations"] <= 1.25 * res0["iterations"], (res0["iterations"], res1["iterations"])
+    # with FCG(5) the stage's corrections keep their Krylov acceleration: fewer iterations
+    # than plain PCG with the V-cycle alone (the gain the trained network brings)
+    S.set_fcg(5)
+    x2, res2, _ = S.pcg_solve(b, rtol=1e-8, maxit=1000)
+    S.set_fcg(0)
+    assert res2["status"] == lib.IMGM_OK and res2["true_rel_residual"] <= 2e-8
+    assert energy_rel(host(x2)[d.active] - xe, xe, d.A) <= 1e-6
     record(loss_first=float(losses[:2].mean()), loss_last=float(losses[-40:].mean()), held_ratio_untrained=ratio0,
            held_ratio_trained=ratio1, plain_iterations=res0["iterations"], learned_iterations=res1["iterations"],
+           learned_fcg5_iterations=res2["iterations"],
            plain_launches=res0["kernel_launches"], learned_launches=res1["kernel_launches"])
+    assert res2["iterations"] < res0["iterations"], (res0["iterations"], res2["iterations"])
     S.set_net(None)
     net.close()
     net0.close()
+
+
+def test_fcg_matches_oracle_and_pcg(problem):
+    """FCG(5) with the fixed V-cycle and no network: after three steps the iterate equals
+    the oracle's fcg (oracle/learned.py), and the converged solve takes plain PCG's
+    iteration count to within one (for a fixed SPD preconditioner FCG(m) is PCG up to
+    rounding); m out of range is rejected."""
+    pr, lay, d, H, S = problem
+    b = dev(d.to_full(d.b))
+    x0, res0, _ = S.pcg_solve(b, rtol=1e-8, maxit=1000)
+    S.set_fcg(5)
+    try:
+        x, res, _ = S.pcg_solve(b, rtol=0.0, maxit=3)
+        ref, it, _ = NL.fcg(d.A, d.b, H.precondition, m=5, rtol=0.0, maxit=3)
+        assert res["iterations"] == 3 == it
+        xa = host(x)[d.active]
+        assert energy_rel(xa - ref, ref, d.A) < 1e-10
+        x, res, _ = S.pcg_solve(b, rtol=1e-8, maxit=1000)
+        assert res["status"] == lib.IMGM_OK and res["true_rel_residual"] <= 2e-8
+        assert abs(res["iterations"] - res0["iterations"]) <= 1, (res["iterations"], res0["iterations"])
+        xe = host(x0)[d.active]
+        assert energy_rel(host(x)[d.active] - xe, xe, d.A) <= 1e-7
+        record(fcg5_iterations=res["iterations"], pcg_iterations=res0["iterations"])
+    finally:
+        S.set_fcg(0)
+    with pytest.raises(lib.ImgmError):
+        S.set_fcg(9)
 
 
 def test_set_net_rejects_2d_and_fp32_vcycle():

@@ -1,6 +1,9 @@
-"""The 3-D sum-factorised tile kernels (operator apply, residual modes, the CG's p^T A p),
-forced onto the small 3-D parity grids with IMGM_TILE3D=1 (on the workloads they run on
-levels with at least one tile per SM): parity with the oracle as for the row kernels."""
+"""The 3-D sum-factorised z-marching kernel (operator apply, residual modes, the CG's
+p^T A p, stored rows as tasks of their own), forced onto the small 3-D parity grids with
+IMGM_TILE3D=1 (on the workloads it runs on levels of 34^3 functions and more): parity with
+the oracle as for the row kernels.  With IMGM_ZM_BLOCKS=1 one block of 8 warps draws every
+task from the level's counter, so each warp runs many tasks and the counter re-arms
+itself between consecutive launches (as on the full-size grids)."""
 import numpy as np
 import pytest
 
@@ -13,7 +16,8 @@ from synthetic import random_grid_vector  # noqa: E402
 pytestmark = pytest.mark.gpu
 EPS = np.finfo(float).eps
 CASES = [dict(n=16, levels=2, depth=1, degree=2), dict(n=8, levels=2, depth=1, degree=1),
-         dict(n=8, levels=2, depth=1, degree=3)]
+         dict(n=8, levels=2, depth=1, degree=3), dict(n=16, levels=2, depth=1, degree=2, blocks=1),
+         dict(n=8, levels=2, depth=1, degree=3, blocks=1)]
 
 
 def dev(v):
@@ -25,11 +29,15 @@ def host(t):
     return t.detach().cpu().numpy()
 
 
-@pytest.fixture(scope="module", params=CASES, ids=[f"p{c['degree']}-n{c['n']}" for c in CASES])
+@pytest.fixture(scope="module", params=CASES,
+                ids=[f"p{c['degree']}-n{c['n']}" + (f"-blocks{c['blocks']}" if "blocks" in c else "") for c in CASES])
 def case(request):
     mp = pytest.MonkeyPatch()
     mp.setenv("IMGM_TILE3D", "1")
-    pr, lay, d, H = oracle_for("spheres20_128_p2", **request.param)
+    ov = dict(request.param)
+    if "blocks" in ov:
+        mp.setenv("IMGM_ZM_BLOCKS", str(ov.pop("blocks")))
+    pr, lay, d, H = oracle_for("spheres20_128_p2", **ov)
     S = solver_for(lib, pr, lay, precision=0)
     Sm = solver_for(lib, pr, lay, precision=1)
     yield d, H, S, Sm
@@ -46,6 +54,8 @@ def test_tile3d_apply_every_level(case):
         full = np.zeros(lev.tb.n_funcs)
         full[lev.active] = x
         y = host(S.apply_operator(dev(full), level=l))
+        y2 = host(S.apply_operator(dev(full), level=l))     # the counter re-armed itself
+        assert np.array_equal(y, y2)
         ref = lev.A @ x
         absA = abs(lev.A).tocsr()
         xmax = absA.sign().multiply(np.abs(x)[None, :]).max(axis=1).toarray().ravel()
@@ -69,3 +79,16 @@ def test_tile3d_vcycle_and_solve(case):
         assert res["status"] == lib.IMGM_OK and res["rel_residual"] <= 1e-8 and res["true_rel_residual"] <= 1e-7
         assert res["iterations"] <= 1.1 * it + 2
         assert mass_rel(host(x)[d.active] - xr, xr, d.M) < 1e-6
+
+
+def test_tile3d_pcg_fixed_iterations(case):
+    """Three CG steps from x0 = 0 (the CG's apply with p^T A p, drawn from the counter, twice
+    per solve step through two solves in a row): the iterates equal the oracle's."""
+    d, H, S, Sm = case
+    ref, it, _ = MG.pcg(d.A, d.b, H.precondition, rtol=0.0, maxit=3)
+    for _ in range(2):
+        x, res, _ = S.pcg_solve(dev(d.to_full(d.b)), rtol=0.0, maxit=3)
+        x = host(x)[d.active]
+        assert res["iterations"] == 3 == it
+        assert mass_rel(x - ref, ref, d.M) < 1e-10
+        assert energy_rel(x - ref, ref, d.A) < 1e-10
