@@ -703,6 +703,79 @@ imgm::DsVcycle ds_params(const imgm_handle* h, int top, const unsigned char* ima
     return V;
 }
 
+// Picks the task shape of the 3-D z-marching operator apply on every level that uses it:
+// rows per lane (1 or 2) and planes per z chunk, by timing the level's residual-mode apply
+// (the V-cycle's) for each candidate on this device and keeping the fastest.  Longer
+// chunks redo fewer halo planes, shorter ones give the warps more tasks; which wins
+// depends on the level's size and on how many SMs the device has.  The same shape then
+// serves the level's other modes (and the CG's apply with p^T A p on the finest level).
+// Levels of both arithmetic types are tuned when the FP32 V-cycle is in use.
+// IMGM_ZM_YT / IMGM_ZM_ZC in the environment bypass it.
+template <typename T>
+cudaError_t tune_zm_level(imgm::DevLevelT<T>& d, const T* x, T* y, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1,
+                          bool verbose, int li) {
+    static const int zcs[] = {4, 6, 8, 11, 16, 22, 32};
+    float best = 0.0f;
+    int best_yt = 0, best_zc = 0;
+    for (int yt = 1; yt <= 2; ++yt)
+        for (int zc : zcs) {
+            if (zc > d.m) continue;
+            imgm::DevLevelT<T> c = d;
+            c.zm_yt = yt;
+            c.zm_zc = zc;
+            cudaError_t e = cudaSuccess;
+            for (int k = 0; k < 2 && e == cudaSuccess; ++k)
+                e = imgm::launch_apply<T>(c, imgm::RESID, x, y, y, nullptr, 0.0, nullptr, s);
+            if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+            for (int k = 0; k < 5 && e == cudaSuccess; ++k)
+                e = imgm::launch_apply<T>(c, imgm::RESID, x, y, y, nullptr, 0.0, nullptr, s);
+            if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float ms = 0.0f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e != cudaSuccess) return e;
+            if (verbose)
+                std::fprintf(stderr, "imgm: level %d (%s) apply, %d rows per lane, %d planes per chunk: %.2f us\n",
+                             li + 1, sizeof(T) == 8 ? "FP64" : "FP32", yt, zc, ms * 200.0f);
+            if (best_yt == 0 || ms < best) {
+                best = ms;
+                best_yt = yt;
+                best_zc = zc;
+            }
+        }
+    d.zm_yt = best_yt;
+    d.zm_zc = best_zc;
+    return cudaSuccess;
+}
+
+cudaError_t autotune_zm(imgm_handle* h) {
+    if (h->dim != 3 || std::getenv("IMGM_ZM_YT") || std::getenv("IMGM_ZM_ZC")) return cudaSuccess;
+    cudaStream_t s = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return e;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const bool verbose = std::getenv("IMGM_VERBOSE") != nullptr;
+    for (int li = 0; li < h->L && e == cudaSuccess; ++li) {
+        LevelDev& L = h->lv[li];
+        if (!imgm::zm_applies(L.d.m)) continue;
+        e = tune_zm_level<double>(L.d, L.t, L.e, s, e0, e1, verbose, li);
+        if (e == cudaSuccess && h->precision >= 1 && L.ft)
+            e = tune_zm_level<float>(L.fd, L.ft, L.fe, s, e0, e1, verbose, li);
+        // the tuning wrote the level's scratch vectors: clear them again
+        if (e == cudaSuccess) e = cudaMemsetAsync(L.t, 0, L.d.N * sizeof(double), s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(L.e, 0, L.d.N * sizeof(double), s);
+        if (e == cudaSuccess && L.fe) e = cudaMemsetAsync(L.fe, 0, L.d.N * sizeof(float), s);
+        if (e == cudaSuccess && L.ft) e = cudaMemsetAsync(L.ft, 0, L.d.N * sizeof(float), s);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaStreamDestroy(s);
+    return e;
+}
+
 // Chooses how many coarse levels of the FP32 V-cycle run in the cluster kernel (none,
 // or levels 1..top for some top) by timing whole V-cycles of each choice on this device.
 cudaError_t autotune_cluster(imgm_handle* h) {
@@ -1044,6 +1117,7 @@ int imgm_setup(const imgm_geometry* geom, const imgm_config* cfg, imgm_handle** 
             g_setup_error = h->err;
             return rc;
         }
+        CK(autotune_zm(h), "apply autotune");
         // the coarse levels of the FP32 V-cycle resident on one cluster, when the device has
         // clusters, the levels fit and the autotuner finds it faster
         if (h->precision == 1 && h->smoother == 0 && h->L >= 2) {

@@ -1565,7 +1565,7 @@ inline int tiles_2d(int m) { return ((m + TX - 1) / TX) * ((m + TY - 1) / TY); }
 // task is one warp's sequential walk, so too few tasks leave the SMs latency-bound),
 // and no shorter than ZM_ZMIN planes.  IMGM_ZM_ZC / IMGM_ZM_ZMIN override the two limits.
 constexpr int ZM_TASKS = 3600, ZM_ZMIN = 4, ZM_ZMAX = 32;
-ZmShape zm_shape(int m, int64_t nb, int P, int yt) {
+ZmShape zm_shape(int m, int64_t nb, int P, int yt, int zc_set) {
     ZmShape s{};
     const int xs = 32 - 2 * P;
     s.sx = (m + xs - 1) / xs;
@@ -1574,6 +1574,7 @@ ZmShape zm_shape(int m, int64_t nb, int P, int yt) {
     if (const char* v = std::getenv("IMGM_ZM_ZMIN")) zmin = std::max(1, std::atoi(v));
     const int want = (ZM_TASKS + s.sx * s.sy - 1) / (s.sx * s.sy);     // chunks for enough tasks
     int zc = std::max(zmin, std::min(zmax, (m + want - 1) / want));
+    if (zc_set > 0) zc = zc_set;
     if (const char* v = std::getenv("IMGM_ZM_ZC")) zc = std::max(1, std::atoi(v));
     const int nz = (m + zc - 1) / zc;
     s.zc = (m + nz - 1) / nz;
@@ -1592,8 +1593,9 @@ bool use_zm_3d(int m) {
 }
 // rows per lane: two on large levels (fewer loads per row), one where the level needs the
 // extra tasks (IMGM_ZM_YT overrides)
-int zm_yt(int m) {
+int zm_yt(int m, int yt_set) {
     if (const char* v = std::getenv("IMGM_ZM_YT")) return std::atoi(v) == 1 ? 1 : 2;
+    if (yt_set == 1 || yt_set == 2) return yt_set;
     return m >= 100 ? 2 : 1;
 }
 int zm_grid(const ZmShape& sh, int cap) {
@@ -1608,7 +1610,7 @@ int zm_grid(const ZmShape& sh, int cap) {
 template <typename T, int P, int YT>
 void launch_zm3d_yt(const DevLevelT<T>& L, int mode, const T* x, const T* rin, T* out, T* xs, T gamma, const int* done,
                     cudaStream_t s) {
-    const ZmShape sh = zm_shape(L.m, L.nb, P, YT);
+    const ZmShape sh = zm_shape(L.m, L.nb, P, YT, L.zm_zc);
     const int g = zm_grid(sh, 2 * num_sms());
     if (mode == APPLY)
         launch_pdl(k_apply_zm3d<T, P, APPLY, false, YT>, g, TPB, 0, s, L, x, rin, out, xs, gamma, done, nullptr, nullptr,
@@ -1625,7 +1627,7 @@ template <typename T, int P>
 cudaError_t launch_zm3d(const DevLevelT<T>& L, int mode, const T* x, const T* rin, T* out, T* xs, T gamma,
                         const int* done, cudaStream_t s) {
     if (L.tile_ctr == nullptr || (L.nb > 0 && L.band_row == nullptr)) return cudaErrorInvalidValue;
-    if (zm_yt(L.m) == 2)
+    if (zm_yt(L.m, L.zm_yt) == 2)
         launch_zm3d_yt<T, P, 2>(L, mode, x, rin, out, xs, gamma, done, s);
     else
         launch_zm3d_yt<T, P, 1>(L, mode, x, rin, out, xs, gamma, done, s);
@@ -1657,6 +1659,7 @@ cudaError_t launch_tile2d(const DevLevelT<T>& L, int mode, const T* x, const T* 
 
 }  // namespace
 
+bool zm_applies(int m) { return use_zm_3d(m); }
 void set_programmatic_launch(bool on) { t_pdl = on; }
 int64_t launch_count() { return t_launches; }
 void add_launches(int64_t k) { t_launches += k; }
@@ -1714,8 +1717,8 @@ cudaError_t launch_apply_pq(const DevLevel& L, const double* p, double* q, doubl
     }
     if (L.dim == 3 && use_zm_3d(L.m)) {
         if (L.tile_ctr == nullptr || (L.nb > 0 && L.band_row == nullptr)) return cudaErrorInvalidValue;
-        const int yt = zm_yt(L.m);
-        const ZmShape sh = zm_shape(L.m, L.nb, L.p, yt);
+        const int yt = zm_yt(L.m, L.zm_yt);
+        const ZmShape sh = zm_shape(L.m, L.nb, L.p, yt, L.zm_zc);
         const int g = zm_grid(sh, std::min(2 * num_sms(), reduction_blocks()));
 #define IMGM_ZM_PQ(PP, YY) \
     launch_pdl(k_apply_zm3d<double, PP, APPLY, true, YY>, g, TPB, 0, s, L, p, nullptr, q, nullptr, 0.0, &st->done, \

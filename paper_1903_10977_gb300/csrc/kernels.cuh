@@ -46,6 +46,9 @@ struct DevLevelT {
     // (m^2 m_c and m m_c^2 doubles; nullptr where the direct kernels run)
     double* xs1 = nullptr;
     double* xs2 = nullptr;
+    // task shape of the 3-D z-marching apply (rows per lane, planes per chunk), picked by the
+    // setup-time autotuner; 0 = the built-in rule
+    int zm_yt = 0, zm_zc = 0;
 };
 using DevLevel = DevLevelT<double>;
 
@@ -71,6 +74,10 @@ struct PcgState {
 constexpr int FCG_MAX = 8;
 
 enum ApplyMode { APPLY = 0, RESID = 1, RESID_SMOOTH = 2 };
+
+// whether a 3-D level of m functions per direction takes the z-marching apply (whose task
+// shape, DevLevelT::zm_yt / zm_zc, the setup autotuner picks)
+bool zm_applies(int m);
 
 // y = A x (APPLY), out = rin - A x (RESID), or out = rin - A x followed by
 // xs += gamma * dinv .* out (RESID_SMOOTH).  `out` may alias `rin`.

@@ -18,8 +18,11 @@ PROBLEMS = [
     ("discs10_512_p2", {"n": 128, "levels": 4}, {"precision": 1}),
     ("discs10_512_p3", {"n": 64, "levels": 3}, {"precision": 0, "smoother": 1}),
     ("spheres20_128_p2", {"n": 16, "levels": 2, "depth": 1}, {"precision": 1}),
+    ("spheres20_128_p2", {"n": 16, "levels": 3, "depth": 1, "degree": 1}, {"precision": 1}),
+    ("spheres20_128_p2", {"n": 8, "levels": 2, "depth": 1, "degree": 3}, {"precision": 0}),
 ]
-RHS_PER_PROBLEM = [1, 3, 2, 1, 2]
+# 3-D members with up to eight right-hand sides (clones of one problem), 2-D ones with 1-3
+RHS_PER_PROBLEM = [1, 3, 2, 1, 8, 4, 2]
 
 
 def dev(v):

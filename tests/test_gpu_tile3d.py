@@ -3,7 +3,9 @@ p^T A p, stored rows as tasks of their own), forced onto the small 3-D parity gr
 IMGM_TILE3D=1 (on the workloads it runs on levels of 34^3 functions and more): parity with
 the oracle as for the row kernels.  With IMGM_ZM_BLOCKS=1 one block of 8 warps draws every
 task from the level's counter, so each warp runs many tasks and the counter re-arms
-itself between consecutive launches (as on the full-size grids)."""
+itself between consecutive launches (as on the full-size grids).  The 32^3 case has a
+level of 34^3 functions, whose restriction and prolongation take the sum-factorised
+three-pass kernels (the levels of the smaller cases take the direct ones)."""
 import numpy as np
 import pytest
 
@@ -17,7 +19,7 @@ pytestmark = pytest.mark.gpu
 EPS = np.finfo(float).eps
 CASES = [dict(n=16, levels=2, depth=1, degree=2), dict(n=8, levels=2, depth=1, degree=1),
          dict(n=8, levels=2, depth=1, degree=3), dict(n=16, levels=2, depth=1, degree=2, blocks=1),
-         dict(n=8, levels=2, depth=1, degree=3, blocks=1)]
+         dict(n=8, levels=2, depth=1, degree=3, blocks=1), dict(n=32, levels=3, depth=0, degree=2)]
 
 
 def dev(v):
@@ -92,3 +94,30 @@ def test_tile3d_pcg_fixed_iterations(case):
         assert res["iterations"] == 3 == it
         assert mass_rel(x - ref, ref, d.M) < 1e-10
         assert energy_rel(x - ref, ref, d.A) < 1e-10
+
+
+def test_tile3d_restrict_and_prolong(case):
+    """R r and R^T x_c on every level, entry by entry within (4 n eps) ||R_i||_1 max|x| with
+    n = (p + 2)^3 (the bound of the direct kernels; the three-pass sums are shorter)."""
+    d, H, S, Sm = case
+    for l in range(H.L, 1, -1):
+        fine, coarse = H.lv[l], H.lv[l - 1]
+        R = fine.R
+        n_terms = (d.p + 2) ** 3
+        r = random_grid_vector(fine.active.size, 20 + l)
+        full = np.zeros(fine.tb.n_funcs)
+        full[fine.active] = r
+        rc = host(S.restrict(dev(full), level=l))
+        ref = R @ r
+        absR = abs(R).tocsr()
+        bound = 4 * n_terms * EPS * np.asarray(absR.sum(axis=1)).ravel() * np.abs(r).max() + 1e-300
+        assert np.max(np.abs(rc[coarse.active] - ref) / bound) <= 1.0, l
+        assert not np.any(np.delete(rc, coarse.active))
+        xc = random_grid_vector(coarse.active.size, 30 + l)
+        fullc = np.zeros(coarse.tb.n_funcs)
+        fullc[coarse.active] = xc
+        e = host(S.prolong(dev(fullc), level=l))
+        ref = R.T @ xc
+        bound = 4 * n_terms * EPS * np.asarray(absR.T.sum(axis=1)).ravel() * np.abs(xc).max() + 1e-300
+        assert np.max(np.abs(e[fine.active] - ref) / bound) <= 1.0, l
+        assert not np.any(np.delete(e, fine.active))
