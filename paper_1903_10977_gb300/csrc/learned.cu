@@ -153,10 +153,12 @@ __global__ void __launch_bounds__(CTPB) k_conv(const TIN* __restrict__ x, const 
 // same layout (16-byte rows per output channel).
 //
 // Per output plane: the CTA waits for the previous plane's MMAs (an mbarrier the MMA
-// commit arrives on), loads the next input plane into the slot they no longer read, and
-// one thread issues the plane's 27 MMAs into one of two accumulators while the four warps
-// read the previous plane's accumulator (tcgen05.ld, one warp per 32 rows), apply the
-// ReLU and store bf16.  Every wait is bounded: after about a second the CTA sets *err and
+// commit arrives on), starts the copy of the input plane two ahead into the ring slot
+// those MMAs no longer read (cp.async, so that it overlaps this plane's work; four slots
+// hold planes z - 1 .. z + 2), waits for the plane one ahead, and one thread issues the
+// plane's 27 MMAs into one of two accumulators while the four warps read the previous
+// plane's accumulator (tcgen05.ld, one warp per 32 rows) and store it through the
+// layer's epilogue.  Every wait is bounded: after about a second the CTA sets *err and
 // stops (the host reports the error), never hanging the GPU.
 constexpr int TC_PX = 8, TC_PY = 16;                 // output patch of one plane: 128 voxels
 constexpr int TC_RX = TC_PX + 2, TC_RY = TC_PY + 2;  // its input region with the halo
@@ -166,10 +168,9 @@ constexpr int TC_SLOT = 2 * TC_GROUP;                // one input plane: 5,760 b
 constexpr int TC_WBYTES = 27 * 512;                  // B operands of the 27 taps
 constexpr int TC_ZC = 16;                            // output planes per CTA
 constexpr int TC_THREADS = 128;
-// shared memory: weights, ring, two mbarriers and the TMEM address, then a margin that
-// keeps every operand view of the ring inside the allocation even if the leading and
-// stride offsets of a descriptor were read the other way round (16 row groups x 2,880 B)
-constexpr int TC_SMEM = TC_WBYTES + 3 * TC_SLOT + 64 + 40960;
+constexpr int TC_SLOTS = 4;                          // ring slots: planes z - 1 .. z + 2
+// shared memory: weights, ring, two mbarriers and the TMEM address
+constexpr int TC_SMEM = TC_WBYTES + TC_SLOTS * TC_SLOT + 64;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -207,13 +208,24 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
     }
 }
 
-__global__ void __launch_bounds__(TC_THREADS) k_conv16_tc(const uint16_t* __restrict__ x,
-                                                          const uint16_t* __restrict__ w, uint16_t* __restrict__ y,
-                                                          int nx, int ny, int nz, int* err) {
+// Instances: the forward 16 -> 16 layer (bf16 input, ReLU, bf16 output), the forward
+// 16 -> 1 layer (CO = 1: the one output channel is column 0 of a 16-column accumulator whose
+// other weights are zero; FP64 and/or FP32 output on the mask), and the 16 -> 16 layer's
+// input gradient (FP32 output gradient rounded to bf16 as it enters shared memory, the
+// transposed weights, FP32 result where the layer's input gate is positive).
+template <typename TIN, int CI, int CO, int EPI>
+__global__ void __launch_bounds__(TC_THREADS) k_conv16_tc(const TIN* __restrict__ x, const uint16_t* __restrict__ w,
+                                                          const uint16_t* __restrict__ gate,
+                                                          const uint8_t* __restrict__ mask, uint16_t* __restrict__ yb,
+                                                          float* __restrict__ yf, double* __restrict__ yd, int nx,
+                                                          int ny, int nz, int* err) {
+    static_assert(CO == 16 || CO == 1, "16 output channels or one");
+    static_assert(CI == 16 || (CI == 1 && sizeof(TIN) == 2), "16 input channels, or one bf16 channel");
+    constexpr bool ASYNC = CI == 16 && sizeof(TIN) == 2;       // bf16 planes copied by cp.async
     extern __shared__ __align__(1024) unsigned char tsm[];
     unsigned char* wsm = tsm;                                    // [27][2 groups][16 out][8 in] bf16
-    unsigned char* ring = tsm + TC_WBYTES;                       // [3 slots][2 groups][180 voxels][8] bf16
-    uint64_t* bars = reinterpret_cast<uint64_t*>(ring + 3 * TC_SLOT);
+    unsigned char* ring = tsm + TC_WBYTES;                       // [4 slots][2 groups][180 voxels][8] bf16
+    uint64_t* bars = reinterpret_cast<uint64_t*>(ring + TC_SLOTS * TC_SLOT);
     uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 2);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int npx = (nx + TC_PX - 1) / TC_PX, npy = (ny + TC_PY - 1) / TC_PY;
@@ -224,7 +236,10 @@ __global__ void __launch_bounds__(TC_THREADS) k_conv16_tc(const uint16_t* __rest
     uint16_t* wsm16 = reinterpret_cast<uint16_t*>(wsm);
     for (int q = tid; q < 27 * 256; q += TC_THREADS) {
         const int t = q >> 8, o = (q >> 4) & 15, i = q & 15;
-        wsm16[t * 256 + (i >> 3) * 128 + o * 8 + (i & 7)] = w[q];
+        // layouts [tap][out][in]: 16 x 16, 1 x 16 (CO = 1) or 16 x 1 (CI = 1), zero-padded
+        const uint16_t v = CI == 1 ? (i == 0 ? w[t * 16 + o] : (uint16_t)0)
+                                   : (CO == 16 ? w[q] : (o == 0 ? w[t * 16 + i] : (uint16_t)0));
+        wsm16[t * 256 + (i >> 3) * 128 + o * 8 + (i & 7)] = v;
     }
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bars[0])) : "memory");
@@ -236,21 +251,47 @@ __global__ void __launch_bounds__(TC_THREADS) k_conv16_tc(const uint16_t* __rest
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    // one input plane into its slot: 180 voxels x 2 groups of 16 bytes
+    // one input plane into its slot: 180 voxels x 2 groups of 16 bytes (zero outside the
+    // grid); bf16 16-channel planes by cp.async (a group per plane; the caller commits and
+    // waits), the others with plain loads and stores
     auto load_plane = [&](int zp) {
-        unsigned char* slot = ring + ((zp - z0 + 3) % 3) * TC_SLOT;
+        unsigned char* slot = ring + ((zp - z0 + 1) & (TC_SLOTS - 1)) * TC_SLOT;
         for (int q = tid; q < 2 * TC_RV; q += TC_THREADS) {
             const int vox = q >> 1, g = q & 1;
             const int gx = x0 - 1 + vox % TC_RX, gy = y0 - 1 + vox / TC_RX;
-            uint4 val = make_uint4(0u, 0u, 0u, 0u);
-            if ((unsigned)gx < (unsigned)nx && (unsigned)gy < (unsigned)ny && (unsigned)zp < (unsigned)nz)
-                val = *reinterpret_cast<const uint4*>(x + ((int64_t)gx + (int64_t)nx * (gy + (int64_t)ny * zp)) * 16 +
-                                                      g * 8);
-            *reinterpret_cast<uint4*>(slot + g * TC_GROUP + vox * 16) = val;
+            const bool in = (unsigned)gx < (unsigned)nx && (unsigned)gy < (unsigned)ny && (unsigned)zp < (unsigned)nz;
+            const int64_t v = in ? (int64_t)gx + (int64_t)nx * (gy + (int64_t)ny * zp) : 0;
+            unsigned char* dst = slot + g * TC_GROUP + vox * 16;
+            if constexpr (ASYNC) {
+                const TIN* src = x + v * 16 + g * 8;
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src),
+                             "r"(in ? 16 : 0)
+                             : "memory");
+            } else {
+                uint4 val = make_uint4(0u, 0u, 0u, 0u);
+                if (in) {
+                    if constexpr (CI == 1) {
+                        if (g == 0) val.x = (uint32_t)x[v];          // channel 0 of 16, the rest zero
+                    } else if constexpr (sizeof(TIN) == 2) {
+                        val = *reinterpret_cast<const uint4*>(x + v * 16 + g * 8);
+                    } else {                              // FP32 channels, rounded to bf16 here
+                        const float4 a = *reinterpret_cast<const float4*>(x + v * 16 + g * 8);
+                        const float4 b = *reinterpret_cast<const float4*>(x + v * 16 + g * 8 + 4);
+                        val = make_uint4(bf_bits(a.x) | (bf_bits(a.y) << 16), bf_bits(a.z) | (bf_bits(a.w) << 16),
+                                         bf_bits(b.x) | (bf_bits(b.y) << 16), bf_bits(b.z) | (bf_bits(b.w) << 16));
+                    }
+                }
+                *reinterpret_cast<uint4*>(dst) = val;
+            }
         }
+        if constexpr (ASYNC) asm volatile("cp.async.commit_group;" ::: "memory");
     };
     load_plane(z0 - 1);
     load_plane(z0);
+    if constexpr (ASYNC) {
+        load_plane(z0 + 1);
+        asm volatile("cp.async.wait_group 1;" ::: "memory");   // planes z0 - 1 and z0 are in
+    }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -271,14 +312,32 @@ __global__ void __launch_bounds__(TC_THREADS) k_conv16_tc(const uint16_t* __rest
         const int row = warp * 32 + lane;
         const int gx = x0 + row % TC_PX, gy = y0 + row / TC_PX, gz = z0 + k;
         if (gx < nx && gy < ny) {
-            uint32_t pk[8];
+            const int64_t vox = (int64_t)gx + (int64_t)nx * (gy + (int64_t)ny * gz);
+            if constexpr (EPI == EPI_RELU) {
+                uint32_t pk[8];
 #pragma unroll
-            for (int c = 0; c < 8; ++c)
-                pk[c] = bf_bits(fmaxf(__uint_as_float(v[2 * c]), 0.f)) |
-                        (bf_bits(fmaxf(__uint_as_float(v[2 * c + 1]), 0.f)) << 16);
-            uint4* out = reinterpret_cast<uint4*>(y + ((int64_t)gx + (int64_t)nx * (gy + (int64_t)ny * gz)) * 16);
-            out[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-            out[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+                for (int c = 0; c < 8; ++c)
+                    pk[c] = bf_bits(fmaxf(__uint_as_float(v[2 * c]), 0.f)) |
+                            (bf_bits(fmaxf(__uint_as_float(v[2 * c + 1]), 0.f)) << 16);
+                uint4* out = reinterpret_cast<uint4*>(yb + vox * 16);
+                out[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                out[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+            } else if constexpr (EPI == EPI_GATE) {
+                float gv[16];
+                load_channels<16, uint16_t>(gate, vox, gv);
+                float4* out = reinterpret_cast<float4*>(yf + vox * 16);
+#pragma unroll
+                for (int c = 0; c < 4; ++c)
+                    out[c] = make_float4(gv[4 * c] > 0.f ? __uint_as_float(v[4 * c]) : 0.f,
+                                         gv[4 * c + 1] > 0.f ? __uint_as_float(v[4 * c + 1]) : 0.f,
+                                         gv[4 * c + 2] > 0.f ? __uint_as_float(v[4 * c + 2]) : 0.f,
+                                         gv[4 * c + 3] > 0.f ? __uint_as_float(v[4 * c + 3]) : 0.f);
+            } else {
+                const bool on = !mask || mask[vox];
+                const float o0 = __uint_as_float(v[0]);
+                if (yd) yd[vox] = on ? (double)o0 : 0.0;
+                if (yf) yf[vox] = on ? o0 : 0.f;
+            }
         }
     };
 
@@ -288,7 +347,12 @@ __global__ void __launch_bounds__(TC_THREADS) k_conv16_tc(const uint16_t* __rest
         const int z = z0 + k;
         if (k > 0) ok = __syncthreads_and(mbar_wait(smem_u32(&bars[(k - 1) & 1]), ((k - 1) >> 1) & 1));
         if (!ok) break;
-        load_plane(z + 1);                            // the slot of plane z - 2, no longer read
+        if constexpr (ASYNC) {
+            load_plane(z + 2);                        // the slot of plane z - 2, no longer read
+            asm volatile("cp.async.wait_group 1;" ::: "memory");   // plane z + 1 is in
+        } else {
+            load_plane(z + 1);                        // the slot of plane z - 3, no longer read
+        }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();
@@ -298,7 +362,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_conv16_tc(const uint16_t* __rest
 #pragma unroll 1
             for (int t = 0; t < 27; ++t) {
                 const int dz = t / 9 - 1, dy = (t / 3) % 3 - 1, dx = t % 3 - 1;
-                const uint32_t a = rbase + ((z + dz - z0 + 3) % 3) * TC_SLOT + 16 * ((dx + 1) + TC_RX * (dy + 1));
+                const uint32_t a = rbase + ((z + dz - z0 + 1) & (TC_SLOTS - 1)) * TC_SLOT + 16 * ((dx + 1) + TC_RX * (dy + 1));
                 const uint64_t ad = tc_desc(a, TC_GROUP, 16 * TC_RX);
                 const uint64_t bd = tc_desc(wbase + t * 512, 256, 128);
                 const uint32_t acc = t > 0 ? 1u : 0u;
@@ -325,6 +389,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_conv16_tc(const uint16_t* __rest
         }
     }
     if (!ok && tid == 0) atomicExch(err, 1);
+    if constexpr (ASYNC) asm volatile("cp.async.wait_group 0;" ::: "memory");   // no copy outlives the CTA
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0)
@@ -547,10 +612,23 @@ bool net_tensor_cores() {
     }();
     static bool attr = false;
     if (on && !attr) {
-        cudaFuncSetAttribute(k_conv16_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+        cudaFuncSetAttribute(k_conv16_tc<uint16_t, 1, NET_C, EPI_RELU>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             TC_SMEM);
+        cudaFuncSetAttribute(k_conv16_tc<uint16_t, NET_C, NET_C, EPI_RELU>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             TC_SMEM);
+        cudaFuncSetAttribute(k_conv16_tc<uint16_t, NET_C, 1, EPI_OUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+        cudaFuncSetAttribute(k_conv16_tc<float, NET_C, NET_C, EPI_GATE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             TC_SMEM);
         attr = true;
     }
     return on;
+}
+
+// CTAs of a tensor-core convolution over the grid of ws (0 if out of range)
+unsigned tc_grid(const NetWorkspace& ws) {
+    const int64_t g = (int64_t)((ws.nx + TC_PX - 1) / TC_PX) * ((ws.ny + TC_PY - 1) / TC_PY) *
+                      ((ws.nz + TC_ZC - 1) / TC_ZC);
+    return (g > 0 && g <= 2147483647LL) ? (unsigned)g : 0u;
 }
 
 int grid_for(int64_t work, int per_block, int max_per_sm) {
@@ -612,19 +690,23 @@ cudaError_t net_forward(const uint16_t* wb, NetWorkspace& ws, const double* in, 
     if (nvox == 0) return cudaSuccess;
     const int gc = grid_for(nvox, CTPB, 16);
     k_pack<<<elementwise_grid(nvox), RTPB, 0, s>>>(nvox, in, mask, in_scale, ws.a0);
-    k_conv<1, NET_C, uint16_t, EPI_RELU><<<gc, CTPB, 0, s>>>(ws.a0, wb, nullptr, nullptr, ws.a1, nullptr, nullptr,
-                                                             ws.nx, ws.ny, ws.nz);
     if (net_tensor_cores()) {
-        const int64_t g = (int64_t)((ws.nx + TC_PX - 1) / TC_PX) * ((ws.ny + TC_PY - 1) / TC_PY) *
-                          ((ws.nz + TC_ZC - 1) / TC_ZC);
-        if (g > 2147483647LL) return cudaErrorInvalidValue;
-        k_conv16_tc<<<(unsigned)g, TC_THREADS, TC_SMEM, s>>>(ws.a1, wb + NET_OFF2, ws.a2, ws.nx, ws.ny, ws.nz, ws.err);
+        const unsigned g = tc_grid(ws);
+        if (g == 0) return cudaErrorInvalidValue;
+        k_conv16_tc<uint16_t, 1, NET_C, EPI_RELU><<<g, TC_THREADS, TC_SMEM, s>>>(
+            ws.a0, wb, nullptr, nullptr, ws.a1, nullptr, nullptr, ws.nx, ws.ny, ws.nz, ws.err);
+        k_conv16_tc<uint16_t, NET_C, NET_C, EPI_RELU><<<g, TC_THREADS, TC_SMEM, s>>>(
+            ws.a1, wb + NET_OFF2, nullptr, nullptr, ws.a2, nullptr, nullptr, ws.nx, ws.ny, ws.nz, ws.err);
+        k_conv16_tc<uint16_t, NET_C, 1, EPI_OUT><<<g, TC_THREADS, TC_SMEM, s>>>(
+            ws.a2, wb + NET_OFF3, nullptr, mask, nullptr, out32, out64, ws.nx, ws.ny, ws.nz, ws.err);
     } else {
+        k_conv<1, NET_C, uint16_t, EPI_RELU><<<gc, CTPB, 0, s>>>(ws.a0, wb, nullptr, nullptr, ws.a1, nullptr, nullptr,
+                                                                 ws.nx, ws.ny, ws.nz);
         k_conv<NET_C, NET_C, uint16_t, EPI_RELU><<<gc, CTPB, 0, s>>>(ws.a1, wb + NET_OFF2, nullptr, nullptr, ws.a2,
                                                                      nullptr, nullptr, ws.nx, ws.ny, ws.nz);
+        k_conv<NET_C, 1, uint16_t, EPI_OUT><<<gc, CTPB, 0, s>>>(ws.a2, wb + NET_OFF3, nullptr, mask, nullptr, out32,
+                                                                out64, ws.nx, ws.ny, ws.nz);
     }
-    k_conv<NET_C, 1, uint16_t, EPI_OUT><<<gc, CTPB, 0, s>>>(ws.a2, wb + NET_OFF3, nullptr, mask, nullptr, out32, out64,
-                                                            ws.nx, ws.ny, ws.nz);
     add_launches(4);
     return cudaGetLastError();
 }
@@ -642,8 +724,15 @@ cudaError_t net_backward(const uint16_t* wbt, NetWorkspace& ws, const double* ta
                                                           nullptr, ws.nx, ws.ny, ws.nz);
     // layer 2: dW2 from (d2, a1); d1 = (W2^T d2) where a1 > 0
     k_wgrad<NET_C, NET_C><<<grid_for(nvox, 32, 4), WTPB, 0, s>>>(ws.d2, ws.a1, grad + NET_OFF2, ws.nx, ws.ny, ws.nz);
-    k_conv<NET_C, NET_C, float, EPI_GATE><<<gc, CTPB, 0, s>>>(ws.d2, wbt + NET_OFF2, ws.a1, nullptr, nullptr, ws.d1,
-                                                              nullptr, ws.nx, ws.ny, ws.nz);
+    if (net_tensor_cores()) {
+        const unsigned g = tc_grid(ws);
+        if (g == 0) return cudaErrorInvalidValue;
+        k_conv16_tc<float, NET_C, NET_C, EPI_GATE><<<g, TC_THREADS, TC_SMEM, s>>>(
+            ws.d2, wbt + NET_OFF2, ws.a1, nullptr, nullptr, ws.d1, nullptr, ws.nx, ws.ny, ws.nz, ws.err);
+    } else {
+        k_conv<NET_C, NET_C, float, EPI_GATE><<<gc, CTPB, 0, s>>>(ws.d2, wbt + NET_OFF2, ws.a1, nullptr, nullptr,
+                                                                  ws.d1, nullptr, ws.nx, ws.ny, ws.nz);
+    }
     // layer 1: dW1 from (d1, a0)
     k_wgrad<1, NET_C><<<grid_for(nvox, (WTPB / NET_C) * 32, 4), WTPB, 0, s>>>(ws.d1, ws.a0, grad, ws.nx, ws.ny,
                                                                               ws.nz);

@@ -74,12 +74,16 @@ def test_batch_matches_oracle(batch):
 
 
 def test_batch_matches_single_solves(batch):
-    """The same context solved alone (its own graph) reaches the same iterate."""
+    """The same context solved alone (its own graph) converges in the same number of
+    iterations (to within one) to the same solution, to the accuracy of the stopping test:
+    the Schwarz scatter's atomic adds and the 3-D apply's dynamic task order make the
+    rounding of two runs differ, so the iterates are not bitwise equal (1e-7 in
+    L2(Omega_h), as for converged solutions in the single-solve parity tests)."""
     entries, bs, xs, results = batch
     for (d, H, ctx, b), bd, x, res in zip(entries, bs, xs, results):
         xs1, r1, _ = ctx.pcg_solve(bd, rtol=1e-8, maxit=1000)
         assert abs(r1["iterations"] - res["iterations"]) <= 1
-        assert mass_rel(host(xs1)[d.active] - x[d.active], x[d.active], d.M) < 1e-8
+        assert mass_rel(host(xs1)[d.active] - x[d.active], x[d.active], d.M) < 1e-7
 
 
 def test_clone_outlives_its_source():
