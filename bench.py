@@ -38,8 +38,15 @@ WORKLOADS = ("spheres20_128_p2", "discs10_512_p2", "discs10_512_p1", "discs10_51
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one finest-level FP64 apply
 # launch with p^T A p, per workload, from one ncu capture of the current kernel (null when
 # none has been taken since the kernel last changed)
-APPLY_TRAFFIC_BYTES = {}
-APPLY_TRAFFIC_SOURCE = {}
+APPLY_TRAFFIC_BYTES = {
+    # dram__bytes_read.sum 238.9 MB + dram__bytes_write.sum 18.6 MB (mean of two launches)
+    "poisson3d-128x128x128-20spheres-bspline-p2-5levels-depth2-nitsche": 2.575e8,
+}
+APPLY_TRAFFIC_SOURCE = {
+    "poisson3d-128x128x128-20spheres-bspline-p2-5levels-depth2-nitsche":
+        "ncu dram__bytes_read.sum + dram__bytes_write.sum of this kernel in this launch configuration "
+        "(profiles/k_apply_zm3d_fp64_poisson3d_128_p2.md)",
+}
 
 
 def workload_name(pr) -> str:
@@ -604,7 +611,7 @@ def run_ours(args, rank, world, local_rank):
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                      "traffic": APPLY_TRAFFIC_BYTES.get(wl),
                      "traffic_source": APPLY_TRAFFIC_SOURCE.get(wl, "no capture of the current kernel"),
-                     "kernel": ("k_apply_tile2d<double>" if pr.dim == 2 else "k_apply_tile3d<double>")
+                     "kernel": ("k_apply_tile2d<double>" if pr.dim == 2 else "k_apply_zm3d<double>")
                                + " (finest-level FP64 operator apply, imgm_apply_operator)",
                      "peak_source": "derived: " + FP64_PEAK_NOTE, "flops_per_launch": flops,
                      "launch_ms": apply_ms,

@@ -427,14 +427,20 @@ struct ZmShape {
     unsigned int ntensor, ntotal;        // tensor tasks; all tasks (tensor + stored)
 };
 
+// blocks per SM the z-marching apply is compiled for: two in FP64 (its FP64 pipe is the
+// bound), four in FP32 (latency-bound: more resident warps hide the plane loads)
+template <typename T>
+constexpr int zm_blocks_per_sm() { return sizeof(T) == 4 ? 4 : 2; }
+
 template <typename T, int P, int MODE, bool DOT, int YT>
-__global__ void __launch_bounds__(TPB) k_apply_zm3d(DevLevelT<T> L, const T* __restrict__ x, const T* rin, T* out,
+__global__ void __launch_bounds__(TPB, zm_blocks_per_sm<T>()) k_apply_zm3d(DevLevelT<T> L, const T* __restrict__ x, const T* rin, T* out,
                                                     T* __restrict__ xs, T gamma, const int* done, double* partial,
                                                     PcgState* st, ZmShape sh) {
     pdl_begin();
     if (done && *done) return;
     constexpr int W = 2 * P + 1, XS = 32 - 2 * P, NV = YT + 2 * P;
     constexpr bool SC = sizeof(T) == 4;              // FP32 path: Jacobi-scaled variables
+    extern __shared__ __align__(16) float zm_stage[];   // FP32: [warp][W planes][x, s][NV][32]
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const int m = L.m;
@@ -462,13 +468,33 @@ __global__ void __launch_bounds__(TPB) k_apply_zm3d(DevLevelT<T> L, const T* __r
                 kx[o] = xin ? ro(L.K1 + (int64_t)gx * W + o) : T(0);
                 mx[o] = xin ? ro(L.M1 + (int64_t)gx * W + o) : T(0);
             }
+            // Away from the open-knot ends the 1-D rows are symmetric (c[o] = c[2P - o]): the sums
+            // along x and y then pair the neighbours first, 2P adds and 3(P+1) FMA instead of
+            // 3(2P+1) FMA along x, P adds and 2(P+1) FMA instead of 2(2P+1) along y.  The test
+            // is per warp (x) and per row (y), so no lane diverges.
+            bool symx = true;
+#pragma unroll
+            for (int o = 0; o < P; ++o) symx = symx && kx[o] == kx[2 * P - o] && mx[o] == mx[2 * P - o];
+            symx = __all_sync(FULL, symx);
+            bool symy[YT];
+#pragma unroll
+            for (int j = 0; j < YT; ++j) {
+                const int gy = y0 + j;
+                bool sy = gy < m;
+#pragma unroll
+                for (int o = 0; o < P; ++o)
+                    sy = sy && ro(L.K1 + (int64_t)gy * W + o) == ro(L.K1 + (int64_t)gy * W + 2 * P - o) &&
+                         ro(L.M1 + (int64_t)gy * W + o) == ro(L.M1 + (int64_t)gy * W + 2 * P - o);
+                symy[j] = sy;
+            }
             T ring[YT][W];
 #pragma unroll
             for (int j = 0; j < YT; ++j)
 #pragma unroll
                 for (int q = 0; q < W; ++q) ring[j][q] = T(0);
             const int nplanes = (zend - zc0) + 2 * P;
-            // the column segment of input plane zp (zero outside the grid)
+            // FP64: the column segment of input plane zp in registers, the next plane's loads
+            // issued before the current plane's arithmetic (zero outside the grid)
             auto load_plane = [&](int zp, T* v) {
                 const bool zin = (unsigned)zp < (unsigned)m;
 #pragma unroll
@@ -476,40 +502,107 @@ __global__ void __launch_bounds__(TPB) k_apply_zm3d(DevLevelT<T> L, const T* __r
                     const int gy = y0 - P + i;
                     const bool in = zin && xin && (unsigned)gy < (unsigned)m;
                     const int64_t g = (int64_t)zp * mm + (int64_t)gy * m + gx;
-                    v[i] = in ? (SC ? x[g] * ro(L.s + g) : x[g]) : T(0);
+                    v[i] = in ? x[g] : T(0);
+                }
+            };
+            // FP32 (latency-bound, not ALU-bound): the segments of x and of the Jacobi scale s of
+            // the next W - 1 planes are in flight at once, copied by cp.async into this warp's ring
+            // of W plane buffers in shared memory.  A lane copies and later reads only its own
+            // column, so its own cp.async.wait_group orders them and no warp barrier is needed.
+            float* stg = nullptr;
+            if constexpr (SC) stg = zm_stage + (threadIdx.x >> 5) * (W * 2 * NV * 32);
+            auto stage_plane = [&](int k) {
+                if constexpr (SC) {
+                    const int zp = zc0 - P + k;
+                    const bool zin = k < nplanes && (unsigned)zp < (unsigned)m;
+                    float* bx = stg + (k % W) * (2 * NV * 32);
+#pragma unroll
+                    for (int i = 0; i < NV; ++i) {
+                        const int gy = y0 - P + i;
+                        const bool in = zin && xin && (unsigned)gy < (unsigned)m;
+                        const int64_t g = in ? (int64_t)zp * mm + (int64_t)gy * m + gx : 0;
+                        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(
+                                         (uint32_t)__cvta_generic_to_shared(bx + i * 32 + lane)),
+                                     "l"(x + g), "r"(in ? 4 : 0)
+                                     : "memory");
+                        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(
+                                         (uint32_t)__cvta_generic_to_shared(bx + (NV + i) * 32 + lane)),
+                                     "l"(L.s + g), "r"(in ? 4 : 0)
+                                     : "memory");
+                    }
+                    asm volatile("cp.async.commit_group;" ::: "memory");
                 }
             };
             T v[NV];
-            load_plane(zc0 - P, v);
+            if constexpr (SC) {
+#pragma unroll
+                for (int k = 0; k < W - 1; ++k) stage_plane(k);
+            } else {
+                load_plane(zc0 - P, v);
+            }
             for (int base = 0; base < nplanes; base += W) {
 #pragma unroll
                 for (int u = 0; u < W; ++u) {
                     const int k = base + u;
                     if (k >= nplanes) break;
                     const int zp = zc0 - P + k;                      // input plane
-                    // the next plane's loads go out before this plane's arithmetic
                     T vn[NV];
-                    if (k + 1 < nplanes) load_plane(zp + 1, vn);
+                    if constexpr (SC) {
+                        stage_plane(k + W - 1);                      // into the buffer of plane k - 1
+                        asm volatile("cp.async.wait_group %0;" ::"n"(W - 1) : "memory");   // plane k is in
+                        const float* bx = stg + (k % W) * (2 * NV * 32);
+#pragma unroll
+                        for (int i = 0; i < NV; ++i) v[i] = bx[i * 32 + lane] * bx[(NV + i) * 32 + lane];
+                    } else {
+                        // the next plane's loads go out before this plane's arithmetic
+                        if (k + 1 < nplanes) load_plane(zp + 1, vn);
+                    }
                     T a[YT], b[YT];
 #pragma unroll
                     for (int j = 0; j < YT; ++j) {
                         const int gy = y0 + j;
+                        const T* __restrict__ My = L.M1 + (int64_t)gy * W;
+                        const T* __restrict__ Ky = L.K1 + (int64_t)gy * W;
                         T my = T(0), ky = T(0);
-                        if (gy < m) {
+                        if (symy[j]) {
+                            my = ro(My + P) * v[j + P];
+                            ky = ro(Ky + P) * v[j + P];
+#pragma unroll
+                            for (int o = 0; o < P; ++o) {
+                                const T pv = v[j + o] + v[j + 2 * P - o];
+                                my = fmaT(ro(My + o), pv, my);
+                                ky = fmaT(ro(Ky + o), pv, ky);
+                            }
+                        } else if (gy < m) {
 #pragma unroll
                             for (int o = 0; o < W; ++o) {
-                                my = fmaT(ro(L.M1 + (int64_t)gy * W + o), v[j + o], my);
-                                ky = fmaT(ro(L.K1 + (int64_t)gy * W + o), v[j + o], ky);
+                                my = fmaT(ro(My + o), v[j + o], my);
+                                ky = fmaT(ro(Ky + o), v[j + o], ky);
                             }
                         }
                         T aa = T(0), bb = T(0);
+                        if (symx) {
+                            aa = mx[P] * my;
+                            bb = fmaT(kx[P], my, mx[P] * ky);
 #pragma unroll
-                        for (int o = 0; o < W; ++o) {
-                            const T mo = __shfl_sync(FULL, my, (lane - P + o) & 31);
-                            const T ko = __shfl_sync(FULL, ky, (lane - P + o) & 31);
-                            aa = fmaT(mx[o], mo, aa);
-                            bb = fmaT(mx[o], ko, bb);
-                            bb = fmaT(kx[o], mo, bb);
+                            for (int o = 0; o < P; ++o) {
+                                const T sm = __shfl_sync(FULL, my, (lane - P + o) & 31) +
+                                             __shfl_sync(FULL, my, (lane + P - o) & 31);
+                                const T sk = __shfl_sync(FULL, ky, (lane - P + o) & 31) +
+                                             __shfl_sync(FULL, ky, (lane + P - o) & 31);
+                                aa = fmaT(mx[o], sm, aa);
+                                bb = fmaT(mx[o], sk, bb);
+                                bb = fmaT(kx[o], sm, bb);
+                            }
+                        } else {
+#pragma unroll
+                            for (int o = 0; o < W; ++o) {
+                                const T mo = __shfl_sync(FULL, my, (lane - P + o) & 31);
+                                const T ko = __shfl_sync(FULL, ky, (lane - P + o) & 31);
+                                aa = fmaT(mx[o], mo, aa);
+                                bb = fmaT(mx[o], ko, bb);
+                                bb = fmaT(kx[o], mo, bb);
+                            }
                         }
                         a[j] = aa;
                         b[j] = bb;
@@ -556,10 +649,13 @@ __global__ void __launch_bounds__(TPB) k_apply_zm3d(DevLevelT<T> L, const T* __r
                         }
                         r = T(0);
                     }
+                    if constexpr (!SC) {
 #pragma unroll
-                    for (int i = 0; i < NV; ++i) v[i] = vn[i];
+                        for (int i = 0; i < NV; ++i) v[i] = vn[i];
+                    }
                 }
             }
+            if constexpr (SC) asm volatile("cp.async.wait_group 0;" ::: "memory");   // the ring is free again
         } else {
             // ---------------- stored rows: 32 consecutive stored row ids, one per lane
             const int64_t k = (int64_t)(t - sh.ntensor) * 32 + lane;
@@ -1607,20 +1703,37 @@ int zm_grid(const ZmShape& sh, int cap) {
     return (int)std::max<int64_t>(g, 1);
 }
 
+// dynamic shared memory of the z-marching apply: the FP32 instances' plane rings
+template <typename T, int P, int YT>
+constexpr size_t zm_smem() {
+    return sizeof(T) == 4 ? (size_t)(TPB / 32) * (2 * P + 1) * 2 * (YT + 2 * P) * 32 * sizeof(float) : 0;
+}
+
 template <typename T, int P, int YT>
 void launch_zm3d_yt(const DevLevelT<T>& L, int mode, const T* x, const T* rin, T* out, T* xs, T gamma, const int* done,
                     cudaStream_t s) {
     const ZmShape sh = zm_shape(L.m, L.nb, P, YT, L.zm_zc);
-    const int g = zm_grid(sh, 2 * num_sms());
+    const int g = zm_grid(sh, zm_blocks_per_sm<T>() * num_sms());
+    constexpr size_t smem = zm_smem<T, P, YT>();
+    if (smem > 48 * 1024) {
+        static bool attr = false;                      // opted in once per instantiation
+        if (!attr) {
+            cudaFuncSetAttribute(k_apply_zm3d<T, P, APPLY, false, YT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            cudaFuncSetAttribute(k_apply_zm3d<T, P, RESID, false, YT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            cudaFuncSetAttribute(k_apply_zm3d<T, P, RESID_SMOOTH, false, YT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
+            attr = true;
+        }
+    }
     if (mode == APPLY)
-        launch_pdl(k_apply_zm3d<T, P, APPLY, false, YT>, g, TPB, 0, s, L, x, rin, out, xs, gamma, done, nullptr, nullptr,
-                   sh);
-    else if (mode == RESID)
-        launch_pdl(k_apply_zm3d<T, P, RESID, false, YT>, g, TPB, 0, s, L, x, rin, out, xs, gamma, done, nullptr, nullptr,
-                   sh);
-    else
-        launch_pdl(k_apply_zm3d<T, P, RESID_SMOOTH, false, YT>, g, TPB, 0, s, L, x, rin, out, xs, gamma, done, nullptr,
+        launch_pdl(k_apply_zm3d<T, P, APPLY, false, YT>, g, TPB, smem, s, L, x, rin, out, xs, gamma, done, nullptr,
                    nullptr, sh);
+    else if (mode == RESID)
+        launch_pdl(k_apply_zm3d<T, P, RESID, false, YT>, g, TPB, smem, s, L, x, rin, out, xs, gamma, done, nullptr,
+                   nullptr, sh);
+    else
+        launch_pdl(k_apply_zm3d<T, P, RESID_SMOOTH, false, YT>, g, TPB, smem, s, L, x, rin, out, xs, gamma, done,
+                   nullptr, nullptr, sh);
 }
 
 template <typename T, int P>
