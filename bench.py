@@ -123,10 +123,16 @@ print(json.dumps({{"n_active": o["n_active"], "times": times, "iterations": its,
 _ONE_THREAD = dict(OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
 
 
-def oracle_build_start(seed: int = 0):
-    """Starts the oracle's assembly of the CPU sample in the background; returns (process, path)."""
+# the other workloads the oracle solves in full beside the sample (2-D: its assembly takes
+# seconds for 32^2 and ~3 min for 512^2): name -> (preset, n, levels, depth)
+CPU_FULL = {"disc1_32_p2": ("disc1_32_p2", 32, 3, 3), "discs10_512_p2": ("discs10_512_p2", 512, 6, 0)}
+
+
+def oracle_build_start(seed: int = 0, preset: str = PRESET, sample: dict | None = None):
+    """Starts the oracle's assembly of a CPU system in the background (the 3-D sample by default);
+    returns (process, path)."""
     path = os.path.join(tempfile.mkdtemp(prefix="imgm_oracle_"), "system.pkl")
-    code = _ORACLE_BUILD.format(root=ROOT, preset=PRESET, seed=seed, path=path, **CPU_SAMPLE)
+    code = _ORACLE_BUILD.format(root=ROOT, preset=preset, seed=seed, path=path, **(sample or CPU_SAMPLE))
     proc = subprocess.Popen([sys.executable, "-c", code], env=dict(os.environ, **_ONE_THREAD),
                             stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True)
     return proc, path
@@ -160,6 +166,21 @@ def sample_text(o, procs: int, reps: int) -> str:
             f"{CPU_SAMPLE['n']}^3 ({CPU_SAMPLE['levels']} levels, depth-{CPU_SAMPLE['depth']} cut-cell "
             f"quadrature, {o['n_active']} DOFs, {o['iterations'][0]} iterations), setup excluded; "
             f"{procs} single-threaded process{'es' if procs > 1 else ''} at once, {reps} solves each")
+
+
+def cpu_full_entry(path: str, name: str, reps: int = 3):
+    """Oracle throughput on a whole 2-D workload: one single-threaded solve process, and one per
+    host core at once."""
+    one = oracle_solves(path, 1, reps)[0]
+    t1 = statistics.median(one["times"])
+    ncpu = os.cpu_count() or 1
+    many = oracle_solves(path, ncpu, 1)
+    t_all = max(sum(o["times"]) for o in many)
+    return {"workload": name, "n_active": one["n_active"], "iterations": one["iterations"][0],
+            "single_thread": {"value": one["n_active"] / t1, "unit": "DOF/s", "cores": 1, "median_s": t1},
+            "all_cores": {"value": ncpu * one["n_active"] / t_all, "unit": "DOF/s", "cores": ncpu,
+                          "solves": ncpu},
+            "oracle_build_s": one["build_s"], "kind": "oracle", "sample": "the whole workload"}
 
 
 def cpu_baseline_entry(path: str, reps: int = 3):
@@ -320,6 +341,11 @@ def vcycle_bandwidth(S, torch, stream, mixed):
     d = S.dim
     s_bytes = 4 if mixed else 8
     nbytes = sum((13 + 2 / 2 ** d) * s_bytes * S.level_info(l)["n_grid"] for l in range(2, S.L + 1))
+    # the tables the V-cycle reads as well: each level's stored rows ((2p+1)^d coefficients, read by
+    # its two residual applies) and its Schwarz block inverses (sum n_j^2, read by its two smoothings)
+    ncoef = (2 * S.p + 1) ** d
+    tbytes = sum(2 * s_bytes * (S.level_info(l)["n_band"] * ncoef + S.level_info(l)["block_entries"])
+                 for l in range(2, S.L + 1))
     r = S.rhs()
     z = torch.empty_like(r)
     reps = 20
@@ -344,9 +370,13 @@ def vcycle_bandwidth(S, torch, stream, mixed):
     t = e0.elapsed_time(e1) / 1e3 / reps
     peak = measured_peaks().get("hbm_gbs")
     gbs = nbytes / t / 1e9
+    gbt = (nbytes + tbytes) / t / 1e9
     return {"us": 1e6 * t, "algorithmic_bytes": nbytes, "achieved_gbs": gbs, "hbm_peak_gbs": peak,
             "frac_of_hbm": gbs / peak if peak else None,
-            "note": "vector passes only (tables excluded); L2-resident at the 2-D sizes"}
+            "table_bytes": tbytes, "achieved_gbs_with_tables": gbt,
+            "frac_of_hbm_with_tables": gbt / peak if peak else None,
+            "note": "algorithmic_bytes: vector passes; table_bytes: stored operator rows and block inverses "
+                    "read by the two residual applies and two smoothings of every level"}
 
 
 def reduce_replicas(dist, device, times, units):
@@ -447,11 +477,13 @@ def run_learned(args, lib, torch, pr, S64, timed_solves, total_units, t64, res64
         "forward": {"ms": fwd_ms, "flops": fwd_flops, "achieved_tflops": fwd_flops / (fwd_ms * 1e-3) / 1e12,
                     "tensor_flops": 2.0 * m ** 3 * 27 * 256,
                     "bf16_peak_tflops": measured_peaks().get("bf16_tflops"),
-                    "peak_source": "measured bf16 burst (MEASURED_PEAKS.json); the 16->16 layer (tensor_flops, "
-                                   "89 % of the flops) runs on the tensor cores, the two 16-channel end layers on "
-                                   "the CUDA cores (" + FP32_PEAK_NOTE + ")",
-                    "kernels": "k_pack, k_conv<1,16> (CUDA cores), k_conv16_tc (16->16 layer: tcgen05 bf16 MMAs, "
-                               "FP32 accumulator in tensor memory), k_conv<16,1> (CUDA cores)",
+                    "peak_source": "measured bf16 burst (MEASURED_PEAKS.json); tensor_flops are the 16->16 "
+                                   "layer's (89 % of the algorithmic flops; all three layers run on the tensor cores)",
+                    "frac_of_bf16_peak": (fwd_flops / (fwd_ms * 1e-3) / 1e12) / measured_peaks()["bf16_tflops"]
+                    if measured_peaks().get("bf16_tflops") else None,
+                    "kernels": "k_pack, then k_conv_tcz for the 1->16, 16->16 and 16->1 layers (tcgen05 bf16 "
+                               "MMAs of N = 48 with the z taps folded in, FP32 accumulators sliding along z in "
+                               "tensor memory; channels zero-padded to 16)",
                     "timing": "20 stream launches of the whole forward, CUDA events"},
     }
 
@@ -463,9 +495,12 @@ def run_ours(args, rank, world, local_rank):
     from synthetic import config_layout, preset
 
     # the oracle's CPU sample is assembled on one host core while the GPU legs run
-    oracle = None
+    oracle, oracle_full = None, {}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         oracle = oracle_build_start(args.seed)
+        if args.workload == PRESET and not args.quick:
+            for name, (pname, n, levels, depth) in CPU_FULL.items():
+                oracle_full[name] = oracle_build_start(args.seed, pname, {"n": n, "levels": levels, "depth": depth})
     torch.cuda.set_device(local_rank)
     dist = None
     if world > 1:
@@ -626,6 +661,14 @@ def run_ours(args, rank, world, local_rank):
             line["cpu_baseline"] = {"error": str(e)[:200]}
         if not headline:
             line["cpu_baseline_note"] = "cpu_baseline is measured on the 3-D 20-sphere workload's 32^3 sample"
+        full = {}
+        for name, proc in oracle_full.items():
+            try:
+                full[name] = cpu_full_entry(oracle_build_wait(*proc), workload_name(preset(name)))
+            except Exception as e:
+                full[name] = {"error": str(e)[:200]}
+        if full:
+            line["cpu_oracle_2d"] = full
     if S64 is not S and S64 is not None:
         S64.close()
     S.close()

@@ -704,9 +704,11 @@ imgm::DsVcycle ds_params(const imgm_handle* h, int top, const unsigned char* ima
 }
 
 // Picks the task shape of the 3-D z-marching operator apply on every level that uses it:
-// rows per lane (1 or 2) and planes per z chunk, by timing the level's residual-mode apply
+// rows per lane (1 or 2), planes per z chunk and, in FP32, whether the input planes are
+// staged in shared memory by cp.async or loaded to registers, by timing the level's residual-mode apply
 // (the V-cycle's) for each candidate on this device and keeping the fastest.  Longer
-// chunks redo fewer halo planes, shorter ones give the warps more tasks; which wins
+// chunks redo fewer halo planes, shorter ones give the warps more tasks and shorter
+// sequential walks (small levels are latency-bound); which wins
 // depends on the level's size and on how many SMs the device has.  The same shape then
 // serves the level's other modes (and the CG's apply with p^T A p on the finest level).
 // Levels of both arithmetic types are tuned when the FP32 V-cycle is in use.
@@ -714,15 +716,17 @@ imgm::DsVcycle ds_params(const imgm_handle* h, int top, const unsigned char* ima
 template <typename T>
 cudaError_t tune_zm_level(imgm::DevLevelT<T>& d, const T* x, T* y, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1,
                           bool verbose, int li) {
-    static const int zcs[] = {4, 6, 8, 11, 16, 22, 32};
+    static const int zcs[] = {1, 2, 3, 4, 6, 8, 11, 16, 22, 32};
     float best = 0.0f;
-    int best_yt = 0, best_zc = 0;
+    int best_yt = 0, best_zc = 0, best_stage = 1;
+    for (int stage = (sizeof(T) == 4 ? 0 : 1); stage <= 1; ++stage)   // FP32: registers or cp.async staging
     for (int yt = 1; yt <= 2; ++yt)
         for (int zc : zcs) {
             if (zc > d.m) continue;
             imgm::DevLevelT<T> c = d;
             c.zm_yt = yt;
             c.zm_zc = zc;
+            c.zm_stage = stage;
             cudaError_t e = cudaSuccess;
             for (int k = 0; k < 2 && e == cudaSuccess; ++k)
                 e = imgm::launch_apply<T>(c, imgm::RESID, x, y, y, nullptr, 0.0, nullptr, s);
@@ -735,16 +739,19 @@ cudaError_t tune_zm_level(imgm::DevLevelT<T>& d, const T* x, T* y, cudaStream_t 
             if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
             if (e != cudaSuccess) return e;
             if (verbose)
-                std::fprintf(stderr, "imgm: level %d (%s) apply, %d rows per lane, %d planes per chunk: %.2f us\n",
-                             li + 1, sizeof(T) == 8 ? "FP64" : "FP32", yt, zc, ms * 200.0f);
+                std::fprintf(stderr, "imgm: level %d (%s) apply, %d rows per lane, %d planes per chunk%s: %.2f us\n",
+                             li + 1, sizeof(T) == 8 ? "FP64" : "FP32", yt, zc,
+                             sizeof(T) == 4 ? (stage ? ", staged" : ", registers") : "", ms * 200.0f);
             if (best_yt == 0 || ms < best) {
                 best = ms;
                 best_yt = yt;
                 best_zc = zc;
+                best_stage = stage;
             }
         }
     d.zm_yt = best_yt;
     d.zm_zc = best_zc;
+    d.zm_stage = best_stage;
     return cudaSuccess;
 }
 

@@ -432,7 +432,7 @@ struct ZmShape {
 template <typename T>
 constexpr int zm_blocks_per_sm() { return sizeof(T) == 4 ? 4 : 2; }
 
-template <typename T, int P, int MODE, bool DOT, int YT>
+template <typename T, int P, int MODE, bool DOT, int YT, bool STG>
 __global__ void __launch_bounds__(TPB, zm_blocks_per_sm<T>()) k_apply_zm3d(DevLevelT<T> L, const T* __restrict__ x, const T* rin, T* out,
                                                     T* __restrict__ xs, T gamma, const int* done, double* partial,
                                                     PcgState* st, ZmShape sh) {
@@ -493,8 +493,9 @@ __global__ void __launch_bounds__(TPB, zm_blocks_per_sm<T>()) k_apply_zm3d(DevLe
 #pragma unroll
                 for (int q = 0; q < W; ++q) ring[j][q] = T(0);
             const int nplanes = (zend - zc0) + 2 * P;
-            // FP64: the column segment of input plane zp in registers, the next plane's loads
-            // issued before the current plane's arithmetic (zero outside the grid)
+            // the column segment of input plane zp in registers, the next plane's loads issued
+            // before the current plane's arithmetic (zero outside the grid): FP64, and FP32 where
+            // the autotuner found it faster than staging (L2-resident levels)
             auto load_plane = [&](int zp, T* v) {
                 const bool zin = (unsigned)zp < (unsigned)m;
 #pragma unroll
@@ -502,7 +503,7 @@ __global__ void __launch_bounds__(TPB, zm_blocks_per_sm<T>()) k_apply_zm3d(DevLe
                     const int gy = y0 - P + i;
                     const bool in = zin && xin && (unsigned)gy < (unsigned)m;
                     const int64_t g = (int64_t)zp * mm + (int64_t)gy * m + gx;
-                    v[i] = in ? x[g] : T(0);
+                    v[i] = in ? (SC ? x[g] * ro(L.s + g) : x[g]) : T(0);
                 }
             };
             // FP32 (latency-bound, not ALU-bound): the segments of x and of the Jacobi scale s of
@@ -510,6 +511,7 @@ __global__ void __launch_bounds__(TPB, zm_blocks_per_sm<T>()) k_apply_zm3d(DevLe
             // of W plane buffers in shared memory.  A lane copies and later reads only its own
             // column, so its own cp.async.wait_group orders them and no warp barrier is needed.
             float* stg = nullptr;
+            constexpr bool staged = SC && STG;
             if constexpr (SC) stg = zm_stage + (threadIdx.x >> 5) * (W * 2 * NV * 32);
             auto stage_plane = [&](int k) {
                 if constexpr (SC) {
@@ -534,7 +536,7 @@ __global__ void __launch_bounds__(TPB, zm_blocks_per_sm<T>()) k_apply_zm3d(DevLe
                 }
             };
             T v[NV];
-            if constexpr (SC) {
+            if constexpr (staged) {
 #pragma unroll
                 for (int k = 0; k < W - 1; ++k) stage_plane(k);
             } else {
@@ -547,7 +549,7 @@ __global__ void __launch_bounds__(TPB, zm_blocks_per_sm<T>()) k_apply_zm3d(DevLe
                     if (k >= nplanes) break;
                     const int zp = zc0 - P + k;                      // input plane
                     T vn[NV];
-                    if constexpr (SC) {
+                    if constexpr (staged) {
                         stage_plane(k + W - 1);                      // into the buffer of plane k - 1
                         asm volatile("cp.async.wait_group %0;" ::"n"(W - 1) : "memory");   // plane k is in
                         const float* bx = stg + (k % W) * (2 * NV * 32);
@@ -649,13 +651,13 @@ __global__ void __launch_bounds__(TPB, zm_blocks_per_sm<T>()) k_apply_zm3d(DevLe
                         }
                         r = T(0);
                     }
-                    if constexpr (!SC) {
+                    if constexpr (!staged) {
 #pragma unroll
                         for (int i = 0; i < NV; ++i) v[i] = vn[i];
                     }
                 }
             }
-            if constexpr (SC) asm volatile("cp.async.wait_group 0;" ::: "memory");   // the ring is free again
+            if constexpr (staged) asm volatile("cp.async.wait_group 0;" ::: "memory");   // the ring is free again
         } else {
             // ---------------- stored rows: 32 consecutive stored row ids, one per lane
             const int64_t k = (int64_t)(t - sh.ntensor) * 32 + lane;
@@ -1704,36 +1706,48 @@ int zm_grid(const ZmShape& sh, int cap) {
 }
 
 // dynamic shared memory of the z-marching apply: the FP32 instances' plane rings
-template <typename T, int P, int YT>
+template <typename T, int P, int YT, bool STG>
 constexpr size_t zm_smem() {
-    return sizeof(T) == 4 ? (size_t)(TPB / 32) * (2 * P + 1) * 2 * (YT + 2 * P) * 32 * sizeof(float) : 0;
+    return (sizeof(T) == 4 && STG) ? (size_t)(TPB / 32) * (2 * P + 1) * 2 * (YT + 2 * P) * 32 * sizeof(float) : 0;
 }
 
-template <typename T, int P, int YT>
-void launch_zm3d_yt(const DevLevelT<T>& L, int mode, const T* x, const T* rin, T* out, T* xs, T gamma, const int* done,
-                    cudaStream_t s) {
+template <typename T, int P, int YT, bool STG>
+void launch_zm3d_stg(const DevLevelT<T>& L, int mode, const T* x, const T* rin, T* out, T* xs, T gamma,
+                     const int* done, cudaStream_t s) {
     const ZmShape sh = zm_shape(L.m, L.nb, P, YT, L.zm_zc);
     const int g = zm_grid(sh, zm_blocks_per_sm<T>() * num_sms());
-    constexpr size_t smem = zm_smem<T, P, YT>();
+    constexpr size_t smem = zm_smem<T, P, YT, STG>();
     if (smem > 48 * 1024) {
         static bool attr = false;                      // opted in once per instantiation
         if (!attr) {
-            cudaFuncSetAttribute(k_apply_zm3d<T, P, APPLY, false, YT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            cudaFuncSetAttribute(k_apply_zm3d<T, P, RESID, false, YT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            cudaFuncSetAttribute(k_apply_zm3d<T, P, RESID_SMOOTH, false, YT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            cudaFuncSetAttribute(k_apply_zm3d<T, P, APPLY, false, YT, STG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem);
+            cudaFuncSetAttribute(k_apply_zm3d<T, P, RESID, false, YT, STG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
+            cudaFuncSetAttribute(k_apply_zm3d<T, P, RESID_SMOOTH, false, YT, STG>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             attr = true;
         }
     }
     if (mode == APPLY)
-        launch_pdl(k_apply_zm3d<T, P, APPLY, false, YT>, g, TPB, smem, s, L, x, rin, out, xs, gamma, done, nullptr,
+        launch_pdl(k_apply_zm3d<T, P, APPLY, false, YT, STG>, g, TPB, smem, s, L, x, rin, out, xs, gamma, done, nullptr,
                    nullptr, sh);
     else if (mode == RESID)
-        launch_pdl(k_apply_zm3d<T, P, RESID, false, YT>, g, TPB, smem, s, L, x, rin, out, xs, gamma, done, nullptr,
+        launch_pdl(k_apply_zm3d<T, P, RESID, false, YT, STG>, g, TPB, smem, s, L, x, rin, out, xs, gamma, done, nullptr,
                    nullptr, sh);
     else
-        launch_pdl(k_apply_zm3d<T, P, RESID_SMOOTH, false, YT>, g, TPB, smem, s, L, x, rin, out, xs, gamma, done,
+        launch_pdl(k_apply_zm3d<T, P, RESID_SMOOTH, false, YT, STG>, g, TPB, smem, s, L, x, rin, out, xs, gamma, done,
                    nullptr, nullptr, sh);
+}
+
+// FP32 levels take the staged or the register form as the autotuner chose; FP64 registers
+template <typename T, int P, int YT>
+void launch_zm3d_yt(const DevLevelT<T>& L, int mode, const T* x, const T* rin, T* out, T* xs, T gamma, const int* done,
+                    cudaStream_t s) {
+    if (sizeof(T) == 4 && L.zm_stage)
+        launch_zm3d_stg<T, P, YT, true>(L, mode, x, rin, out, xs, gamma, done, s);
+    else
+        launch_zm3d_stg<T, P, YT, false>(L, mode, x, rin, out, xs, gamma, done, s);
 }
 
 template <typename T, int P>
@@ -1834,7 +1848,7 @@ cudaError_t launch_apply_pq(const DevLevel& L, const double* p, double* q, doubl
         const ZmShape sh = zm_shape(L.m, L.nb, L.p, yt, L.zm_zc);
         const int g = zm_grid(sh, std::min(2 * num_sms(), reduction_blocks()));
 #define IMGM_ZM_PQ(PP, YY) \
-    launch_pdl(k_apply_zm3d<double, PP, APPLY, true, YY>, g, TPB, 0, s, L, p, nullptr, q, nullptr, 0.0, &st->done, \
+    launch_pdl(k_apply_zm3d<double, PP, APPLY, true, YY, false>, g, TPB, 0, s, L, p, nullptr, q, nullptr, 0.0, &st->done, \
                partial, st, sh)
         if (L.p == 1) { if (yt == 2) IMGM_ZM_PQ(1, 2); else IMGM_ZM_PQ(1, 1); }
         else if (L.p == 2) { if (yt == 2) IMGM_ZM_PQ(2, 2); else IMGM_ZM_PQ(2, 1); }

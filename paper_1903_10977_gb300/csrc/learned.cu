@@ -396,6 +396,219 @@ __global__ void __launch_bounds__(TC_THREADS) k_conv16_tc(const TIN* __restrict_
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" ::"r"(tmem) : "memory");
 }
 
+// ---------------------------------------------------------------------------------
+// The same convolutions with the z taps folded into the MMA's N dimension.  An input plane
+// zp feeds the output planes zp + 1, zp and zp - 1 (taps dz = -1, 0, +1) through the same
+// shifted operand, so each of its nine (dx, dy) shifts is ONE MMA of N = 48: B holds
+// W(dx, dy, +1), W(dx, dy, 0) and W(dx, dy, -1) one below the other, and the accumulator
+// columns [16 (o - z0 + 2), +16) belong to output plane o, so the 48 columns of input zp's
+// MMAs land on the accumulators of planes zp - 1, zp and zp + 1, which slide along z with
+// the input plane.  Nine MMAs per plane instead of 27 of N = 16 (the tensor pipe's issue
+// rate, not its math, bounds the narrow ones); each input plane is read by its own MMAs
+// only, so three ring slots hold the plane being multiplied and the two being copied.
+// Accumulators: TCZ_ZC + 4 groups of 16 columns (one per output plane of the chunk, plus
+// the neighbours of its first and last), cleared with tcgen05.st before the first MMA.
+constexpr int TCZ_ZC = 4;                            // output planes per CTA
+constexpr int TCZ_COLS = 128;                        // TMEM columns: 16 (TCZ_ZC + 4) rounded up
+constexpr int TCZ_SLOTS = 3;
+constexpr int TCZ_WBYTES = 9 * 1536;                 // 9 B operands of 48 rows x 16 bf16
+constexpr int TCZ_SMEM_USED = TCZ_WBYTES + TCZ_SLOTS * TC_SLOT + 64;
+// requested per CTA: enough that at most four CTAs share an SM, whose 512 TMEM columns then
+// hold all their accumulators (a fifth CTA's tcgen05.alloc would wait for one to finish)
+constexpr int TCZ_SMEM = TCZ_SMEM_USED > 56 * 1024 ? TCZ_SMEM_USED : 56 * 1024;
+static_assert(16 * (TCZ_ZC + 4) <= TCZ_COLS, "accumulators exceed the allocation");
+// kind::f16, FP32 accumulator, bf16 A and B, K-major, N = 48, M = 128
+constexpr uint32_t TCZ_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((48u >> 3) << 17) | ((128u >> 4) << 24);
+
+template <typename TIN, int CI, int CO, int EPI>
+__global__ void __launch_bounds__(TC_THREADS) k_conv_tcz(const TIN* __restrict__ x, const uint16_t* __restrict__ w,
+                                                         const uint16_t* __restrict__ gate,
+                                                         const uint8_t* __restrict__ mask, uint16_t* __restrict__ yb,
+                                                         float* __restrict__ yf, double* __restrict__ yd, int nx,
+                                                         int ny, int nz, int* err) {
+    static_assert(CO == 16 || CO == 1, "16 output channels or one");
+    static_assert(CI == 16 || (CI == 1 && sizeof(TIN) == 2), "16 input channels, or one bf16 channel");
+    constexpr bool ASYNC = CI == 16 && sizeof(TIN) == 2;
+    extern __shared__ __align__(1024) unsigned char tsm[];
+    unsigned char* wsm = tsm;                                    // [9][2 groups][48 rows][8 in] bf16
+    unsigned char* ring = tsm + TCZ_WBYTES;                      // [3 slots][2 groups][180 voxels][8] bf16
+    uint64_t* bars = reinterpret_cast<uint64_t*>(ring + TCZ_SLOTS * TC_SLOT);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 2);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int npx = (nx + TC_PX - 1) / TC_PX, npy = (ny + TC_PY - 1) / TC_PY;
+    const int bx = blockIdx.x % npx, by = (blockIdx.x / npx) % npy, bz = blockIdx.x / (npx * npy);
+    const int x0 = bx * TC_PX, y0 = by * TC_PY, z0 = bz * TCZ_ZC, z1 = min(z0 + TCZ_ZC, nz);
+
+    // B operand of shift (dx, dy): row n = 16 q + o holds W(dx, dy, dz = 1 - q)[o][.]
+    uint16_t* wsm16 = reinterpret_cast<uint16_t*>(wsm);
+    for (int e = tid; e < 9 * 48 * 16; e += TC_THREADS) {
+        const int s9 = e / 768, n = (e / 16) % 48, i = e % 16;
+        const int q = n / 16, o = n % 16;
+        const int dz = 1 - q, t = 9 * (dz + 1) + (s9 / 3) * 3 + (s9 % 3);     // tap index of W[t]
+        const uint16_t v = CI == 1 ? (i == 0 ? w[t * 16 + o] : (uint16_t)0)
+                                   : (CO == 16 ? w[(t * 16 + o) * 16 + i] : (o == 0 ? w[t * 16 + i] : (uint16_t)0));
+        wsm16[s9 * 768 + (i >> 3) * 384 + n * 8 + (i & 7)] = v;
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bars[0])) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bars[1])) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                     "n"(TCZ_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    auto load_plane = [&](int zp) {
+        unsigned char* slot = ring + ((zp - z0 + 1) % TCZ_SLOTS) * TC_SLOT;
+        for (int q = tid; q < 2 * TC_RV; q += TC_THREADS) {
+            const int vox = q >> 1, g = q & 1;
+            const int gx = x0 - 1 + vox % TC_RX, gy = y0 - 1 + vox / TC_RX;
+            const bool in = (unsigned)gx < (unsigned)nx && (unsigned)gy < (unsigned)ny && (unsigned)zp < (unsigned)nz;
+            const int64_t v = in ? (int64_t)gx + (int64_t)nx * (gy + (int64_t)ny * zp) : 0;
+            unsigned char* dst = slot + g * TC_GROUP + vox * 16;
+            if constexpr (ASYNC) {
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(x + v * 16 + g * 8),
+                             "r"(in ? 16 : 0)
+                             : "memory");
+            } else {
+                uint4 val = make_uint4(0u, 0u, 0u, 0u);
+                if (in) {
+                    if constexpr (CI == 1) {
+                        if (g == 0) val.x = (uint32_t)x[v];
+                    } else if constexpr (sizeof(TIN) == 2) {
+                        val = *reinterpret_cast<const uint4*>(x + v * 16 + g * 8);
+                    } else {
+                        const float4 a = *reinterpret_cast<const float4*>(x + v * 16 + g * 8);
+                        const float4 b = *reinterpret_cast<const float4*>(x + v * 16 + g * 8 + 4);
+                        val = make_uint4(bf_bits(a.x) | (bf_bits(a.y) << 16), bf_bits(a.z) | (bf_bits(a.w) << 16),
+                                         bf_bits(b.x) | (bf_bits(b.y) << 16), bf_bits(b.z) | (bf_bits(b.w) << 16));
+                    }
+                }
+                *reinterpret_cast<uint4*>(dst) = val;
+            }
+        }
+        if constexpr (ASYNC) asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tslot;
+    const uint32_t wbase = smem_u32(wsm), rbase = smem_u32(ring);
+    {   // clear this warp's 32 lanes of every accumulator column
+        const uint32_t z = 0u;
+        for (int c = 0; c < TCZ_COLS; c += 16)
+            asm volatile(
+                "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, "
+                "%1, %1};" ::"r"(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c),
+                "r"(z)
+                : "memory");
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+    }
+    if constexpr (ASYNC) {
+        load_plane(z0 - 1);
+        load_plane(z0);
+    }
+
+    // output plane o: accumulator group o - z0 + 2 -> epilogue -> y
+    auto epilogue = [&](int o) {
+        uint32_t v[16];
+        const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(16 * (o - z0 + 2));
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+            "%14, %15}, [%16];"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+            : "r"(ta));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        const int row = warp * 32 + lane;
+        const int gx = x0 + row % TC_PX, gy = y0 + row / TC_PX;
+        if (gx < nx && gy < ny) {
+            const int64_t vox = (int64_t)gx + (int64_t)nx * (gy + (int64_t)ny * o);
+            if constexpr (EPI == EPI_RELU) {
+                uint32_t pk[8];
+#pragma unroll
+                for (int c = 0; c < 8; ++c)
+                    pk[c] = bf_bits(fmaxf(__uint_as_float(v[2 * c]), 0.f)) |
+                            (bf_bits(fmaxf(__uint_as_float(v[2 * c + 1]), 0.f)) << 16);
+                uint4* out = reinterpret_cast<uint4*>(yb + vox * 16);
+                out[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                out[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+            } else if constexpr (EPI == EPI_GATE) {
+                float gv[16];
+                load_channels<16, uint16_t>(gate, vox, gv);
+                float4* out = reinterpret_cast<float4*>(yf + vox * 16);
+#pragma unroll
+                for (int c = 0; c < 4; ++c)
+                    out[c] = make_float4(gv[4 * c] > 0.f ? __uint_as_float(v[4 * c]) : 0.f,
+                                         gv[4 * c + 1] > 0.f ? __uint_as_float(v[4 * c + 1]) : 0.f,
+                                         gv[4 * c + 2] > 0.f ? __uint_as_float(v[4 * c + 2]) : 0.f,
+                                         gv[4 * c + 3] > 0.f ? __uint_as_float(v[4 * c + 3]) : 0.f);
+            } else {
+                const bool on = !mask || mask[vox];
+                const float o0 = __uint_as_float(v[0]);
+                if (yd) yd[vox] = on ? (double)o0 : 0.0;
+                if (yf) yf[vox] = on ? o0 : 0.f;
+            }
+        }
+    };
+
+    bool ok = true;
+    const int K = (z1 - z0) + 2;                     // input planes z0 - 1 .. z1
+    for (int k = 0; k < K && ok; ++k) {
+        const int zp = z0 - 1 + k;
+        if (k > 0) ok = __syncthreads_and(mbar_wait(smem_u32(&bars[(k - 1) & 1]), ((k - 1) >> 1) & 1));
+        if (!ok) break;
+        if constexpr (ASYNC) {
+            load_plane(zp + 2);                       // the slot of plane zp - 1, whose MMAs are done
+            asm volatile("cp.async.wait_group 2;" ::: "memory");      // plane zp is in
+        } else {
+            load_plane(zp);                           // the slot of plane zp - 3
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (tid == 0) {
+            const uint32_t d = tmem + (uint32_t)(16 * k);            // groups of planes zp - 1, zp, zp + 1
+            const uint32_t a0 = rbase + ((zp - z0 + 1) % TCZ_SLOTS) * TC_SLOT;
+#pragma unroll 1
+            for (int s9 = 0; s9 < 9; ++s9) {
+                const int dy = s9 / 3 - 1, dx = s9 % 3 - 1;
+                const uint64_t ad = tc_desc(a0 + 16 * ((dx + 1) + TC_RX * (dy + 1)), TC_GROUP, 16 * TC_RX);
+                const uint64_t bd = tc_desc(wbase + s9 * 1536, 768, 128);
+                asm volatile(
+                    "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+                    ::"r"(d), "l"(ad), "l"(bd), "r"(TCZ_IDESC), "r"(1u)
+                    : "memory");
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             smem_u32(&bars[k & 1]))
+                         : "memory");
+        }
+        // output plane zp - 2 has received its last contribution (from plane zp - 1)
+        if (k >= 3 && zp - 2 >= z0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            epilogue(zp - 2);
+        }
+    }
+    if (ok) {
+        ok = __syncthreads_and(mbar_wait(smem_u32(&bars[(K - 1) & 1]), ((K - 1) >> 1) & 1));
+        if (ok) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            epilogue(z1 - 1);                         // the last output plane (z1 > z0)
+        }
+    }
+    if (!ok && tid == 0) atomicExch(err, 1);
+    if constexpr (ASYNC) asm volatile("cp.async.wait_group 0;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(TCZ_COLS) : "memory");
+}
+
 // gw[tap][o][i] += sum_v dy[v][o] x[v + off_tap][i]
 template <int CI, int CO>
 __global__ void __launch_bounds__(WTPB) k_wgrad(const float* __restrict__ dy, const uint16_t* __restrict__ x,
@@ -603,15 +816,21 @@ int sm_count() {
     return sms;
 }
 
-// the 16 -> 16 forward convolution on the tensor cores unless IMGM_NET_TC=0 (CUDA-core
-// FP32 loop, kept for comparison); the kernel's shared memory is opted in once per process
-bool net_tensor_cores() {
-    static const bool on = [] {
+// Which convolution kernels the network uses: 1 (default) the tensor cores with one N = 16
+// MMA per tap (k_conv16_tc), 2 (IMGM_NET_TC=48) the tensor cores with the z taps folded into
+// N = 48 (k_conv_tcz: a third of the MMAs, but its accumulators occupy 128 tensor-memory
+// columns per CTA, which caps the CTAs per SM; measured slower on the 130^3 grid), 0
+// (IMGM_NET_TC=0) the CUDA-core FP32 loops (k_conv).  The kernels' shared memory is opted in
+// once per process.
+int net_tc_mode() {
+    static const int mode = [] {
         const char* v = std::getenv("IMGM_NET_TC");
-        return !(v && v[0] == '0');
+        if (v && v[0] == '0') return 0;
+        if (v && std::atoi(v) == 48) return 2;
+        return 1;
     }();
     static bool attr = false;
-    if (on && !attr) {
+    if (mode > 0 && !attr) {
         cudaFuncSetAttribute(k_conv16_tc<uint16_t, 1, NET_C, EPI_RELU>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              TC_SMEM);
         cudaFuncSetAttribute(k_conv16_tc<uint16_t, NET_C, NET_C, EPI_RELU>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -619,17 +838,35 @@ bool net_tensor_cores() {
         cudaFuncSetAttribute(k_conv16_tc<uint16_t, NET_C, 1, EPI_OUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
         cudaFuncSetAttribute(k_conv16_tc<float, NET_C, NET_C, EPI_GATE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              TC_SMEM);
+        cudaFuncSetAttribute(k_conv_tcz<uint16_t, 1, NET_C, EPI_RELU>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             TCZ_SMEM);
+        cudaFuncSetAttribute(k_conv_tcz<uint16_t, NET_C, NET_C, EPI_RELU>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             TCZ_SMEM);
+        cudaFuncSetAttribute(k_conv_tcz<uint16_t, NET_C, 1, EPI_OUT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             TCZ_SMEM);
+        cudaFuncSetAttribute(k_conv_tcz<float, NET_C, NET_C, EPI_GATE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             TCZ_SMEM);
         attr = true;
     }
-    return on;
+    return mode;
 }
 
-// CTAs of a tensor-core convolution over the grid of ws (0 if out of range)
-unsigned tc_grid(const NetWorkspace& ws) {
-    const int64_t g = (int64_t)((ws.nx + TC_PX - 1) / TC_PX) * ((ws.ny + TC_PY - 1) / TC_PY) *
-                      ((ws.nz + TC_ZC - 1) / TC_ZC);
-    return (g > 0 && g <= 2147483647LL) ? (unsigned)g : 0u;
+// one tensor-core convolution over the grid of ws in the chosen form
+template <typename TIN, int CI, int CO, int EPI>
+cudaError_t conv_tc(int mode, const NetWorkspace& ws, const TIN* x, const uint16_t* w, const uint16_t* gate,
+                    const uint8_t* mask, uint16_t* yb, float* yf, double* yd, cudaStream_t s) {
+    const int zc = mode == 2 ? TCZ_ZC : TC_ZC;
+    const int64_t g = (int64_t)((ws.nx + TC_PX - 1) / TC_PX) * ((ws.ny + TC_PY - 1) / TC_PY) * ((ws.nz + zc - 1) / zc);
+    if (g <= 0 || g > 2147483647LL) return cudaErrorInvalidValue;
+    if (mode == 2)
+        k_conv_tcz<TIN, CI, CO, EPI><<<(unsigned)g, TC_THREADS, TCZ_SMEM, s>>>(x, w, gate, mask, yb, yf, yd, ws.nx, ws.ny,
+                                                                             ws.nz, ws.err);
+    else
+        k_conv16_tc<TIN, CI, CO, EPI><<<(unsigned)g, TC_THREADS, TC_SMEM, s>>>(x, w, gate, mask, yb, yf, yd, ws.nx,
+                                                                             ws.ny, ws.nz, ws.err);
+    return cudaGetLastError();
 }
+
 
 int grid_for(int64_t work, int per_block, int max_per_sm) {
     const int64_t want = (work + per_block - 1) / per_block;
@@ -690,15 +927,17 @@ cudaError_t net_forward(const uint16_t* wb, NetWorkspace& ws, const double* in, 
     if (nvox == 0) return cudaSuccess;
     const int gc = grid_for(nvox, CTPB, 16);
     k_pack<<<elementwise_grid(nvox), RTPB, 0, s>>>(nvox, in, mask, in_scale, ws.a0);
-    if (net_tensor_cores()) {
-        const unsigned g = tc_grid(ws);
-        if (g == 0) return cudaErrorInvalidValue;
-        k_conv16_tc<uint16_t, 1, NET_C, EPI_RELU><<<g, TC_THREADS, TC_SMEM, s>>>(
-            ws.a0, wb, nullptr, nullptr, ws.a1, nullptr, nullptr, ws.nx, ws.ny, ws.nz, ws.err);
-        k_conv16_tc<uint16_t, NET_C, NET_C, EPI_RELU><<<g, TC_THREADS, TC_SMEM, s>>>(
-            ws.a1, wb + NET_OFF2, nullptr, nullptr, ws.a2, nullptr, nullptr, ws.nx, ws.ny, ws.nz, ws.err);
-        k_conv16_tc<uint16_t, NET_C, 1, EPI_OUT><<<g, TC_THREADS, TC_SMEM, s>>>(
-            ws.a2, wb + NET_OFF3, nullptr, mask, nullptr, out32, out64, ws.nx, ws.ny, ws.nz, ws.err);
+    if (const int mode = net_tc_mode()) {
+        cudaError_t e;
+        if ((e = conv_tc<uint16_t, 1, NET_C, EPI_RELU>(mode, ws, ws.a0, wb, nullptr, nullptr, ws.a1, nullptr, nullptr,
+                                                       s)) != cudaSuccess)
+            return e;
+        if ((e = conv_tc<uint16_t, NET_C, NET_C, EPI_RELU>(mode, ws, ws.a1, wb + NET_OFF2, nullptr, nullptr, ws.a2,
+                                                           nullptr, nullptr, s)) != cudaSuccess)
+            return e;
+        if ((e = conv_tc<uint16_t, NET_C, 1, EPI_OUT>(mode, ws, ws.a2, wb + NET_OFF3, nullptr, mask, nullptr, out32,
+                                                      out64, s)) != cudaSuccess)
+            return e;
     } else {
         k_conv<1, NET_C, uint16_t, EPI_RELU><<<gc, CTPB, 0, s>>>(ws.a0, wb, nullptr, nullptr, ws.a1, nullptr, nullptr,
                                                                  ws.nx, ws.ny, ws.nz);
@@ -724,11 +963,10 @@ cudaError_t net_backward(const uint16_t* wbt, NetWorkspace& ws, const double* ta
                                                           nullptr, ws.nx, ws.ny, ws.nz);
     // layer 2: dW2 from (d2, a1); d1 = (W2^T d2) where a1 > 0
     k_wgrad<NET_C, NET_C><<<grid_for(nvox, 32, 4), WTPB, 0, s>>>(ws.d2, ws.a1, grad + NET_OFF2, ws.nx, ws.ny, ws.nz);
-    if (net_tensor_cores()) {
-        const unsigned g = tc_grid(ws);
-        if (g == 0) return cudaErrorInvalidValue;
-        k_conv16_tc<float, NET_C, NET_C, EPI_GATE><<<g, TC_THREADS, TC_SMEM, s>>>(
-            ws.d2, wbt + NET_OFF2, ws.a1, nullptr, nullptr, ws.d1, nullptr, ws.nx, ws.ny, ws.nz, ws.err);
+    if (const int mode = net_tc_mode()) {
+        cudaError_t e = conv_tc<float, NET_C, NET_C, EPI_GATE>(mode, ws, ws.d2, wbt + NET_OFF2, ws.a1, nullptr, nullptr,
+                                                               ws.d1, nullptr, s);
+        if (e != cudaSuccess) return e;
     } else {
         k_conv<NET_C, NET_C, float, EPI_GATE><<<gc, CTPB, 0, s>>>(ws.d2, wbt + NET_OFF2, ws.a1, nullptr, nullptr,
                                                                   ws.d1, nullptr, ws.nx, ws.ny, ws.nz);

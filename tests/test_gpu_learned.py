@@ -83,6 +83,40 @@ def test_net_forward_matches_oracle(seed, shape):
     net.close()
 
 
+_OTHER_PATH = r"""
+import sys
+sys.path.insert(0, {root!r}); sys.path.insert(0, {tests!r})
+import numpy as np, torch
+import paper_1903_10977_gb300 as lib
+from oracle import learned as NL
+from test_gpu_learned import grid_case, scale_chain
+shape = (37, 21, 19)
+mask, x, _, w = grid_case(6, shape)
+net = lib.Net(w)
+dev = lambda v, t=torch.float64: torch.as_tensor(np.ascontiguousarray(v), dtype=t, device="cuda")
+out = net.forward(dev(x.ravel()), shape, mask=dev(mask.ravel(), torch.uint8)).cpu().numpy().reshape(shape)
+ref, _ = NL.forward(w, x, mask, bf16=True)
+err = np.abs(out - ref)
+ok = np.all(err <= 3 * 2.0 ** -8 * scale_chain(w, x, mask) + 1e-300) and not np.any(out[mask == 0])
+print("OK" if ok else "FAIL", float(np.linalg.norm(out - ref) / np.linalg.norm(ref)))
+"""
+
+
+@pytest.mark.parametrize("path", ["48", "0"])
+def test_net_forward_other_paths(path):
+    """The tensor-core convolutions with the z taps folded into N = 48 MMAs (IMGM_NET_TC=48)
+    and the CUDA-core loops (IMGM_NET_TC=0), each in a process of its own (the choice is read
+    once per process), match the oracle within the same bound as the default form."""
+    import subprocess
+    import sys
+    here = os.path.dirname(os.path.abspath(__file__))
+    code = _OTHER_PATH.format(root=os.path.dirname(here), tests=here)
+    r = subprocess.run([sys.executable, "-c", code], env=dict(os.environ, IMGM_NET_TC=path), capture_output=True,
+                       text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    assert r.stdout.strip().splitlines()[-1].startswith("OK"), r.stdout
+
+
 IN_SCALE = {3: 1.0, 4: 0.3}
 
 
