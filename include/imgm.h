@@ -23,6 +23,14 @@
  *   vectors and must not run concurrently on different streams.
  * - Return value: IMGM_OK (0) or a negative IMGM_ERR_* code; imgm_last_error(h) gives
  *   a message.  No call aborts the process or traps on the GPU.
+ *
+ * Deliberately narrower than a general interface: imgm_setup is host-synchronous and
+ * takes no stream (setup is not on the timed path); Lagrange bases are supported for
+ * degree 1 only (the same space as linear B-splines); there is no timeout status (no
+ * kernel waits on anything but its own grid; should a tensor-core convolution's bounded
+ * wait on its own matrix multiplies give up, it leaves the GPU usable and the next
+ * imgm_pcg_solve of a handle with that network, or imgm_net_get_weights / _get_grads,
+ * returns IMGM_ERR_CUDA); sizes come from imgm_get_level_info.
  */
 #ifndef IMGM_H
 #define IMGM_H

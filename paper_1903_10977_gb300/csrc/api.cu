@@ -205,6 +205,18 @@ int fail(imgm_handle* h, int code, const std::string& msg) {
     return code;
 }
 
+// A tensor-core convolution whose bounded wait gave up sets the workspace's flag (it never
+// hangs the GPU); a call that waits for the device reads and clears it.
+int net_wait_status(imgm_handle* h, const imgm::NetWorkspace& ws) {
+    if (!ws.err) return IMGM_OK;
+    int flag = 0;
+    if (cudaMemcpy(&flag, ws.err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return fail(h, IMGM_ERR_CUDA, "reading the network's status");
+    if (!flag) return IMGM_OK;
+    cudaMemset(ws.err, 0, sizeof(int));
+    return fail(h, IMGM_ERR_CUDA, "a tensor-core convolution gave up waiting for its matrix multiplies");
+}
+
 int cuda_fail(imgm_handle* h, cudaError_t e, const char* where) {
     return fail(h, IMGM_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
 }
@@ -718,8 +730,13 @@ cudaError_t tune_zm_level(imgm::DevLevelT<T>& d, const T* x, T* y, cudaStream_t 
                           bool verbose, int li) {
     static const int zcs[] = {1, 2, 3, 4, 6, 8, 11, 16, 22, 32};
     float best = 0.0f;
-    int best_yt = 0, best_zc = 0, best_stage = 1;
-    for (int stage = (sizeof(T) == 4 ? 0 : 1); stage <= 1; ++stage)   // FP32: registers or cp.async staging
+    int best_yt = 0, best_zc = 0, best_stage = 0;
+    // FP32: registers (0), per-warp cp.async staging (1) or the CTA form (2), or only the form
+    // IMGM_ZM_FORM names (tests); FP64 registers
+    int s_lo = 0, s_hi = sizeof(T) == 4 ? 2 : 0;
+    if (const char* f = std::getenv("IMGM_ZM_FORM"))
+        if (sizeof(T) == 4) s_lo = s_hi = std::min(2, std::max(0, std::atoi(f)));
+    for (int stage = s_lo; stage <= s_hi; ++stage)
     for (int yt = 1; yt <= 2; ++yt)
         for (int zc : zcs) {
             if (zc > d.m) continue;
@@ -741,7 +758,8 @@ cudaError_t tune_zm_level(imgm::DevLevelT<T>& d, const T* x, T* y, cudaStream_t 
             if (verbose)
                 std::fprintf(stderr, "imgm: level %d (%s) apply, %d rows per lane, %d planes per chunk%s: %.2f us\n",
                              li + 1, sizeof(T) == 8 ? "FP64" : "FP32", yt, zc,
-                             sizeof(T) == 4 ? (stage ? ", staged" : ", registers") : "", ms * 200.0f);
+                             sizeof(T) == 4 ? (stage == 2 ? ", CTA-staged" : stage ? ", staged" : ", registers") : "",
+                             ms * 200.0f);
             if (best_yt == 0 || ms < best) {
                 best = ms;
                 best_yt = yt;
@@ -1340,6 +1358,10 @@ int imgm_pcg_solve(imgm_handle* h, const double* dev_b, double* dev_x, double rt
                                    : imgm::launch_count() - launches0;
     out->rel_residual = fin.bb > 0 ? std::sqrt(fin.rr / fin.bb) : 0.0;
     out->true_rel_residual = fin.bb > 0 ? std::sqrt(fin.true_rr / fin.bb) : 0.0;
+    if (h->net) {
+        int c2 = net_wait_status(h, h->lws);
+        if (c2) return c2;
+    }
     return fin.status == -5 ? IMGM_ERR_BREAKDOWN : (fin.status == 1 ? IMGM_MAX_ITER : IMGM_OK);
 }
 
@@ -1800,6 +1822,7 @@ int imgm_net_destroy(imgm_net* net) {
 int imgm_net_get_weights(const imgm_net* net, float* host_weights) {
     if (!net || !host_weights) return net_fail(IMGM_ERR_INVALID, "null pointer");
     NCK(cudaDeviceSynchronize(), "sync");
+    if (int c = net_wait_status(nullptr, net->ws)) return c;
     NCK(cudaMemcpy(host_weights, net->w, imgm::NET_NW * sizeof(float), cudaMemcpyDeviceToHost), "weights");
     return IMGM_OK;
 }
@@ -1807,6 +1830,7 @@ int imgm_net_get_weights(const imgm_net* net, float* host_weights) {
 int imgm_net_get_grads(const imgm_net* net, float* host_grads) {
     if (!net || !host_grads) return net_fail(IMGM_ERR_INVALID, "null pointer");
     NCK(cudaDeviceSynchronize(), "sync");
+    if (int c = net_wait_status(nullptr, net->ws)) return c;
     NCK(cudaMemcpy(host_grads, net->g, imgm::NET_NW * sizeof(float), cudaMemcpyDeviceToHost), "gradients");
     return IMGM_OK;
 }

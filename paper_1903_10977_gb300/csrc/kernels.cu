@@ -714,6 +714,243 @@ __global__ void __launch_bounds__(TPB, zm_blocks_per_sm<T>()) k_apply_zm3d(DevLe
     }
 }
 
+// ---------------------------------------------------------------------------------
+// FP32 form of the z-marching apply for levels that stream from HBM: the 8 warps of a CTA
+// march together through one x strip, 8 YT rows and a z chunk, and the CTA stages each input
+// plane's region (32 columns x (8 YT + 2P) rows of x and of the Jacobi scale s) once in a
+// shared-memory ring, ZMC_DEPTH - 1 planes ahead by cp.async, so the y halo of a warp's rows
+// is read from shared memory instead of again from L2, and the CTA keeps three planes of its
+// tile in flight.  One CTA barrier per plane.  The per-warp arithmetic is that of
+// k_apply_zm3d.  Stored rows are CTA tasks of 256 rows.
+constexpr int ZMC_DEPTH = 4;
+
+template <int P, int YT>
+constexpr size_t zmc_smem() {
+    return (size_t)ZMC_DEPTH * 2 * (8 * YT + 2 * P) * 32 * sizeof(float);
+}
+
+template <int P, int MODE, int YT>
+__global__ void __launch_bounds__(TPB, 3) k_apply_zmc3d(DevLevelT<float> L, const float* __restrict__ x,
+                                                        const float* rin, float* out, float* __restrict__ xs,
+                                                        float gamma, const int* done, ZmShape sh) {
+    pdl_begin();
+    using T = float;
+    if (done && *done) return;
+    constexpr int W = 2 * P + 1, XS = 32 - 2 * P, NV = YT + 2 * P, RY = 8 * YT + 2 * P;
+    constexpr int BUF = 2 * RY * 32;                     // floats of one plane buffer (x, then s)
+    extern __shared__ __align__(16) float zc_ring[];     // [ZMC_DEPTH][2][RY][32]
+    __shared__ unsigned int s_task;
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int m = L.m;
+    const int64_t mm = (int64_t)m * m;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_task = atomicAdd(&L.tile_ctr[0], 1u);
+        __syncthreads();
+        const unsigned int t = s_task;
+        if (t >= sh.ntotal) break;
+        if (t < sh.ntensor) {
+            const int sxi = (int)(t % (unsigned)sh.sx);
+            const int syi = (int)((t / (unsigned)sh.sx) % (unsigned)sh.sy);
+            const int szi = (int)(t / ((unsigned)sh.sx * (unsigned)sh.sy));
+            const int gx = sxi * XS - P + lane;
+            const int yc = syi * 8 * YT;                     // the CTA's first row
+            const int y0 = yc + warp * YT;                   // this warp's first row
+            const int zc0 = szi * sh.zc;
+            const int zend = min(zc0 + sh.zc, m);
+            const bool xin = (unsigned)gx < (unsigned)m;
+            const bool own = lane >= P && lane < 32 - P && xin;
+            T kx[W], mx[W];
+#pragma unroll
+            for (int o = 0; o < W; ++o) {
+                kx[o] = xin ? ro(L.K1 + (int64_t)gx * W + o) : T(0);
+                mx[o] = xin ? ro(L.M1 + (int64_t)gx * W + o) : T(0);
+            }
+            bool symx = true;
+#pragma unroll
+            for (int o = 0; o < P; ++o) symx = symx && kx[o] == kx[2 * P - o] && mx[o] == mx[2 * P - o];
+            symx = __all_sync(FULL, symx);
+            bool symy[YT];
+#pragma unroll
+            for (int j = 0; j < YT; ++j) {
+                const int gy = y0 + j;
+                bool sy = gy < m;
+#pragma unroll
+                for (int o = 0; o < P; ++o)
+                    sy = sy && ro(L.K1 + (int64_t)gy * W + o) == ro(L.K1 + (int64_t)gy * W + 2 * P - o) &&
+                         ro(L.M1 + (int64_t)gy * W + o) == ro(L.M1 + (int64_t)gy * W + 2 * P - o);
+                symy[j] = sy;
+            }
+            T ring[YT][W];
+#pragma unroll
+            for (int j = 0; j < YT; ++j)
+#pragma unroll
+                for (int q = 0; q < W; ++q) ring[j][q] = T(0);
+            const int nplanes = (zend - zc0) + 2 * P;
+            // the CTA copies plane k's region (x and s, zero outside the grid) into buffer k mod D
+            auto stage = [&](int k) {
+                const int zp = zc0 - P + k;
+                const bool zin = k < nplanes && (unsigned)zp < (unsigned)m;
+                float* b = zc_ring + (k % ZMC_DEPTH) * BUF;
+                for (int e = threadIdx.x; e < 2 * RY * 32; e += TPB) {
+                    const int arr = e / (RY * 32), r = (e >> 5) % RY, c = e & 31;
+                    const int cx = sxi * XS - P + c, cy = yc - P + r;
+                    const bool in = zin && (unsigned)cx < (unsigned)m && (unsigned)cy < (unsigned)m;
+                    const int64_t g = in ? (int64_t)zp * mm + (int64_t)cy * m + cx : 0;
+                    const float* src = (arr ? L.s : x) + g;
+                    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(
+                                     (uint32_t)__cvta_generic_to_shared(b + e)),
+                                 "l"(src), "r"(in ? 4 : 0)
+                                 : "memory");
+                }
+                asm volatile("cp.async.commit_group;" ::: "memory");
+            };
+#pragma unroll
+            for (int k = 0; k < ZMC_DEPTH - 1; ++k) stage(k);
+            for (int base = 0; base < nplanes; base += W) {
+#pragma unroll
+                for (int u = 0; u < W; ++u) {
+                    const int k = base + u;
+                    if (k >= nplanes) break;
+                    const int zp = zc0 - P + k;
+                    asm volatile("cp.async.wait_group %0;" ::"n"(ZMC_DEPTH - 2) : "memory");   // own copies of k
+                    __syncthreads();                 // everyone's copies of k; everyone done with k - 1
+                    stage(k + ZMC_DEPTH - 1);        // into the buffer of plane k - 1
+                    const float* b = zc_ring + (k % ZMC_DEPTH) * BUF;
+                    T v[NV];
+#pragma unroll
+                    for (int i = 0; i < NV; ++i)
+                        v[i] = b[(warp * YT + i) * 32 + lane] * b[(RY + warp * YT + i) * 32 + lane];
+                    T a[YT], bb2[YT];
+#pragma unroll
+                    for (int j = 0; j < YT; ++j) {
+                        const int gy = y0 + j;
+                        const T* __restrict__ My = L.M1 + (int64_t)gy * W;
+                        const T* __restrict__ Ky = L.K1 + (int64_t)gy * W;
+                        T my = T(0), ky = T(0);
+                        if (symy[j]) {
+                            my = ro(My + P) * v[j + P];
+                            ky = ro(Ky + P) * v[j + P];
+#pragma unroll
+                            for (int o = 0; o < P; ++o) {
+                                const T pv = v[j + o] + v[j + 2 * P - o];
+                                my = fmaT(ro(My + o), pv, my);
+                                ky = fmaT(ro(Ky + o), pv, ky);
+                            }
+                        } else if (gy < m) {
+#pragma unroll
+                            for (int o = 0; o < W; ++o) {
+                                my = fmaT(ro(My + o), v[j + o], my);
+                                ky = fmaT(ro(Ky + o), v[j + o], ky);
+                            }
+                        }
+                        T aa = T(0), bb = T(0);
+                        if (symx) {
+                            aa = mx[P] * my;
+                            bb = fmaT(kx[P], my, mx[P] * ky);
+#pragma unroll
+                            for (int o = 0; o < P; ++o) {
+                                const T sm = __shfl_sync(FULL, my, (lane - P + o) & 31) +
+                                             __shfl_sync(FULL, my, (lane + P - o) & 31);
+                                const T sk = __shfl_sync(FULL, ky, (lane - P + o) & 31) +
+                                             __shfl_sync(FULL, ky, (lane + P - o) & 31);
+                                aa = fmaT(mx[o], sm, aa);
+                                bb = fmaT(mx[o], sk, bb);
+                                bb = fmaT(kx[o], sm, bb);
+                            }
+                        } else {
+#pragma unroll
+                            for (int o = 0; o < W; ++o) {
+                                const T mo = __shfl_sync(FULL, my, (lane - P + o) & 31);
+                                const T ko = __shfl_sync(FULL, ky, (lane - P + o) & 31);
+                                aa = fmaT(mx[o], mo, aa);
+                                bb = fmaT(mx[o], ko, bb);
+                                bb = fmaT(kx[o], mo, bb);
+                            }
+                        }
+                        a[j] = aa;
+                        bb2[j] = bb;
+                    }
+#pragma unroll
+                    for (int jz = 0; jz < W; ++jz) {
+                        const int z = zp - P + jz;
+                        if ((unsigned)z < (unsigned)m) {
+                            const T kz = ro(L.K1 + (int64_t)z * W + (2 * P - jz));
+                            const T mz = ro(L.M1 + (int64_t)z * W + (2 * P - jz));
+#pragma unroll
+                            for (int j = 0; j < YT; ++j) {
+                                T& r = ring[j][(u + 1 + jz) % W];
+                                r = fmaT(kz, a[j], r);
+                                r = fmaT(mz, bb2[j], r);
+                            }
+                        }
+                    }
+                    const int zo = zp - P;
+#pragma unroll
+                    for (int j = 0; j < YT; ++j) {
+                        T& r = ring[j][(u + 1) % W];
+                        const int gy = y0 + j;
+                        if (own && zo >= zc0 && zo < zend && gy < m) {
+                            const int64_t oi = (int64_t)zo * mm + (int64_t)gy * m + gx;
+                            const int ri = L.rowinfo[oi];
+                            if (ri < 0) {
+                                const T y = (ri == -1) ? r * ro(L.s + oi) : T(0);
+                                if (MODE == APPLY) {
+                                    out[oi] = y;
+                                } else {
+                                    const T rr = (ri == -2) ? T(0) : rin[oi] - y;
+                                    out[oi] = rr;
+                                    if (MODE == RESID_SMOOTH && ri == -1)
+                                        xs[oi] = fmaT(gamma * ro(L.dinv + oi), rr, xs[oi]);
+                                }
+                            }
+                        }
+                        r = T(0);
+                    }
+                }
+            }
+            asm volatile("cp.async.wait_group 0;" ::: "memory");   // the ring is free for the next task
+        } else {
+            // ---------------- stored rows: 256 consecutive stored row ids, one per thread
+            const int64_t k = (int64_t)(t - sh.ntensor) * TPB + threadIdx.x;
+            if (k < L.nb) {
+                const int64_t oi = L.band_row[k];
+                const int ix = (int)(oi % m), iy = (int)((oi / m) % m), iz = (int)(oi / mm);
+                const T* __restrict__ c = L.band_coef + k;
+                const int64_t nb = L.nb;
+                T y = T(0);
+#pragma unroll
+                for (int oz = 0; oz < W; ++oz) {
+                    const bool zin = (unsigned)(iz + oz - P) < (unsigned)m;
+#pragma unroll
+                    for (int oy = 0; oy < W; ++oy) {
+                        const bool yin = zin && (unsigned)(iy + oy - P) < (unsigned)m;
+#pragma unroll
+                        for (int ox = 0; ox < W; ++ox) {
+                            const bool in = yin && (unsigned)(ix + ox - P) < (unsigned)m;
+                            const int64_t g = oi + (ox - P) + (int64_t)(oy - P) * m + (int64_t)(oz - P) * mm;
+                            y = fmaT(ro(c + (int64_t)(ox + W * (oy + W * oz)) * nb), in ? x[g] : T(0), y);
+                        }
+                    }
+                }
+                if (MODE == APPLY) {
+                    out[oi] = y;
+                } else {
+                    const T rr = rin[oi] - y;
+                    out[oi] = rr;
+                    if (MODE == RESID_SMOOTH) xs[oi] = fmaT(gamma * ro(L.dinv + oi), rr, xs[oi]);
+                }
+            }
+        }
+    }
+    // every CTA has drawn past the end once; the last one re-arms the counter
+    if (threadIdx.x == 0 && atomicAdd(&L.tile_ctr[1], 1u) == gridDim.x - 1) {
+        L.tile_ctr[0] = 0u;
+        L.tile_ctr[1] = 0u;
+    }
+}
+
 template <int DIM, int P>
 __global__ void __launch_bounds__(TPB) k_apply_pq(DevLevel L, const double* __restrict__ p, double* __restrict__ q,
                                                   double* partial, PcgState* st) {
@@ -1740,10 +1977,39 @@ void launch_zm3d_stg(const DevLevelT<T>& L, int mode, const T* x, const T* rin, 
                    nullptr, nullptr, sh);
 }
 
-// FP32 levels take the staged or the register form as the autotuner chose; FP64 registers
+// the CTA form (FP32): strips x CTA row blocks of 8 YT rows x z chunks, stored rows in tasks of 256
+template <int P, int YT>
+void launch_zmc3d(const DevLevelT<float>& L, int mode, const float* x, const float* rin, float* out, float* xs,
+                  float gamma, const int* done, cudaStream_t s) {
+    ZmShape sh = zm_shape(L.m, L.nb, P, 8 * YT, L.zm_zc);
+    sh.ntotal = sh.ntensor + (unsigned)((L.nb + TPB - 1) / TPB);
+    int64_t g = std::min<int64_t>(sh.ntotal, 3 * num_sms());
+    if (const char* v = std::getenv("IMGM_ZM_BLOCKS")) {
+        const int k = std::atoi(v);
+        if (k > 0) g = std::min<int64_t>(g, k);
+    }
+    g = std::max<int64_t>(g, 1);
+    constexpr size_t smem = zmc_smem<P, YT>();
+    static_assert(zmc_smem<P, YT>() <= 48 * 1024, "CTA ring within the default shared memory");
+    if (mode == APPLY)
+        launch_pdl(k_apply_zmc3d<P, APPLY, YT>, (int)g, TPB, smem, s, L, x, rin, out, xs, gamma, done, sh);
+    else if (mode == RESID)
+        launch_pdl(k_apply_zmc3d<P, RESID, YT>, (int)g, TPB, smem, s, L, x, rin, out, xs, gamma, done, sh);
+    else
+        launch_pdl(k_apply_zmc3d<P, RESID_SMOOTH, YT>, (int)g, TPB, smem, s, L, x, rin, out, xs, gamma, done, sh);
+}
+
+// FP32 levels take the form the autotuner chose (0 registers, 1 warp-staged, 2 CTA-staged);
+// FP64 the register form
 template <typename T, int P, int YT>
 void launch_zm3d_yt(const DevLevelT<T>& L, int mode, const T* x, const T* rin, T* out, T* xs, T gamma, const int* done,
                     cudaStream_t s) {
+    if constexpr (sizeof(T) == 4) {
+        if (L.zm_stage == 2) {
+            launch_zmc3d<P, YT>(L, mode, x, rin, out, xs, gamma, done, s);
+            return;
+        }
+    }
     if (sizeof(T) == 4 && L.zm_stage)
         launch_zm3d_stg<T, P, YT, true>(L, mode, x, rin, out, xs, gamma, done, s);
     else

@@ -49,7 +49,7 @@ struct DevLevelT {
     // task shape of the 3-D z-marching apply (rows per lane, planes per chunk), picked by the
     // setup-time autotuner; 0 = the built-in rule
     int zm_yt = 0, zm_zc = 0;
-    int zm_stage = 1;                   // FP32: input planes staged by cp.async (1) or loaded to registers (0)
+    int zm_stage = 1;                   // FP32 input planes: 0 registers, 1 per-warp cp.async ring, 2 CTA ring
 };
 using DevLevel = DevLevelT<double>;
 

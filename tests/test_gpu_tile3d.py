@@ -5,7 +5,9 @@ the oracle as for the row kernels.  With IMGM_ZM_BLOCKS=1 one block of 8 warps d
 task from the level's counter, so each warp runs many tasks and the counter re-arms
 itself between consecutive launches (as on the full-size grids).  The 32^3 case has a
 level of 34^3 functions, whose restriction and prolongation take the sum-factorised
-three-pass kernels (the levels of the smaller cases take the direct ones)."""
+three-pass kernels (the levels of the smaller cases take the direct ones).  IMGM_ZM_FORM
+fixes the FP32 instances' form (planes in registers, staged per warp, or staged per CTA),
+which the setup autotuner otherwise picks, so that every form meets the oracle."""
 import numpy as np
 import pytest
 
@@ -19,7 +21,9 @@ pytestmark = pytest.mark.gpu
 EPS = np.finfo(float).eps
 CASES = [dict(n=16, levels=2, depth=1, degree=2), dict(n=8, levels=2, depth=1, degree=1),
          dict(n=8, levels=2, depth=1, degree=3), dict(n=16, levels=2, depth=1, degree=2, blocks=1),
-         dict(n=8, levels=2, depth=1, degree=3, blocks=1), dict(n=32, levels=3, depth=0, degree=2)]
+         dict(n=8, levels=2, depth=1, degree=3, blocks=1), dict(n=32, levels=3, depth=0, degree=2),
+         dict(n=16, levels=2, depth=1, degree=2, form=1), dict(n=16, levels=2, depth=1, degree=2, form=2),
+         dict(n=16, levels=2, depth=1, degree=3, form=2, blocks=1)]
 
 
 def dev(v):
@@ -32,13 +36,16 @@ def host(t):
 
 
 @pytest.fixture(scope="module", params=CASES,
-                ids=[f"p{c['degree']}-n{c['n']}" + (f"-blocks{c['blocks']}" if "blocks" in c else "") for c in CASES])
+                ids=[f"p{c['degree']}-n{c['n']}" + (f"-blocks{c['blocks']}" if "blocks" in c else "")
+                     + (f"-form{c['form']}" if "form" in c else "") for c in CASES])
 def case(request):
     mp = pytest.MonkeyPatch()
     mp.setenv("IMGM_TILE3D", "1")
     ov = dict(request.param)
     if "blocks" in ov:
         mp.setenv("IMGM_ZM_BLOCKS", str(ov.pop("blocks")))
+    if "form" in ov:                      # the FP32 apply's form: 1 warp-staged, 2 CTA-staged
+        mp.setenv("IMGM_ZM_FORM", str(ov.pop("form")))
     pr, lay, d, H = oracle_for("spheres20_128_p2", **ov)
     S = solver_for(lib, pr, lay, precision=0)
     Sm = solver_for(lib, pr, lay, precision=1)
