@@ -332,6 +332,45 @@ def run_batched(lib, torch, steps, warmup):
             "launch": "one CUDA graph: every solve a branch with its own device-side CG loop"}
 
 
+def smoother_bandwidth(S, torch, stream):
+    """The finest level's FP64 additive Schwarz smoothing (imgm_smooth: the one-function blocks'
+    diagonal scaling and the stored blocks), timed from a captured CUDA graph of 50, against its
+    algorithmic bytes: the inverses (sum n_j^2 x 8 B), per (block, function) pair its index (4 B),
+    block id (4 B), gathered residual (8 B) and atomic update of z (2 x 8 B), and the diagonal pass
+    over the level (r in, z out, 1/A_ii: 24 B per row)."""
+    info = S.level_info(S.L)
+    _, npairs, nvals = S.host_block_sizes(S.L)  # sum n_j (pairs), sum n_j^2 (inverse entries)
+    r = S.rhs()
+    z = torch.empty_like(r)
+    reps = 50
+    g = torch.cuda.CUDAGraph()
+    try:
+        with torch.cuda.graph(g):
+            for _ in range(reps):
+                S.smooth(r, z)
+        g.replay()
+        torch.cuda.synchronize()
+    except Exception:
+        g = None
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    if g is not None:
+        g.replay()
+    else:
+        for _ in range(reps):
+            S.smooth(r, z)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / 1e3 / reps
+    nbytes = 8 * nvals + 32 * npairs + 24 * info["n_grid"]
+    peak = measured_peaks().get("hbm_gbs")
+    gbs = nbytes / t / 1e9
+    return {"us": 1e6 * t, "algorithmic_bytes": nbytes, "achieved_gbs": gbs, "hbm_peak_gbs": peak,
+            "frac_of_hbm": gbs / peak if peak else None, "blocks": info["n_blocks"], "block_pairs": npairs,
+            "block_entries": nvals,
+            "kernels": "k_scale_diag + k_blocks_pairs (finest level, FP64)"}
+
+
 def vcycle_bandwidth(S, torch, stream, mixed):
     """One V-cycle (imgm_apply_preconditioner) timed from a captured CUDA graph of 20, with
     its algorithmic vector traffic: per level (13 + 2/2^d) s N_l bytes (pre-smoothing 2,
@@ -599,6 +638,7 @@ def run_ours(args, rank, world, local_rank):
 
     apply_ms, apply_graph = time_finest_apply(S, torch, stream, n_grid)
     vcycle = vcycle_bandwidth(S, torch, stream, code == 1)
+    smoother = smoother_bandwidth(S64 if S64 is not None else S, torch, stream)
     # the 2-D 512x512 workload and the batch beside the 3-D headline
     poisson2d = run_2d(args, lib, torch, timed_solves) if headline and not args.quick else None
     batched = run_batched(lib, torch, max(1, args.steps // 2), 1) if headline and not args.quick else None
@@ -640,6 +680,7 @@ def run_ours(args, rank, world, local_rank):
         "batched": batched,
         "learned": learned,
         "vcycle": vcycle,
+        "smoother": smoother,
         "e2e": {"value": total_units / t_e2e, "unit": "DOF/s", "h2d_bytes_per_step": 8 * n_grid,
                 "d2h_bytes_per_step": 8 * n_grid},
         "gpu_launches": sum(int(r["kernel_launches"]) for r in results),

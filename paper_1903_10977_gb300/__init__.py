@@ -326,6 +326,13 @@ class Solver:
         self._check(_lib.imgm_host_rhs(self._h, out.ctypes.data_as(ctypes.c_void_p)))
         return out
 
+    def host_block_sizes(self, level=None):
+        """(stored blocks, sum of their sizes n_j, sum of n_j^2) of a level."""
+        level = self.L if level is None else level
+        nb, ni, nv = _I64(), _I64(), _I64()
+        self._check(_lib.imgm_host_block_sizes(self._h, level, ctypes.byref(nb), ctypes.byref(ni), ctypes.byref(nv)))
+        return nb.value, ni.value, nv.value
+
     def host_blocks(self, level=None):
         level = self.L if level is None else level
         nb, ni, nv = _I64(), _I64(), _I64()
