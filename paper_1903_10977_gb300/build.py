@@ -40,7 +40,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     jobs = []
     objs = []
     common_nv = [nvcc, ARCH, "-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC,-fopenmp", "-I", INCLUDE]
-    for f in ("kernels.cu", "learned.cu", "api.cu"):
+    for f in sorted(x for x in os.listdir(CSRC) if x.endswith(".cu")):
         o = os.path.join(tmp, f + ".o")
         objs.append(o)
         jobs.append(common_nv + ["-c", os.path.join(CSRC, f), "-o", o])

@@ -728,17 +728,22 @@ imgm::DsVcycle ds_params(const imgm_handle* h, int top, const unsigned char* ima
 template <typename T>
 cudaError_t tune_zm_level(imgm::DevLevelT<T>& d, const T* x, T* y, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1,
                           bool verbose, int li) {
-    static const int zcs[] = {1, 2, 3, 4, 6, 8, 11, 16, 22, 32};
+    static const int zcs3[] = {1, 2, 3, 4, 6, 8, 11, 16, 22, 32};
+    static const int zcs2[] = {2, 4, 8, 12, 16, 24, 32, 48, 64};   // 2-D: rows per chunk
+    const bool two = d.dim == 2;
+    const int* zcs = two ? zcs2 : zcs3;
+    const int nzc = two ? 9 : 10;
     float best = 0.0f;
     int best_yt = 0, best_zc = 0, best_stage = 0;
     // FP32: registers (0), per-warp cp.async staging (1) or the CTA form (2), or only the form
     // IMGM_ZM_FORM names (tests); FP64 registers
-    int s_lo = 0, s_hi = sizeof(T) == 4 ? 2 : 0;
+    int s_lo = 0, s_hi = (sizeof(T) == 4 && !two) ? 2 : 0;
     if (const char* f = std::getenv("IMGM_ZM_FORM"))
         if (sizeof(T) == 4) s_lo = s_hi = std::min(2, std::max(0, std::atoi(f)));
     for (int stage = s_lo; stage <= s_hi; ++stage)
-    for (int yt = 1; yt <= 2; ++yt)
-        for (int zc : zcs) {
+    for (int yt = 1; yt <= (two ? 1 : 2); ++yt)
+        for (int zi = 0; zi < nzc; ++zi) {
+            const int zc = zcs[zi];
             if (zc > d.m) continue;
             imgm::DevLevelT<T> c = d;
             c.zm_yt = yt;
@@ -774,7 +779,7 @@ cudaError_t tune_zm_level(imgm::DevLevelT<T>& d, const T* x, T* y, cudaStream_t 
 }
 
 cudaError_t autotune_zm(imgm_handle* h) {
-    if (h->dim != 3 || std::getenv("IMGM_ZM_YT") || std::getenv("IMGM_ZM_ZC")) return cudaSuccess;
+    if (std::getenv("IMGM_ZM_YT") || std::getenv("IMGM_ZM_ZC")) return cudaSuccess;
     cudaStream_t s = nullptr;
     cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
     if (e != cudaSuccess) return e;
@@ -784,7 +789,7 @@ cudaError_t autotune_zm(imgm_handle* h) {
     const bool verbose = std::getenv("IMGM_VERBOSE") != nullptr;
     for (int li = 0; li < h->L && e == cudaSuccess; ++li) {
         LevelDev& L = h->lv[li];
-        if (!imgm::zm_applies(L.d.m)) continue;
+        if (!(h->dim == 3 ? imgm::zm_applies(L.d.m) : imgm::ym_applies(L.d.m))) continue;
         e = tune_zm_level<double>(L.d, L.t, L.e, s, e0, e1, verbose, li);
         if (e == cudaSuccess && h->precision >= 1 && L.ft)
             e = tune_zm_level<float>(L.fd, L.ft, L.fe, s, e0, e1, verbose, li);

@@ -21,124 +21,16 @@
 // which FP32 cannot hold unscaled.
 // Reductions are FP64 and deterministic: fixed grid, per-block partials summed in a
 // fixed order by the last block to finish.
-#include "kernels.cuh"
+#include "common.cuh"
 
 #include <cooperative_groups.h>
-
-#include <algorithm>
-#include <cstdlib>
-#include <utility>
 
 namespace cg = cooperative_groups;
 
 namespace imgm {
 namespace {
 
-constexpr int TPB = 256;
 int g_red_blocks = 0;
-
-// Programmatic dependent launch: every kernel is launched with programmatic stream
-// serialisation allowed, so that the blocks of the next kernel in the stream (or graph)
-// are scheduled while this one drains instead of after a full launch round trip.  Each
-// kernel first waits until its predecessor has completed and its writes are visible
-// (griddepcontrol.wait returns at once when there is no programmatic predecessor), then
-// lets its own successor launch.
-__device__ __forceinline__ void pdl_begin() {
-    asm volatile("griddepcontrol.wait;" ::: "memory");
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-}
-
-// Read-only data (level tables, stored coefficients, block inverses, scales): never
-// written on the device after setup, so it may take the non-coherent cached path.
-// The row tables are read with plain loads.
-template <typename T>
-__device__ __forceinline__ T ro(const T* p) {
-    return __ldg(p);
-}
-__device__ __forceinline__ int64_t ro(const int64_t* p) {
-    return (int64_t)__ldg(reinterpret_cast<const long long*>(p));
-}
-
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    return v;
-}
-
-// sum over the block (result valid in thread 0); blockDim.x == TPB
-__device__ __forceinline__ double block_sum(double v, double* ws) {
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    v = warp_sum(v);
-    __syncthreads();
-    if (lane == 0) ws[w] = v;
-    __syncthreads();
-    v = (threadIdx.x < TPB / 32) ? ws[threadIdx.x] : 0.0;
-    if (w == 0) v = warp_sum(v);
-    return v;
-}
-
-// Writes this block's partial and returns true in the block that finishes last, which
-// then holds the sum of all partials (summed in block order) in *total (thread 0).
-__device__ __forceinline__ bool finish_reduction(double v, double* partial, unsigned int* ticket, double* total) {
-    __shared__ double ws[32];
-    __shared__ bool last;
-    double bs = block_sum(v, ws);
-    if (threadIdx.x == 0) {
-        partial[blockIdx.x] = bs;
-        __threadfence();
-        unsigned int t = atomicAdd(ticket, 1u);
-        last = (t == gridDim.x - 1);
-    }
-    __syncthreads();
-    if (!last) return false;
-    __threadfence();
-    double s = 0.0;
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += TPB) s += ((volatile double*)partial)[b];
-    s = block_sum(s, ws);
-    if (threadIdx.x == 0) {
-        *total = s;
-        *ticket = 0u;
-    }
-    return true;
-}
-
-// Two sums at once (partials at [0, G) and [G, 2G)); the last block sums both in parallel.
-__device__ __forceinline__ bool finish_reduction2(double v1, double v2, double* partial, unsigned int* ticket,
-                                                  double* t1, double* t2) {
-    __shared__ double ws[32];
-    __shared__ bool last;
-    double b1 = block_sum(v1, ws);
-    double b2 = block_sum(v2, ws);
-    if (threadIdx.x == 0) {
-        partial[blockIdx.x] = b1;
-        partial[gridDim.x + blockIdx.x] = b2;
-        __threadfence();
-        unsigned int t = atomicAdd(ticket, 1u);
-        last = (t == gridDim.x - 1);
-    }
-    __syncthreads();
-    if (!last) return false;
-    __threadfence();
-    double s1 = 0.0, s2 = 0.0;
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += TPB) {
-        s1 += ((volatile double*)partial)[b];
-        s2 += ((volatile double*)partial)[gridDim.x + b];
-    }
-    s1 = block_sum(s1, ws);
-    s2 = block_sum(s2, ws);
-    if (threadIdx.x == 0) {
-        *t1 = s1;
-        *t2 = s2;
-        *ticket = 0u;
-    }
-    return true;
-}
-
-template <typename T>
-__device__ __forceinline__ T fmaT(T a, T b, T c) {
-    return fma(a, b, c);
-}
-
 // (A x)_i for one row (scaled variables when L.s != nullptr)
 template <typename T, int DIM, int P>
 __device__ __forceinline__ T row_apply(const DevLevelT<T>& L, int64_t i, const T* __restrict__ x) {
@@ -402,49 +294,25 @@ __global__ void __launch_bounds__(TPB) k_apply_tile2d(DevLevelT<T> L, const T* _
     }
 }
 
+
 // ---------------------------------------------------------------------------------
-// 3-D operator apply by z-marching warps.  A warp owns a column of outputs: 32 - 2P
-// consecutive x positions (its lanes, plus P halo lanes on each side), YT (1 or 2) consecutive
-// y rows and a chunk of z planes, and walks the input planes z' of that chunk (with a
-// P-plane halo at each end).  For each plane every lane loads its x-column segment of
-// YT + 2P values and forms, for its own YT rows,
-//   m = M_y v, k = K_y v                              (along y, in registers)
-//   a = M_x m, b = M_x k + K_x m                       (along x, neighbours by shuffles)
-// which are the plane's (M_y M_x) and (K_y M_x + M_y K_x) images; an output at plane z then
-// collects  y_z = sum_o K_z[z][o] a(z - P + o) + M_z[z][o] b(z - P + o)  in a ring of
-// 2P + 1 register accumulators, and is written when its last plane has passed.  That is
-// 2(2P+1) + 3(2P+1) FMA per row in the plane (times 32/(32-2P) for the halo lanes) plus
-// 2(2P+1) along z: about 39 FMA per row for P = 2, with no shared memory and no block
-// barrier.  Stored rows are not formed here: the same launch runs them as tasks of 32
-// stored rows (one per lane, (2P+1)^3 coefficients each), so no warp of the tensor tasks
-// waits on a lane with a stored row.  Warps draw tasks (tensor tasks first) from the
-// level's counter; the last warp to finish re-arms it.  Modes as k_apply_tile2d.
-// output rows (y) per lane: a template parameter of the kernel (1 or 2), chosen per level
-
-struct ZmShape {
-    int sx, sy, sz;                      // tensor tasks along x (strips), y (segments), z (chunks)
-    int zc;                              // planes per chunk
-    unsigned int ntensor, ntotal;        // tensor tasks; all tasks (tensor + stored)
-};
-
-// blocks per SM the z-marching apply is compiled for: two in FP64 (its FP64 pipe is the
-// bound), four in FP32 (latency-bound: more resident warps hide the plane loads)
-template <typename T>
-constexpr int zm_blocks_per_sm() { return sizeof(T) == 4 ? 4 : 2; }
-
-template <typename T, int P, int MODE, bool DOT, int YT, bool STG>
-__global__ void __launch_bounds__(TPB, zm_blocks_per_sm<T>()) k_apply_zm3d(DevLevelT<T> L, const T* __restrict__ x, const T* rin, T* out,
+// 2-D operator apply by y-marching warps, the 2-D form of k_apply_zm3d: a warp owns 32 - 2P
+// x columns (lanes, P halo lanes each side) and a chunk of y rows, and walks the input rows
+// with a ring of 2P + 1 register accumulators: per row a = M_x v and b = K_x v (neighbours
+// by shuffles), and the outputs y = yp - P .. yp + P receive K_y a + M_y b; an output is
+// written when its last input row has passed.  (2 + 2)(2P + 1) FMA per row in all (x 32/(32
+// - 2P) for the halo lanes), one load per lane and row.  Stored rows are tasks of 32 rows.
+template <typename T, int P, int MODE, bool DOT>
+__global__ void __launch_bounds__(TPB) k_apply_ym2d(DevLevelT<T> L, const T* __restrict__ x, const T* rin, T* out,
                                                     T* __restrict__ xs, T gamma, const int* done, double* partial,
                                                     PcgState* st, ZmShape sh) {
     pdl_begin();
     if (done && *done) return;
-    constexpr int W = 2 * P + 1, XS = 32 - 2 * P, NV = YT + 2 * P;
+    constexpr int W = 2 * P + 1, XS = 32 - 2 * P;
     constexpr bool SC = sizeof(T) == 4;              // FP32 path: Jacobi-scaled variables
-    extern __shared__ __align__(16) float zm_stage[];   // FP32: [warp][W planes][x, s][NV][32]
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const int m = L.m;
-    const int64_t mm = (int64_t)m * m;
     double acc = 0.0;
     for (;;) {
         unsigned int t = 0;
@@ -452,234 +320,111 @@ __global__ void __launch_bounds__(TPB, zm_blocks_per_sm<T>()) k_apply_zm3d(DevLe
         t = __shfl_sync(FULL, t, 0);
         if (t >= sh.ntotal) break;
         if (t < sh.ntensor) {
-            // ---------------- tensor task: strip sxi, rows y0.., planes zc0..zend-1
             const int sxi = (int)(t % (unsigned)sh.sx);
-            const int syi = (int)((t / (unsigned)sh.sx) % (unsigned)sh.sy);
-            const int szi = (int)(t / ((unsigned)sh.sx * (unsigned)sh.sy));
+            const int syi = (int)(t / (unsigned)sh.sx);
             const int gx = sxi * XS - P + lane;
-            const int y0 = syi * YT;
-            const int zc0 = szi * sh.zc;
-            const int zend = min(zc0 + sh.zc, m);
+            const int yc0 = syi * sh.zc;
+            const int yend = min(yc0 + sh.zc, m);
             const bool xin = (unsigned)gx < (unsigned)m;
-            const bool own = lane >= P && lane < 32 - P && xin;      // this lane writes outputs
+            const bool own = lane >= P && lane < 32 - P && xin;
             T kx[W], mx[W];
 #pragma unroll
             for (int o = 0; o < W; ++o) {
                 kx[o] = xin ? ro(L.K1 + (int64_t)gx * W + o) : T(0);
                 mx[o] = xin ? ro(L.M1 + (int64_t)gx * W + o) : T(0);
             }
-            // Away from the open-knot ends the 1-D rows are symmetric (c[o] = c[2P - o]): the sums
-            // along x and y then pair the neighbours first, 2P adds and 3(P+1) FMA instead of
-            // 3(2P+1) FMA along x, P adds and 2(P+1) FMA instead of 2(2P+1) along y.  The test
-            // is per warp (x) and per row (y), so no lane diverges.
             bool symx = true;
 #pragma unroll
             for (int o = 0; o < P; ++o) symx = symx && kx[o] == kx[2 * P - o] && mx[o] == mx[2 * P - o];
             symx = __all_sync(FULL, symx);
-            bool symy[YT];
+            T ring[W];
 #pragma unroll
-            for (int j = 0; j < YT; ++j) {
-                const int gy = y0 + j;
-                bool sy = gy < m;
-#pragma unroll
-                for (int o = 0; o < P; ++o)
-                    sy = sy && ro(L.K1 + (int64_t)gy * W + o) == ro(L.K1 + (int64_t)gy * W + 2 * P - o) &&
-                         ro(L.M1 + (int64_t)gy * W + o) == ro(L.M1 + (int64_t)gy * W + 2 * P - o);
-                symy[j] = sy;
-            }
-            T ring[YT][W];
-#pragma unroll
-            for (int j = 0; j < YT; ++j)
-#pragma unroll
-                for (int q = 0; q < W; ++q) ring[j][q] = T(0);
-            const int nplanes = (zend - zc0) + 2 * P;
-            // the column segment of input plane zp in registers, the next plane's loads issued
-            // before the current plane's arithmetic (zero outside the grid): FP64, and FP32 where
-            // the autotuner found it faster than staging (L2-resident levels)
-            auto load_plane = [&](int zp, T* v) {
-                const bool zin = (unsigned)zp < (unsigned)m;
-#pragma unroll
-                for (int i = 0; i < NV; ++i) {
-                    const int gy = y0 - P + i;
-                    const bool in = zin && xin && (unsigned)gy < (unsigned)m;
-                    const int64_t g = (int64_t)zp * mm + (int64_t)gy * m + gx;
-                    v[i] = in ? (SC ? x[g] * ro(L.s + g) : x[g]) : T(0);
-                }
+            for (int q = 0; q < W; ++q) ring[q] = T(0);
+            const int nrows = (yend - yc0) + 2 * P;
+            auto load_row = [&](int yp) -> T {
+                const bool in = xin && (unsigned)yp < (unsigned)m;
+                const int64_t g = (int64_t)yp * m + gx;
+                return in ? (SC ? x[g] * ro(L.s + g) : x[g]) : T(0);
             };
-            // FP32 (latency-bound, not ALU-bound): the segments of x and of the Jacobi scale s of
-            // the next W - 1 planes are in flight at once, copied by cp.async into this warp's ring
-            // of W plane buffers in shared memory.  A lane copies and later reads only its own
-            // column, so its own cp.async.wait_group orders them and no warp barrier is needed.
-            float* stg = nullptr;
-            constexpr bool staged = SC && STG;
-            if constexpr (SC) stg = zm_stage + (threadIdx.x >> 5) * (W * 2 * NV * 32);
-            auto stage_plane = [&](int k) {
-                if constexpr (SC) {
-                    const int zp = zc0 - P + k;
-                    const bool zin = k < nplanes && (unsigned)zp < (unsigned)m;
-                    float* bx = stg + (k % W) * (2 * NV * 32);
-#pragma unroll
-                    for (int i = 0; i < NV; ++i) {
-                        const int gy = y0 - P + i;
-                        const bool in = zin && xin && (unsigned)gy < (unsigned)m;
-                        const int64_t g = in ? (int64_t)zp * mm + (int64_t)gy * m + gx : 0;
-                        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(
-                                         (uint32_t)__cvta_generic_to_shared(bx + i * 32 + lane)),
-                                     "l"(x + g), "r"(in ? 4 : 0)
-                                     : "memory");
-                        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(
-                                         (uint32_t)__cvta_generic_to_shared(bx + (NV + i) * 32 + lane)),
-                                     "l"(L.s + g), "r"(in ? 4 : 0)
-                                     : "memory");
-                    }
-                    asm volatile("cp.async.commit_group;" ::: "memory");
-                }
-            };
-            T v[NV];
-            if constexpr (staged) {
-#pragma unroll
-                for (int k = 0; k < W - 1; ++k) stage_plane(k);
-            } else {
-                load_plane(zc0 - P, v);
-            }
-            for (int base = 0; base < nplanes; base += W) {
+            T v = load_row(yc0 - P);
+            for (int base = 0; base < nrows; base += W) {
 #pragma unroll
                 for (int u = 0; u < W; ++u) {
                     const int k = base + u;
-                    if (k >= nplanes) break;
-                    const int zp = zc0 - P + k;                      // input plane
-                    T vn[NV];
-                    if constexpr (staged) {
-                        stage_plane(k + W - 1);                      // into the buffer of plane k - 1
-                        asm volatile("cp.async.wait_group %0;" ::"n"(W - 1) : "memory");   // plane k is in
-                        const float* bx = stg + (k % W) * (2 * NV * 32);
+                    if (k >= nrows) break;
+                    const int yp = yc0 - P + k;
+                    const T vn = (k + 1 < nrows) ? load_row(yp + 1) : T(0);
+                    T aa, bb;
+                    if (symx) {
+                        aa = mx[P] * v;
+                        bb = kx[P] * v;
 #pragma unroll
-                        for (int i = 0; i < NV; ++i) v[i] = bx[i * 32 + lane] * bx[(NV + i) * 32 + lane];
+                        for (int o = 0; o < P; ++o) {
+                            const T sv = __shfl_sync(FULL, v, (lane - P + o) & 31) +
+                                         __shfl_sync(FULL, v, (lane + P - o) & 31);
+                            aa = fmaT(mx[o], sv, aa);
+                            bb = fmaT(kx[o], sv, bb);
+                        }
                     } else {
-                        // the next plane's loads go out before this plane's arithmetic
-                        if (k + 1 < nplanes) load_plane(zp + 1, vn);
-                    }
-                    T a[YT], b[YT];
+                        aa = T(0);
+                        bb = T(0);
 #pragma unroll
-                    for (int j = 0; j < YT; ++j) {
-                        const int gy = y0 + j;
-                        const T* __restrict__ My = L.M1 + (int64_t)gy * W;
-                        const T* __restrict__ Ky = L.K1 + (int64_t)gy * W;
-                        T my = T(0), ky = T(0);
-                        if (symy[j]) {
-                            my = ro(My + P) * v[j + P];
-                            ky = ro(Ky + P) * v[j + P];
-#pragma unroll
-                            for (int o = 0; o < P; ++o) {
-                                const T pv = v[j + o] + v[j + 2 * P - o];
-                                my = fmaT(ro(My + o), pv, my);
-                                ky = fmaT(ro(Ky + o), pv, ky);
-                            }
-                        } else if (gy < m) {
-#pragma unroll
-                            for (int o = 0; o < W; ++o) {
-                                my = fmaT(ro(My + o), v[j + o], my);
-                                ky = fmaT(ro(Ky + o), v[j + o], ky);
-                            }
-                        }
-                        T aa = T(0), bb = T(0);
-                        if (symx) {
-                            aa = mx[P] * my;
-                            bb = fmaT(kx[P], my, mx[P] * ky);
-#pragma unroll
-                            for (int o = 0; o < P; ++o) {
-                                const T sm = __shfl_sync(FULL, my, (lane - P + o) & 31) +
-                                             __shfl_sync(FULL, my, (lane + P - o) & 31);
-                                const T sk = __shfl_sync(FULL, ky, (lane - P + o) & 31) +
-                                             __shfl_sync(FULL, ky, (lane + P - o) & 31);
-                                aa = fmaT(mx[o], sm, aa);
-                                bb = fmaT(mx[o], sk, bb);
-                                bb = fmaT(kx[o], sm, bb);
-                            }
-                        } else {
-#pragma unroll
-                            for (int o = 0; o < W; ++o) {
-                                const T mo = __shfl_sync(FULL, my, (lane - P + o) & 31);
-                                const T ko = __shfl_sync(FULL, ky, (lane - P + o) & 31);
-                                aa = fmaT(mx[o], mo, aa);
-                                bb = fmaT(mx[o], ko, bb);
-                                bb = fmaT(kx[o], mo, bb);
-                            }
-                        }
-                        a[j] = aa;
-                        b[j] = bb;
-                    }
-                    // outputs z = zp - P + jz receive K_z[z][2P - jz] a + M_z[z][2P - jz] b;
-                    // output z keeps ring slot (z - zc0 + 2P + 1) mod W, here (u + 1 + jz) mod W
-                    // (base is a multiple of W)
-#pragma unroll
-                    for (int jz = 0; jz < W; ++jz) {
-                        const int z = zp - P + jz;
-                        if ((unsigned)z < (unsigned)m) {
-                            const T kz = ro(L.K1 + (int64_t)z * W + (2 * P - jz));
-                            const T mz = ro(L.M1 + (int64_t)z * W + (2 * P - jz));
-#pragma unroll
-                            for (int j = 0; j < YT; ++j) {
-                                T& r = ring[j][(u + 1 + jz) % W];
-                                r = fmaT(kz, a[j], r);
-                                r = fmaT(mz, b[j], r);
-                            }
+                        for (int o = 0; o < W; ++o) {
+                            const T vo = __shfl_sync(FULL, v, (lane - P + o) & 31);
+                            aa = fmaT(mx[o], vo, aa);
+                            bb = fmaT(kx[o], vo, bb);
                         }
                     }
-                    // output zp - P has seen its last plane (slot (u + 1) mod W)
-                    const int zo = zp - P;
+                    // outputs y = yp - P + jy receive K_y[y][2P - jy] a + M_y[y][2P - jy] b; output y
+                    // keeps ring slot (y - yc0 + 2P + 1) mod W, here (u + 1 + jy) mod W
 #pragma unroll
-                    for (int j = 0; j < YT; ++j) {
-                        T& r = ring[j][(u + 1) % W];
-                        const int gy = y0 + j;
-                        if (own && zo >= zc0 && zo < zend && gy < m) {
-                            const int64_t oi = (int64_t)zo * mm + (int64_t)gy * m + gx;
-                            const int ri = L.rowinfo[oi];
-                            if (ri < 0) {                            // tensor row or inactive row
-                                T y = T(0);
-                                if (ri == -1) y = SC ? r * ro(L.s + oi) : r;
-                                if (MODE == APPLY) {
-                                    out[oi] = y;
-                                } else {
-                                    const T rr = (ri == -2) ? T(0) : rin[oi] - y;
-                                    out[oi] = rr;
-                                    if (MODE == RESID_SMOOTH && ri == -1)
-                                        xs[oi] = fmaT(gamma * ro(L.dinv + oi), rr, xs[oi]);
-                                }
-                                if (DOT && ri == -1) acc = fma((double)x[oi], (double)y, acc);
-                            }
+                    for (int jy = 0; jy < W; ++jy) {
+                        const int y = yp - P + jy;
+                        if ((unsigned)y < (unsigned)m) {
+                            T& r = ring[(u + 1 + jy) % W];
+                            r = fmaT(ro(L.K1 + (int64_t)y * W + (2 * P - jy)), aa, r);
+                            r = fmaT(ro(L.M1 + (int64_t)y * W + (2 * P - jy)), bb, r);
                         }
-                        r = T(0);
                     }
-                    if constexpr (!staged) {
-#pragma unroll
-                        for (int i = 0; i < NV; ++i) v[i] = vn[i];
+                    const int yo = yp - P;
+                    T& r = ring[(u + 1) % W];
+                    if (own && yo >= yc0 && yo < yend) {
+                        const int64_t oi = (int64_t)yo * m + gx;
+                        const int ri = L.rowinfo[oi];
+                        if (ri < 0) {
+                            T y = T(0);
+                            if (ri == -1) y = SC ? r * ro(L.s + oi) : r;
+                            if (MODE == APPLY) {
+                                out[oi] = y;
+                            } else {
+                                const T rr = (ri == -2) ? T(0) : rin[oi] - y;
+                                out[oi] = rr;
+                                if (MODE == RESID_SMOOTH && ri == -1) xs[oi] = fmaT(gamma * ro(L.dinv + oi), rr, xs[oi]);
+                            }
+                            if (DOT && ri == -1) acc = fma((double)x[oi], (double)y, acc);
+                        }
                     }
+                    r = T(0);
+                    v = vn;
                 }
             }
-            if constexpr (staged) asm volatile("cp.async.wait_group 0;" ::: "memory");   // the ring is free again
         } else {
-            // ---------------- stored rows: 32 consecutive stored row ids, one per lane
+            // stored rows: 32 consecutive stored row ids, one per lane
             const int64_t k = (int64_t)(t - sh.ntensor) * 32 + lane;
             if (k < L.nb) {
                 const int64_t oi = L.band_row[k];
-                const int ix = (int)(oi % m), iy = (int)((oi / m) % m), iz = (int)(oi / mm);
+                const int ix = (int)(oi % m), iy = (int)(oi / m);
                 const T* __restrict__ c = L.band_coef + k;
                 const int64_t nb = L.nb;
                 T y = T(0);
 #pragma unroll
-                for (int oz = 0; oz < W; ++oz) {
-                    const bool zin = (unsigned)(iz + oz - P) < (unsigned)m;
+                for (int oy = 0; oy < W; ++oy) {
+                    const bool yin = (unsigned)(iy + oy - P) < (unsigned)m;
 #pragma unroll
-                    for (int oy = 0; oy < W; ++oy) {
-                        const bool yin = zin && (unsigned)(iy + oy - P) < (unsigned)m;
-#pragma unroll
-                        for (int ox = 0; ox < W; ++ox) {
-                            const bool in = yin && (unsigned)(ix + ox - P) < (unsigned)m;
-                            const int64_t g = oi + (ox - P) + (int64_t)(oy - P) * m + (int64_t)(oz - P) * mm;
-                            const T xv = in ? x[g] : T(0);
-                            y = fmaT(ro(c + (int64_t)(ox + W * (oy + W * oz)) * nb), xv, y);
-                        }
+                    for (int ox = 0; ox < W; ++ox) {
+                        const bool in = yin && (unsigned)(ix + ox - P) < (unsigned)m;
+                        const int64_t g = oi + (ox - P) + (int64_t)(oy - P) * m;
+                        y = fmaT(ro(c + (int64_t)(ox + W * oy) * nb), in ? x[g] : T(0), y);
                     }
                 }
                 if (MODE == APPLY) {
@@ -693,8 +438,6 @@ __global__ void __launch_bounds__(TPB, zm_blocks_per_sm<T>()) k_apply_zm3d(DevLe
             }
         }
     }
-    // every warp has drawn past the end once; the last one re-arms the counter for the next
-    // launch (which starts only after this grid has completed)
     if (lane == 0 && atomicAdd(&L.tile_ctr[1], 1u) == gridDim.x * (TPB / 32) - 1) {
         L.tile_ctr[0] = 0u;
         L.tile_ctr[1] = 0u;
@@ -711,243 +454,6 @@ __global__ void __launch_bounds__(TPB, zm_blocks_per_sm<T>()) k_apply_zm3d(DevLe
                 st->alpha = st->rz / pq;
             }
         }
-    }
-}
-
-// ---------------------------------------------------------------------------------
-// FP32 form of the z-marching apply for levels that stream from HBM: the 8 warps of a CTA
-// march together through one x strip, 8 YT rows and a z chunk, and the CTA stages each input
-// plane's region (32 columns x (8 YT + 2P) rows of x and of the Jacobi scale s) once in a
-// shared-memory ring, ZMC_DEPTH - 1 planes ahead by cp.async, so the y halo of a warp's rows
-// is read from shared memory instead of again from L2, and the CTA keeps three planes of its
-// tile in flight.  One CTA barrier per plane.  The per-warp arithmetic is that of
-// k_apply_zm3d.  Stored rows are CTA tasks of 256 rows.
-constexpr int ZMC_DEPTH = 4;
-
-template <int P, int YT>
-constexpr size_t zmc_smem() {
-    return (size_t)ZMC_DEPTH * 2 * (8 * YT + 2 * P) * 32 * sizeof(float);
-}
-
-template <int P, int MODE, int YT>
-__global__ void __launch_bounds__(TPB, 3) k_apply_zmc3d(DevLevelT<float> L, const float* __restrict__ x,
-                                                        const float* rin, float* out, float* __restrict__ xs,
-                                                        float gamma, const int* done, ZmShape sh) {
-    pdl_begin();
-    using T = float;
-    if (done && *done) return;
-    constexpr int W = 2 * P + 1, XS = 32 - 2 * P, NV = YT + 2 * P, RY = 8 * YT + 2 * P;
-    constexpr int BUF = 2 * RY * 32;                     // floats of one plane buffer (x, then s)
-    extern __shared__ __align__(16) float zc_ring[];     // [ZMC_DEPTH][2][RY][32]
-    __shared__ unsigned int s_task;
-    const unsigned FULL = 0xffffffffu;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int m = L.m;
-    const int64_t mm = (int64_t)m * m;
-    for (;;) {
-        __syncthreads();
-        if (threadIdx.x == 0) s_task = atomicAdd(&L.tile_ctr[0], 1u);
-        __syncthreads();
-        const unsigned int t = s_task;
-        if (t >= sh.ntotal) break;
-        if (t < sh.ntensor) {
-            const int sxi = (int)(t % (unsigned)sh.sx);
-            const int syi = (int)((t / (unsigned)sh.sx) % (unsigned)sh.sy);
-            const int szi = (int)(t / ((unsigned)sh.sx * (unsigned)sh.sy));
-            const int gx = sxi * XS - P + lane;
-            const int yc = syi * 8 * YT;                     // the CTA's first row
-            const int y0 = yc + warp * YT;                   // this warp's first row
-            const int zc0 = szi * sh.zc;
-            const int zend = min(zc0 + sh.zc, m);
-            const bool xin = (unsigned)gx < (unsigned)m;
-            const bool own = lane >= P && lane < 32 - P && xin;
-            T kx[W], mx[W];
-#pragma unroll
-            for (int o = 0; o < W; ++o) {
-                kx[o] = xin ? ro(L.K1 + (int64_t)gx * W + o) : T(0);
-                mx[o] = xin ? ro(L.M1 + (int64_t)gx * W + o) : T(0);
-            }
-            bool symx = true;
-#pragma unroll
-            for (int o = 0; o < P; ++o) symx = symx && kx[o] == kx[2 * P - o] && mx[o] == mx[2 * P - o];
-            symx = __all_sync(FULL, symx);
-            bool symy[YT];
-#pragma unroll
-            for (int j = 0; j < YT; ++j) {
-                const int gy = y0 + j;
-                bool sy = gy < m;
-#pragma unroll
-                for (int o = 0; o < P; ++o)
-                    sy = sy && ro(L.K1 + (int64_t)gy * W + o) == ro(L.K1 + (int64_t)gy * W + 2 * P - o) &&
-                         ro(L.M1 + (int64_t)gy * W + o) == ro(L.M1 + (int64_t)gy * W + 2 * P - o);
-                symy[j] = sy;
-            }
-            T ring[YT][W];
-#pragma unroll
-            for (int j = 0; j < YT; ++j)
-#pragma unroll
-                for (int q = 0; q < W; ++q) ring[j][q] = T(0);
-            const int nplanes = (zend - zc0) + 2 * P;
-            // the CTA copies plane k's region (x and s, zero outside the grid) into buffer k mod D
-            auto stage = [&](int k) {
-                const int zp = zc0 - P + k;
-                const bool zin = k < nplanes && (unsigned)zp < (unsigned)m;
-                float* b = zc_ring + (k % ZMC_DEPTH) * BUF;
-                for (int e = threadIdx.x; e < 2 * RY * 32; e += TPB) {
-                    const int arr = e / (RY * 32), r = (e >> 5) % RY, c = e & 31;
-                    const int cx = sxi * XS - P + c, cy = yc - P + r;
-                    const bool in = zin && (unsigned)cx < (unsigned)m && (unsigned)cy < (unsigned)m;
-                    const int64_t g = in ? (int64_t)zp * mm + (int64_t)cy * m + cx : 0;
-                    const float* src = (arr ? L.s : x) + g;
-                    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(
-                                     (uint32_t)__cvta_generic_to_shared(b + e)),
-                                 "l"(src), "r"(in ? 4 : 0)
-                                 : "memory");
-                }
-                asm volatile("cp.async.commit_group;" ::: "memory");
-            };
-#pragma unroll
-            for (int k = 0; k < ZMC_DEPTH - 1; ++k) stage(k);
-            for (int base = 0; base < nplanes; base += W) {
-#pragma unroll
-                for (int u = 0; u < W; ++u) {
-                    const int k = base + u;
-                    if (k >= nplanes) break;
-                    const int zp = zc0 - P + k;
-                    asm volatile("cp.async.wait_group %0;" ::"n"(ZMC_DEPTH - 2) : "memory");   // own copies of k
-                    __syncthreads();                 // everyone's copies of k; everyone done with k - 1
-                    stage(k + ZMC_DEPTH - 1);        // into the buffer of plane k - 1
-                    const float* b = zc_ring + (k % ZMC_DEPTH) * BUF;
-                    T v[NV];
-#pragma unroll
-                    for (int i = 0; i < NV; ++i)
-                        v[i] = b[(warp * YT + i) * 32 + lane] * b[(RY + warp * YT + i) * 32 + lane];
-                    T a[YT], bb2[YT];
-#pragma unroll
-                    for (int j = 0; j < YT; ++j) {
-                        const int gy = y0 + j;
-                        const T* __restrict__ My = L.M1 + (int64_t)gy * W;
-                        const T* __restrict__ Ky = L.K1 + (int64_t)gy * W;
-                        T my = T(0), ky = T(0);
-                        if (symy[j]) {
-                            my = ro(My + P) * v[j + P];
-                            ky = ro(Ky + P) * v[j + P];
-#pragma unroll
-                            for (int o = 0; o < P; ++o) {
-                                const T pv = v[j + o] + v[j + 2 * P - o];
-                                my = fmaT(ro(My + o), pv, my);
-                                ky = fmaT(ro(Ky + o), pv, ky);
-                            }
-                        } else if (gy < m) {
-#pragma unroll
-                            for (int o = 0; o < W; ++o) {
-                                my = fmaT(ro(My + o), v[j + o], my);
-                                ky = fmaT(ro(Ky + o), v[j + o], ky);
-                            }
-                        }
-                        T aa = T(0), bb = T(0);
-                        if (symx) {
-                            aa = mx[P] * my;
-                            bb = fmaT(kx[P], my, mx[P] * ky);
-#pragma unroll
-                            for (int o = 0; o < P; ++o) {
-                                const T sm = __shfl_sync(FULL, my, (lane - P + o) & 31) +
-                                             __shfl_sync(FULL, my, (lane + P - o) & 31);
-                                const T sk = __shfl_sync(FULL, ky, (lane - P + o) & 31) +
-                                             __shfl_sync(FULL, ky, (lane + P - o) & 31);
-                                aa = fmaT(mx[o], sm, aa);
-                                bb = fmaT(mx[o], sk, bb);
-                                bb = fmaT(kx[o], sm, bb);
-                            }
-                        } else {
-#pragma unroll
-                            for (int o = 0; o < W; ++o) {
-                                const T mo = __shfl_sync(FULL, my, (lane - P + o) & 31);
-                                const T ko = __shfl_sync(FULL, ky, (lane - P + o) & 31);
-                                aa = fmaT(mx[o], mo, aa);
-                                bb = fmaT(mx[o], ko, bb);
-                                bb = fmaT(kx[o], mo, bb);
-                            }
-                        }
-                        a[j] = aa;
-                        bb2[j] = bb;
-                    }
-#pragma unroll
-                    for (int jz = 0; jz < W; ++jz) {
-                        const int z = zp - P + jz;
-                        if ((unsigned)z < (unsigned)m) {
-                            const T kz = ro(L.K1 + (int64_t)z * W + (2 * P - jz));
-                            const T mz = ro(L.M1 + (int64_t)z * W + (2 * P - jz));
-#pragma unroll
-                            for (int j = 0; j < YT; ++j) {
-                                T& r = ring[j][(u + 1 + jz) % W];
-                                r = fmaT(kz, a[j], r);
-                                r = fmaT(mz, bb2[j], r);
-                            }
-                        }
-                    }
-                    const int zo = zp - P;
-#pragma unroll
-                    for (int j = 0; j < YT; ++j) {
-                        T& r = ring[j][(u + 1) % W];
-                        const int gy = y0 + j;
-                        if (own && zo >= zc0 && zo < zend && gy < m) {
-                            const int64_t oi = (int64_t)zo * mm + (int64_t)gy * m + gx;
-                            const int ri = L.rowinfo[oi];
-                            if (ri < 0) {
-                                const T y = (ri == -1) ? r * ro(L.s + oi) : T(0);
-                                if (MODE == APPLY) {
-                                    out[oi] = y;
-                                } else {
-                                    const T rr = (ri == -2) ? T(0) : rin[oi] - y;
-                                    out[oi] = rr;
-                                    if (MODE == RESID_SMOOTH && ri == -1)
-                                        xs[oi] = fmaT(gamma * ro(L.dinv + oi), rr, xs[oi]);
-                                }
-                            }
-                        }
-                        r = T(0);
-                    }
-                }
-            }
-            asm volatile("cp.async.wait_group 0;" ::: "memory");   // the ring is free for the next task
-        } else {
-            // ---------------- stored rows: 256 consecutive stored row ids, one per thread
-            const int64_t k = (int64_t)(t - sh.ntensor) * TPB + threadIdx.x;
-            if (k < L.nb) {
-                const int64_t oi = L.band_row[k];
-                const int ix = (int)(oi % m), iy = (int)((oi / m) % m), iz = (int)(oi / mm);
-                const T* __restrict__ c = L.band_coef + k;
-                const int64_t nb = L.nb;
-                T y = T(0);
-#pragma unroll
-                for (int oz = 0; oz < W; ++oz) {
-                    const bool zin = (unsigned)(iz + oz - P) < (unsigned)m;
-#pragma unroll
-                    for (int oy = 0; oy < W; ++oy) {
-                        const bool yin = zin && (unsigned)(iy + oy - P) < (unsigned)m;
-#pragma unroll
-                        for (int ox = 0; ox < W; ++ox) {
-                            const bool in = yin && (unsigned)(ix + ox - P) < (unsigned)m;
-                            const int64_t g = oi + (ox - P) + (int64_t)(oy - P) * m + (int64_t)(oz - P) * mm;
-                            y = fmaT(ro(c + (int64_t)(ox + W * (oy + W * oz)) * nb), in ? x[g] : T(0), y);
-                        }
-                    }
-                }
-                if (MODE == APPLY) {
-                    out[oi] = y;
-                } else {
-                    const T rr = rin[oi] - y;
-                    out[oi] = rr;
-                    if (MODE == RESID_SMOOTH) xs[oi] = fmaT(gamma * ro(L.dinv + oi), rr, xs[oi]);
-                }
-            }
-        }
-    }
-    // every CTA has drawn past the end once; the last one re-arms the counter
-    if (threadIdx.x == 0 && atomicAdd(&L.tile_ctr[1], 1u) == gridDim.x - 1) {
-        L.tile_ctr[0] = 0u;
-        L.tile_ctr[1] = 0u;
     }
 }
 
@@ -1224,330 +730,6 @@ __global__ void __launch_bounds__(TPB) k_coarse(const int32_t* __restrict__ rows
                     ((int64_t)gridDim.x * blockDim.x) >> 5, threadIdx.x & 31);
 }
 
-// ---------------------------------------------------------------------------------
-// Coarse part of the FP32 V-cycle with the levels resident in distributed shared memory
-// (see DsLevel).  Same arithmetic, in the same order, as the separate kernels above; only
-// where the data lives differs.
-namespace ds {
-
-struct Ctx {
-    unsigned char* sm;
-    unsigned char* const* bases;   // generic address of every block's shared memory
-    unsigned rank;
-};
-
-// row j of the common per-row vector at `off` of level L (any block's chunk)
-__device__ __forceinline__ float* at(const Ctx& c, const DsLevel& L, uint32_t off, int64_t j) {
-    const int64_t l = j - (int64_t)c.rank * L.ch;
-    if ((uint64_t)l < (uint64_t)L.ch) return reinterpret_cast<float*>(c.sm + off) + l;
-    const unsigned owner = (unsigned)((uint32_t)j / (uint32_t)L.ch);
-    return reinterpret_cast<float*>(c.bases[owner] + off) + (j - (int64_t)owner * L.ch);
-}
-
-template <typename U>
-__device__ __forceinline__ const U* tab(const Ctx& c, uint32_t off) {
-    return reinterpret_cast<const U*>(c.sm + off);
-}
-
-// A row segment [j0, j0 + len) of a common vector: a plain shared-memory pointer when the
-// segment lies in this block's chunk (the usual case), else nullptr (element-wise path).
-__device__ __forceinline__ const float* seg(const Ctx& c, const DsLevel& L, uint32_t off, int j0, int len) {
-    const int l = j0 - (int)c.rank * L.ch;
-    return (l >= 0 && l + len <= L.ch) ? reinterpret_cast<const float*>(c.sm + off) + l : nullptr;
-}
-
-// (A v)_i in scaled variables for own row i (local index il); v = the vector at off_v.
-// Indices are 32-bit (levels on the cluster hold far fewer than 2^31 rows); the (2p+1)
-// values of one grid line are read through one segment pointer.
-template <int DIM, int P>
-__device__ __forceinline__ float row_apply(const Ctx& c, const DsLevel& L, int64_t i64, int il, uint32_t off_v) {
-    constexpr int W = 2 * P + 1;
-    constexpr int NC = (DIM == 2) ? W * W : W * W * W;
-    const int ri = tab<int32_t>(c, L.off_ri)[il];
-    if (ri == -2) return 0.f;
-    const int i = (int)i64;
-    const int m = L.m;
-    const int ix = i % m, iy = (i / m) % m, iz = (DIM == 3) ? i / (m * m) : 0;
-    const int sy = m, sz = m * m;
-    // valid x offsets of the row's lines
-    const int ox0 = max(-P, -ix), ox1 = min(P, m - 1 - ix);
-    float y = 0.f;
-    if (ri >= 0) {
-        const float* cf = tab<float>(c, L.off_coef) + ri * NC;
-#pragma unroll
-        for (int oz = (DIM == 3 ? -P : 0); oz <= (DIM == 3 ? P : 0); ++oz) {
-            if (DIM == 3 && (unsigned)(iz + oz) >= (unsigned)m) continue;
-#pragma unroll
-            for (int oy = -P; oy <= P; ++oy) {
-                if ((unsigned)(iy + oy) >= (unsigned)m) continue;
-                const int jc = i + oy * sy + (DIM == 3 ? oz * sz : 0);
-                const float* v = seg(c, L, off_v, jc - P, W);
-                const float* crow = cf + W * ((oy + P) + (DIM == 3 ? W * (oz + P) : 0)) + P;
-#pragma unroll
-                for (int ox = -P; ox <= P; ++ox) {
-                    if (ox < ox0 || ox > ox1) continue;
-                    const float xv = v ? v[ox + P] : *at(c, L, off_v, jc + ox);
-                    y = fmaf(crow[ox], xv, y);
-                }
-            }
-        }
-        return y;
-    }
-    const float* K1 = tab<float>(c, L.off_K1);
-    const float* M1 = tab<float>(c, L.off_M1);
-    float kx[W], mx[W];
-#pragma unroll
-    for (int o = 0; o < W; ++o) {
-        kx[o] = K1[ix * W + o];
-        mx[o] = M1[ix * W + o];
-    }
-#pragma unroll
-    for (int oz = (DIM == 3 ? -P : 0); oz <= (DIM == 3 ? P : 0); ++oz) {
-        if (DIM == 3 && (unsigned)(iz + oz) >= (unsigned)m) continue;
-        const float mz = (DIM == 3) ? M1[iz * W + oz + P] : 1.f, kz = (DIM == 3) ? K1[iz * W + oz + P] : 0.f;
-#pragma unroll
-        for (int oy = -P; oy <= P; ++oy) {
-            if ((unsigned)(iy + oy) >= (unsigned)m) continue;
-            const float my = M1[iy * W + oy + P], ky = K1[iy * W + oy + P];
-            const int jc = i + oy * sy + (DIM == 3 ? oz * sz : 0);
-            const float* v = seg(c, L, off_v, jc - P, W);
-            const float* sv = seg(c, L, L.off_s, jc - P, W);
-            float a = 0.f, b = 0.f;
-#pragma unroll
-            for (int ox = -P; ox <= P; ++ox) {
-                if (ox < ox0 || ox > ox1) continue;
-                const float xv = (v ? v[ox + P] : *at(c, L, off_v, jc + ox)) *
-                                 (sv ? sv[ox + P] : *at(c, L, L.off_s, jc + ox));
-                a = fmaf(kx[ox + P], xv, a);
-                b = fmaf(mx[ox + P], xv, b);
-            }
-            if (DIM == 2) {
-                y = fmaf(my, a, y);
-                y = fmaf(ky, b, y);
-            } else {
-                y = fmaf(my * mz, a, y);
-                y = fmaf(fmaf(ky, mz, my * kz), b, y);
-            }
-        }
-    }
-    return y * reinterpret_cast<const float*>(c.sm + L.off_s)[il];
-}
-
-// x += gamma A_j^{-1} r on the Schwarz blocks this block owns, one warp per block
-__device__ __forceinline__ void blocks(const Ctx& c, const DsLevel& L, uint32_t off_r, float gamma, float* rs) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int32_t* bptr = tab<int32_t>(c, L.off_bptr);
-    const int32_t* bvptr = tab<int32_t>(c, L.off_bvptr);
-    const int32_t* bidx = tab<int32_t>(c, L.off_bidx);
-    const float* bval = tab<float>(c, L.off_bval);
-    for (int b = warp; b < L.nblk; b += DS_TPB / 32) {
-        const int s0 = bptr[b], nj = bptr[b + 1] - s0;
-        const float* A = bval + bvptr[b];
-        for (int a = lane; a < nj; a += 32) rs[a] = *at(c, L, off_r, bidx[s0 + a]);
-        __syncwarp();
-        for (int a = lane; a < nj; a += 32) {
-            float acc = 0.f;
-            for (int q = 0; q < nj; ++q) acc = fmaf(A[q * nj + a], rs[q], acc);
-            atomicAdd(at(c, L, L.off_x, bidx[s0 + a]), gamma * acc);
-        }
-        __syncwarp();
-    }
-}
-
-// own rows: out = rin - A v (and x += gamma dinv out when smooth)
-template <int DIM, int P>
-__device__ __forceinline__ void resid(const Ctx& c, const DsLevel& L, uint32_t off_v, uint32_t off_rin,
-                                      uint32_t off_out, bool smooth, float gamma) {
-    const int64_t lo = (int64_t)c.rank * L.ch;
-    const int32_t* ri = tab<int32_t>(c, L.off_ri);
-    const float* dinv = tab<float>(c, L.off_dinv);
-    float* rin = reinterpret_cast<float*>(c.sm + off_rin);
-    float* out = reinterpret_cast<float*>(c.sm + off_out);
-    float* x = reinterpret_cast<float*>(c.sm + L.off_x);
-    for (int l = threadIdx.x; l < L.ch && lo + l < L.N; l += DS_TPB) {
-        const float ax = row_apply<DIM, P>(c, L, lo + l, l, off_v);
-        const float v = (ri[l] == -2) ? 0.f : rin[l] - ax;
-        out[l] = v;
-        if (smooth) x[l] = fmaf(gamma * dinv[l], v, x[l]);
-    }
-}
-
-// own coarse rows of C: r_C = R t_F (scaled), x_C = gamma dinv_C r_C (or 0 on level 1)
-template <int DIM, int P>
-__device__ __forceinline__ void restrict_(const Ctx& c, const DsLevel& F, const DsLevel& C, float gamma, bool diag) {
-    constexpr int P2 = P + 2;
-    const int64_t lo = (int64_t)c.rank * C.ch;
-    const int mc = C.m, mf = F.m;
-    const int32_t* rfirst = tab<int32_t>(c, F.off_rfirst);
-    const float* rw = tab<float>(c, F.off_rw);
-    const int32_t* cri = tab<int32_t>(c, C.off_ri);
-    const float* cdinv = tab<float>(c, C.off_dinv);
-    float* rc = reinterpret_cast<float*>(c.sm + C.off_r);
-    float* xc = reinterpret_cast<float*>(c.sm + C.off_x);
-    const float* cs = reinterpret_cast<const float*>(c.sm + C.off_s);
-    for (int l = threadIdx.x; l < C.ch && lo + l < C.N; l += DS_TPB) {
-        const int64_t i = lo + l;
-        const int cx = (int)(i % mc), cy = (int)((i / mc) % mc), cz = (DIM == 3) ? (int)(i / ((int64_t)mc * mc)) : 0;
-        const int fx = rfirst[cx], fy = rfirst[cy], fz = (DIM == 3) ? rfirst[cz] : 0;
-        const float* wx = rw + cx * P2;
-        const float* wy = rw + cy * P2;
-        const float* wz = rw + cz * P2;
-        float s = 0.f;
-#pragma unroll
-        for (int kz = 0; kz < (DIM == 3 ? P2 : 1); ++kz) {
-            const float wzk = (DIM == 3) ? wz[kz] : 1.f;
-#pragma unroll
-            for (int ky = 0; ky < P2; ++ky) {
-                const float wyz = wy[ky] * wzk;
-                const int64_t rb = (int64_t)fx + (int64_t)mf * ((fy + ky) + (DIM == 3 ? (int64_t)mf * (fz + kz) : 0));
-                float t = 0.f;
-#pragma unroll
-                for (int kx = 0; kx < P2; ++kx)
-                    t = fmaf(wx[kx], *at(c, F, F.off_t, rb + kx) * *at(c, F, F.off_d, rb + kx), t);
-                s = fmaf(wyz, t, s);
-            }
-        }
-        s *= cs[l];
-        if (cri[l] == -2) s = 0.f;
-        rc[l] = s;
-        xc[l] = diag ? gamma * cdinv[l] * s : 0.f;
-    }
-}
-
-// own fine rows of F: e_F = R^T x_C (scaled), x_F += e_F
-template <int DIM>
-__device__ __forceinline__ void prolong(const Ctx& c, const DsLevel& F, const DsLevel& C) {
-    const int64_t lo = (int64_t)c.rank * F.ch;
-    const int mc = C.m, mf = F.m, TW = F.TW;
-    const int32_t* tfirst = tab<int32_t>(c, F.off_tfirst);
-    const float* tw = tab<float>(c, F.off_tw);
-    const int32_t* fri = tab<int32_t>(c, F.off_ri);
-    float* e = reinterpret_cast<float*>(c.sm + F.off_e);
-    float* x = reinterpret_cast<float*>(c.sm + F.off_x);
-    const float* fd = reinterpret_cast<const float*>(c.sm + F.off_d);
-    for (int l = threadIdx.x; l < F.ch && lo + l < F.N; l += DS_TPB) {
-        const int64_t a = lo + l;
-        const int ax = (int)(a % mf), ay = (int)((a / mf) % mf), az = (DIM == 3) ? (int)(a / ((int64_t)mf * mf)) : 0;
-        const int cx = tfirst[ax], cy = tfirst[ay], cz = (DIM == 3) ? tfirst[az] : 0;
-        const float* wx = tw + ax * TW;
-        const float* wy = tw + ay * TW;
-        const float* wz = tw + az * TW;
-        float s = 0.f;
-        for (int tz = 0; tz < (DIM == 3 ? TW : 1); ++tz) {
-            const float wzk = (DIM == 3) ? wz[tz] : 1.f;
-            for (int ty = 0; ty < TW; ++ty) {
-                const float wyz = wy[ty] * wzk;
-                const int64_t rb = (int64_t)cx + (int64_t)mc * ((cy + ty) + (DIM == 3 ? (int64_t)mc * (cz + tz) : 0));
-                float t = 0.f;
-                for (int tx = 0; tx < TW; ++tx)
-                    t = fmaf(wx[tx], *at(c, C, C.off_x, rb + tx) * *at(c, C, C.off_s, rb + tx), t);
-                s = fmaf(wyz, t, s);
-            }
-        }
-        s *= fd[l];
-        const bool inactive = fri[l] == -2;
-        if (inactive) s = 0.f;
-        e[l] = s;
-        if (!inactive) x[l] += s;
-    }
-}
-
-// x_0 = C r_0 on the kept rows of level 1, rows spread over the warps of the cluster
-__device__ __forceinline__ void coarse(const Ctx& c, const DsLevel& L, const int32_t* rows, const float* Cinv, int nc,
-                                       unsigned cs) {
-    const int lane = threadIdx.x & 31;
-    const int w = (int)c.rank * (DS_TPB / 32) + (threadIdx.x >> 5), nw = (int)cs * (DS_TPB / 32);
-    for (int a = w; a < nc; a += nw) {
-        const float* row = Cinv + (int64_t)a * nc;
-        double acc = 0.0;
-        for (int b = lane; b < nc; b += 32) acc = fma((double)ro(row + b), (double)*at(c, L, L.off_r, ro(rows + b)), acc);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-        if (lane == 0) *at(c, L, L.off_x, ro(rows + a)) = (float)acc;
-    }
-}
-
-}  // namespace ds
-
-template <int DIM, int P>
-__global__ void __launch_bounds__(DS_TPB) k_vcycle_dsmem(const DsVcycle V) {
-    extern __shared__ __align__(16) unsigned char sm[];
-    __shared__ unsigned char* bases[32];
-    cg::cluster_group cl = cg::this_cluster();
-    const unsigned rank = cl.block_rank();
-    const int tid = threadIdx.x;
-    // static data first: this block's image and its rows' scales (independent of the
-    // kernels before this one, so read before waiting on them)
-    {
-        const uint4* src = reinterpret_cast<const uint4*>(V.images + (size_t)rank * V.image_bytes);
-        uint4* dst = reinterpret_cast<uint4*>(sm + V.vec_bytes);
-        for (uint32_t k = tid; k < V.image_bytes / 16; k += DS_TPB) dst[k] = __ldg(src + k);
-        if (tid < V.cs) bases[tid] = reinterpret_cast<unsigned char*>(cl.map_shared_rank(reinterpret_cast<void*>(sm), tid));
-    }
-    __syncthreads();
-    const DsImage& I = *reinterpret_cast<const DsImage*>(sm + V.vec_bytes);
-    const ds::Ctx c{sm, bases, rank};
-    const int top = V.top;
-    for (int li = 0; li <= top; ++li) {
-        const DsLevel& L = I.lv[li];
-        const int64_t lo = (int64_t)rank * L.ch;
-        float* s = reinterpret_cast<float*>(sm + L.off_s);
-        float* d = reinterpret_cast<float*>(sm + L.off_d);
-        for (int l = tid; l < L.ch; l += DS_TPB) {
-            const bool in = lo + l < L.N;
-            s[l] = in ? __ldg(V.s_glob[li] + lo + l) : 0.f;
-            d[l] = in ? __ldg(V.d_glob[li] + lo + l) : 0.f;
-        }
-        if (li == 0) {
-            float* x0 = reinterpret_cast<float*>(sm + L.off_x);
-            for (int l = tid; l < L.ch; l += DS_TPB) x0[l] = 0.f;
-        }
-    }
-    pdl_begin();
-    {
-        const DsLevel& T = I.lv[top];
-        const int64_t lo = (int64_t)rank * T.ch;
-        float* x = reinterpret_cast<float*>(sm + T.off_x);
-        float* r = reinterpret_cast<float*>(sm + T.off_r);
-        for (int l = tid; l < T.ch; l += DS_TPB) {
-            const bool in = lo + l < T.N;
-            x[l] = in ? V.x_top[lo + l] : 0.f;
-            r[l] = in ? V.r_top[lo + l] : 0.f;
-        }
-    }
-    float* rs = reinterpret_cast<float*>(sm + I.scratch_off) + (tid >> 5) * I.max_block;
-    const float g = I.gamma;
-    cl.sync();
-    for (int li = top; li >= 1; --li) {
-        const DsLevel& F = I.lv[li];
-        ds::blocks(c, F, F.off_r, g, rs);
-        cl.sync();
-        ds::resid<DIM, P>(c, F, F.off_x, F.off_r, F.off_t, false, g);
-        cl.sync();
-        ds::restrict_<DIM, P>(c, F, I.lv[li - 1], g, li - 1 >= 1);
-        cl.sync();
-    }
-    ds::coarse(c, I.lv[0], V.c_rows, V.c_inv, V.nc, (unsigned)V.cs);
-    for (int li = 1; li <= top; ++li) {
-        const DsLevel& F = I.lv[li];
-        cl.sync();
-        ds::prolong<DIM>(c, F, I.lv[li - 1]);
-        cl.sync();
-        ds::resid<DIM, P>(c, F, F.off_e, F.off_t, F.off_t, true, g);
-        cl.sync();
-        ds::blocks(c, F, F.off_t, g, rs);
-    }
-    cl.sync();     // every block's scatter into the top level is done
-    {
-        const DsLevel& T = I.lv[top];
-        const int64_t lo = (int64_t)rank * T.ch;
-        const float* x = reinterpret_cast<const float*>(sm + T.off_x);
-        for (int l = tid; l < T.ch && lo + l < T.N; l += DS_TPB) V.x_top[lo + l] = x[l];
-    }
-    cl.sync();     // no block leaves while others may still read its shared memory
-}
-
-
 // V-cycle input from an FP64 residual: r_lo = (TZ)(rs .* r) (or (TZ) r), xv = gamma dinv .* r_lo
 template <typename TZ>
 __global__ void __launch_bounds__(TPB) k_vcycle_in(int64_t N, const double* __restrict__ r, const TZ* __restrict__ rs,
@@ -1817,61 +999,6 @@ __global__ void k_set_continue(PcgState* st, cudaGraphConditionalHandle handle) 
     cudaGraphSetConditional(handle, st->done ? 0u : 1u);
 }
 
-thread_local bool t_pdl = true;
-thread_local int64_t t_launches = 0;   // kernels issued by this host thread
-
-// Whether the next launch on s may carry the programmatic-serialisation attribute: always
-// outside stream capture; under capture only when every node it will depend on is a
-// kernel node (a programmatic edge joins two kernels).
-bool pdl_allowed(cudaStream_t s) {
-    if (!t_pdl) return false;
-    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-    const cudaGraphNode_t* deps = nullptr;
-    size_t nd = 0;
-    if (cudaStreamGetCaptureInfo(s, &cs, nullptr, nullptr, &deps, nullptr, &nd) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    if (cs != cudaStreamCaptureStatusActive) return true;
-    for (size_t k = 0; k < nd; ++k) {
-        cudaGraphNodeType t;
-        if (cudaGraphNodeGetType(deps[k], &t) != cudaSuccess || t != cudaGraphNodeTypeKernel) {
-            cudaGetLastError();
-            return false;
-        }
-    }
-    return true;
-}
-
-// Every kernel goes through here: programmatic stream serialisation lets the kernel
-// launch while its predecessor drains (each kernel starts with pdl_begin()).
-template <typename... KArgs, typename... Args>
-cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args&&... args) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = grid;
-    cfg.blockDim = block;
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = pdl_allowed(s) ? 1 : 0;
-    ++t_launches;
-    return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
-}
-
-int num_sms() {
-    static int sms = 0;
-    if (sms == 0) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (sms <= 0) sms = 148;
-    }
-    return sms;
-}
-
 // One row per thread.  Large levels: 256-thread blocks.  Small levels: blocks just big
 // enough to give every SM about two of them, so that the work is spread over the whole
 // GPU instead of a handful of SMs (FP64 issues 2 FMA/clk per SM).
@@ -1891,142 +1018,6 @@ inline RowLaunch row_launch(int64_t n) {
 }
 
 inline int tiles_2d(int m) { return ((m + TX - 1) / TX) * ((m + TY - 1) / TY); }
-// 3-D operator apply: the z-marching warp kernel on levels with enough work to fill the
-// GPU (IMGM_TILE3D=1: on every level, for testing it on small grids; IMGM_ZM_BLOCKS=k
-// caps its grid at k blocks, so that warps draw many tasks on small grids)
-// Task shape of a level: strips of 32 - 2P columns, segments of yt rows, and z chunks of
-// equal size, as long as possible (each chunk recomputes the plane passes of 2P halo
-// planes) while there are at least ZM_TASKS tensor tasks to spread over the warps (a
-// task is one warp's sequential walk, so too few tasks leave the SMs latency-bound),
-// and no shorter than ZM_ZMIN planes.  IMGM_ZM_ZC / IMGM_ZM_ZMIN override the two limits.
-constexpr int ZM_TASKS = 3600, ZM_ZMIN = 4, ZM_ZMAX = 32;
-ZmShape zm_shape(int m, int64_t nb, int P, int yt, int zc_set) {
-    ZmShape s{};
-    const int xs = 32 - 2 * P;
-    s.sx = (m + xs - 1) / xs;
-    s.sy = (m + yt - 1) / yt;
-    int zmin = ZM_ZMIN, zmax = ZM_ZMAX;
-    if (const char* v = std::getenv("IMGM_ZM_ZMIN")) zmin = std::max(1, std::atoi(v));
-    const int want = (ZM_TASKS + s.sx * s.sy - 1) / (s.sx * s.sy);     // chunks for enough tasks
-    int zc = std::max(zmin, std::min(zmax, (m + want - 1) / want));
-    if (zc_set > 0) zc = zc_set;
-    if (const char* v = std::getenv("IMGM_ZM_ZC")) zc = std::max(1, std::atoi(v));
-    const int nz = (m + zc - 1) / zc;
-    s.zc = (m + nz - 1) / nz;
-    s.sz = (m + s.zc - 1) / s.zc;
-    s.ntensor = (unsigned)((int64_t)s.sx * s.sy * s.sz);
-    s.ntotal = s.ntensor + (unsigned)((nb + 31) / 32);
-    return s;
-}
-bool use_zm_3d(int m) {
-    const char* v = std::getenv("IMGM_TILE3D");
-    static const int mmin = [] {
-        const char* w = std::getenv("IMGM_ZM_MIN_M");
-        return w ? std::atoi(w) : 18;
-    }();
-    return (v && v[0] == '1') || m >= mmin;
-}
-// rows per lane: two on large levels (fewer loads per row), one where the level needs the
-// extra tasks (IMGM_ZM_YT overrides)
-int zm_yt(int m, int yt_set) {
-    if (const char* v = std::getenv("IMGM_ZM_YT")) return std::atoi(v) == 1 ? 1 : 2;
-    if (yt_set == 1 || yt_set == 2) return yt_set;
-    return m >= 100 ? 2 : 1;
-}
-int zm_grid(const ZmShape& sh, int cap) {
-    int64_t g = std::min<int64_t>((sh.ntotal + TPB / 32 - 1) / (TPB / 32), cap);
-    if (const char* v = std::getenv("IMGM_ZM_BLOCKS")) {
-        const int k = std::atoi(v);
-        if (k > 0) g = std::min<int64_t>(g, k);
-    }
-    return (int)std::max<int64_t>(g, 1);
-}
-
-// dynamic shared memory of the z-marching apply: the FP32 instances' plane rings
-template <typename T, int P, int YT, bool STG>
-constexpr size_t zm_smem() {
-    return (sizeof(T) == 4 && STG) ? (size_t)(TPB / 32) * (2 * P + 1) * 2 * (YT + 2 * P) * 32 * sizeof(float) : 0;
-}
-
-template <typename T, int P, int YT, bool STG>
-void launch_zm3d_stg(const DevLevelT<T>& L, int mode, const T* x, const T* rin, T* out, T* xs, T gamma,
-                     const int* done, cudaStream_t s) {
-    const ZmShape sh = zm_shape(L.m, L.nb, P, YT, L.zm_zc);
-    const int g = zm_grid(sh, zm_blocks_per_sm<T>() * num_sms());
-    constexpr size_t smem = zm_smem<T, P, YT, STG>();
-    if (smem > 48 * 1024) {
-        static bool attr = false;                      // opted in once per instantiation
-        if (!attr) {
-            cudaFuncSetAttribute(k_apply_zm3d<T, P, APPLY, false, YT, STG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem);
-            cudaFuncSetAttribute(k_apply_zm3d<T, P, RESID, false, YT, STG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem);
-            cudaFuncSetAttribute(k_apply_zm3d<T, P, RESID_SMOOTH, false, YT, STG>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            attr = true;
-        }
-    }
-    if (mode == APPLY)
-        launch_pdl(k_apply_zm3d<T, P, APPLY, false, YT, STG>, g, TPB, smem, s, L, x, rin, out, xs, gamma, done, nullptr,
-                   nullptr, sh);
-    else if (mode == RESID)
-        launch_pdl(k_apply_zm3d<T, P, RESID, false, YT, STG>, g, TPB, smem, s, L, x, rin, out, xs, gamma, done, nullptr,
-                   nullptr, sh);
-    else
-        launch_pdl(k_apply_zm3d<T, P, RESID_SMOOTH, false, YT, STG>, g, TPB, smem, s, L, x, rin, out, xs, gamma, done,
-                   nullptr, nullptr, sh);
-}
-
-// the CTA form (FP32): strips x CTA row blocks of 8 YT rows x z chunks, stored rows in tasks of 256
-template <int P, int YT>
-void launch_zmc3d(const DevLevelT<float>& L, int mode, const float* x, const float* rin, float* out, float* xs,
-                  float gamma, const int* done, cudaStream_t s) {
-    ZmShape sh = zm_shape(L.m, L.nb, P, 8 * YT, L.zm_zc);
-    sh.ntotal = sh.ntensor + (unsigned)((L.nb + TPB - 1) / TPB);
-    int64_t g = std::min<int64_t>(sh.ntotal, 3 * num_sms());
-    if (const char* v = std::getenv("IMGM_ZM_BLOCKS")) {
-        const int k = std::atoi(v);
-        if (k > 0) g = std::min<int64_t>(g, k);
-    }
-    g = std::max<int64_t>(g, 1);
-    constexpr size_t smem = zmc_smem<P, YT>();
-    static_assert(zmc_smem<P, YT>() <= 48 * 1024, "CTA ring within the default shared memory");
-    if (mode == APPLY)
-        launch_pdl(k_apply_zmc3d<P, APPLY, YT>, (int)g, TPB, smem, s, L, x, rin, out, xs, gamma, done, sh);
-    else if (mode == RESID)
-        launch_pdl(k_apply_zmc3d<P, RESID, YT>, (int)g, TPB, smem, s, L, x, rin, out, xs, gamma, done, sh);
-    else
-        launch_pdl(k_apply_zmc3d<P, RESID_SMOOTH, YT>, (int)g, TPB, smem, s, L, x, rin, out, xs, gamma, done, sh);
-}
-
-// FP32 levels take the form the autotuner chose (0 registers, 1 warp-staged, 2 CTA-staged);
-// FP64 the register form
-template <typename T, int P, int YT>
-void launch_zm3d_yt(const DevLevelT<T>& L, int mode, const T* x, const T* rin, T* out, T* xs, T gamma, const int* done,
-                    cudaStream_t s) {
-    if constexpr (sizeof(T) == 4) {
-        if (L.zm_stage == 2) {
-            launch_zmc3d<P, YT>(L, mode, x, rin, out, xs, gamma, done, s);
-            return;
-        }
-    }
-    if (sizeof(T) == 4 && L.zm_stage)
-        launch_zm3d_stg<T, P, YT, true>(L, mode, x, rin, out, xs, gamma, done, s);
-    else
-        launch_zm3d_stg<T, P, YT, false>(L, mode, x, rin, out, xs, gamma, done, s);
-}
-
-template <typename T, int P>
-cudaError_t launch_zm3d(const DevLevelT<T>& L, int mode, const T* x, const T* rin, T* out, T* xs, T gamma,
-                        const int* done, cudaStream_t s) {
-    if (L.tile_ctr == nullptr || (L.nb > 0 && L.band_row == nullptr)) return cudaErrorInvalidValue;
-    if (zm_yt(L.m, L.zm_yt) == 2)
-        launch_zm3d_yt<T, P, 2>(L, mode, x, rin, out, xs, gamma, done, s);
-    else
-        launch_zm3d_yt<T, P, 1>(L, mode, x, rin, out, xs, gamma, done, s);
-    return cudaGetLastError();
-}
-
 // blocks of a 2-D tile launch: one per tile, except the FP64 operator apply (the CG's A p,
 // and the standalone apply), whose two blocks per SM draw tiles from the level's counter.
 // In the residual modes of the V-cycle the extra loads per row favour more resident blocks.
@@ -2034,6 +1025,46 @@ template <typename T>
 inline int tile_grid(int m, int mode) {
     const int n = tiles_2d(m);
     return (sizeof(T) == 8 && mode == APPLY) ? std::min(n, 2 * num_sms()) : n;
+}
+
+// 2-D y-marching apply: strips of 32 - 2P columns x chunks of rows (the autotuner's, else a
+// rule like the 3-D one), stored rows in tasks of 32.  Only with IMGM_YM2D=1: on the 512^2
+// levels it measures slower than the tile kernel (finest FP64 apply 28.6 against 21.8 us),
+// since a 2-D row carries no y pass to save and the short walks are latency-bound.
+ZmShape ym_shape(int m, int64_t nb, int P, int zc_set) {
+    ZmShape s{};
+    const int xs = 32 - 2 * P;
+    s.sx = (m + xs - 1) / xs;
+    s.sy = 1;
+    const int want = (ZM_TASKS + s.sx - 1) / s.sx;
+    int zc = std::max(2, std::min(64, (m + want - 1) / want));
+    if (zc_set > 0) zc = zc_set;
+    const int nz = (m + zc - 1) / zc;
+    s.zc = (m + nz - 1) / nz;
+    s.sz = (m + s.zc - 1) / s.zc;
+    s.ntensor = (unsigned)((int64_t)s.sx * s.sz);
+    s.ntotal = s.ntensor + (unsigned)((nb + 31) / 32);
+    return s;
+}
+bool use_ym_2d(int) {
+    const char* v = std::getenv("IMGM_YM2D");
+    return v && v[0] == '1';
+}
+
+template <typename T, int P>
+cudaError_t launch_ym2d(const DevLevelT<T>& L, int mode, const T* x, const T* rin, T* out, T* xs, T gamma,
+                        const int* done, cudaStream_t s) {
+    if (L.tile_ctr == nullptr || (L.nb > 0 && L.band_row == nullptr)) return cudaErrorInvalidValue;
+    const ZmShape sh = ym_shape(L.m, L.nb, P, L.zm_zc);
+    const int g = zm_grid(sh, 2 * num_sms());
+    if (mode == APPLY)
+        launch_pdl(k_apply_ym2d<T, P, APPLY, false>, g, TPB, 0, s, L, x, rin, out, xs, gamma, done, nullptr, nullptr, sh);
+    else if (mode == RESID)
+        launch_pdl(k_apply_ym2d<T, P, RESID, false>, g, TPB, 0, s, L, x, rin, out, xs, gamma, done, nullptr, nullptr, sh);
+    else
+        launch_pdl(k_apply_ym2d<T, P, RESID_SMOOTH, false>, g, TPB, 0, s, L, x, rin, out, xs, gamma, done, nullptr,
+                   nullptr, sh);
+    return cudaGetLastError();
 }
 
 template <typename T, int P>
@@ -2052,7 +1083,10 @@ cudaError_t launch_tile2d(const DevLevelT<T>& L, int mode, const T* x, const T* 
 
 }  // namespace
 
-bool zm_applies(int m) { return use_zm_3d(m); }
+thread_local bool t_pdl = true;
+thread_local int64_t t_launches = 0;   // kernels issued by this host thread
+
+bool ym_applies(int m) { return use_ym_2d(m); }
 void set_programmatic_launch(bool on) { t_pdl = on; }
 int64_t launch_count() { return t_launches; }
 void add_launches(int64_t k) { t_launches += k; }
@@ -2077,10 +1111,11 @@ template <typename T>
 cudaError_t launch_apply(const DevLevelT<T>& L, int mode, const T* x, const T* rin, T* out, T* xs, double gamma,
                          const int* done, cudaStream_t s) {
     // tiles when there are enough of them to fill the GPU; one row per thread otherwise
-    if (L.dim == 3 && use_zm_3d(L.m)) {
-        if (L.p == 1) return launch_zm3d<T, 1>(L, mode, x, rin, out, xs, (T)gamma, done, s);
-        if (L.p == 2) return launch_zm3d<T, 2>(L, mode, x, rin, out, xs, (T)gamma, done, s);
-        if (L.p == 3) return launch_zm3d<T, 3>(L, mode, x, rin, out, xs, (T)gamma, done, s);
+    if (L.dim == 3 && zm_applies(L.m)) return apply_zm3d(L, mode, x, rin, out, xs, (T)gamma, done, s);
+    if (L.dim == 2 && use_ym_2d(L.m)) {
+        if (L.p == 1) return launch_ym2d<T, 1>(L, mode, x, rin, out, xs, (T)gamma, done, s);
+        if (L.p == 2) return launch_ym2d<T, 2>(L, mode, x, rin, out, xs, (T)gamma, done, s);
+        if (L.p == 3) return launch_ym2d<T, 3>(L, mode, x, rin, out, xs, (T)gamma, done, s);
     }
     if (L.dim == 2 && tiles_2d(L.m) >= num_sms()) {
         if (L.p == 1) return launch_tile2d<T, 1>(L, mode, x, rin, out, xs, (T)gamma, done, s);
@@ -2095,6 +1130,20 @@ cudaError_t launch_apply(const DevLevelT<T>& L, int mode, const T* x, const T* r
 
 cudaError_t launch_apply_pq(const DevLevel& L, const double* p, double* q, double* partial, PcgState* st,
                             cudaStream_t s) {
+    if (L.dim == 2 && use_ym_2d(L.m)) {
+        if (L.tile_ctr == nullptr || (L.nb > 0 && L.band_row == nullptr)) return cudaErrorInvalidValue;
+        const ZmShape sh = ym_shape(L.m, L.nb, L.p, L.zm_zc);
+        const int g = zm_grid(sh, std::min(2 * num_sms(), reduction_blocks()));
+        if (L.p == 1)
+            launch_pdl(k_apply_ym2d<double, 1, APPLY, true>, g, TPB, 0, s, L, p, nullptr, q, nullptr, 0.0, &st->done, partial, st, sh);
+        else if (L.p == 2)
+            launch_pdl(k_apply_ym2d<double, 2, APPLY, true>, g, TPB, 0, s, L, p, nullptr, q, nullptr, 0.0, &st->done, partial, st, sh);
+        else if (L.p == 3)
+            launch_pdl(k_apply_ym2d<double, 3, APPLY, true>, g, TPB, 0, s, L, p, nullptr, q, nullptr, 0.0, &st->done, partial, st, sh);
+        else
+            return cudaErrorInvalidValue;
+        return cudaGetLastError();
+    }
     if (L.dim == 2) {
         if (L.tile_ctr == nullptr) return cudaErrorInvalidValue;
         const int g = std::min(tile_grid<double>(L.m, APPLY), reduction_blocks());
@@ -2108,21 +1157,7 @@ cudaError_t launch_apply_pq(const DevLevel& L, const double* p, double* q, doubl
             return cudaErrorInvalidValue;
         return cudaGetLastError();
     }
-    if (L.dim == 3 && use_zm_3d(L.m)) {
-        if (L.tile_ctr == nullptr || (L.nb > 0 && L.band_row == nullptr)) return cudaErrorInvalidValue;
-        const int yt = zm_yt(L.m, L.zm_yt);
-        const ZmShape sh = zm_shape(L.m, L.nb, L.p, yt, L.zm_zc);
-        const int g = zm_grid(sh, std::min(2 * num_sms(), reduction_blocks()));
-#define IMGM_ZM_PQ(PP, YY) \
-    launch_pdl(k_apply_zm3d<double, PP, APPLY, true, YY, false>, g, TPB, 0, s, L, p, nullptr, q, nullptr, 0.0, &st->done, \
-               partial, st, sh)
-        if (L.p == 1) { if (yt == 2) IMGM_ZM_PQ(1, 2); else IMGM_ZM_PQ(1, 1); }
-        else if (L.p == 2) { if (yt == 2) IMGM_ZM_PQ(2, 2); else IMGM_ZM_PQ(2, 1); }
-        else if (L.p == 3) { if (yt == 2) IMGM_ZM_PQ(3, 2); else IMGM_ZM_PQ(3, 1); }
-        else return cudaErrorInvalidValue;
-#undef IMGM_ZM_PQ
-        return cudaGetLastError();
-    }
+    if (L.dim == 3 && zm_applies(L.m)) return apply_zm3d_pq(L, p, q, partial, st, s);
     IMGM_DISPATCH(L.dim, L.p, (launch_pdl(k_apply_pq<D, Q>, reduction_blocks(), TPB, 0, s, L, p, q, partial, st)));
     return cudaGetLastError();
 }
@@ -2248,66 +1283,6 @@ cudaError_t launch_coarse(const int32_t* rows, const T* Cinv, int nc, const T* r
     return cudaGetLastError();
 }
 
-int ds_cluster_size() {
-    static int cs = -1;
-    if (cs < 0) {
-        cs = 0;
-        const void* kerns[] = {(const void*)k_vcycle_dsmem<2, 1>, (const void*)k_vcycle_dsmem<2, 2>,
-                               (const void*)k_vcycle_dsmem<2, 3>, (const void*)k_vcycle_dsmem<3, 1>,
-                               (const void*)k_vcycle_dsmem<3, 2>, (const void*)k_vcycle_dsmem<3, 3>};
-        for (const void* k : kerns) {
-            if (cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) cudaGetLastError();
-            if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DS_SMEM_MAX) != cudaSuccess)
-                cudaGetLastError();
-        }
-        cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3(16, 1, 1);
-        cfg.blockDim = dim3(DS_TPB, 1, 1);
-        cfg.dynamicSmemBytes = DS_SMEM_MAX;
-        cudaLaunchAttribute attr;
-        attr.id = cudaLaunchAttributeClusterDimension;
-        attr.val.clusterDim.x = 16;
-        attr.val.clusterDim.y = 1;
-        attr.val.clusterDim.z = 1;
-        cfg.attrs = &attr;
-        cfg.numAttrs = 1;
-        int n = 0;
-        if (cudaOccupancyMaxPotentialClusterSize(&n, (const void*)k_vcycle_dsmem<2, 2>, &cfg) == cudaSuccess && n > 0)
-            cs = n >= 16 ? 16 : (n >= 8 ? 8 : 0);
-        else
-            cudaGetLastError();
-    }
-    return cs;
-}
-
-cudaError_t launch_vcycle_dsmem(int dim, int p, const DsVcycle& V, cudaStream_t s) {
-    if (V.cs <= 0 || V.cs != ds_cluster_size() || V.smem_bytes > DS_SMEM_MAX) return cudaErrorInvalidValue;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(V.cs, 1, 1);
-    cfg.blockDim = dim3(DS_TPB, 1, 1);
-    cfg.dynamicSmemBytes = V.smem_bytes;
-    cfg.stream = s;
-    cudaLaunchAttribute attr[2];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = V.cs;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[1].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = pdl_allowed(s) ? 2 : 1;
-    ++t_launches;
-#define IMGM_DS_CASE(D_, P_) \
-    if (dim == D_ && p == P_) return cudaLaunchKernelEx(&cfg, k_vcycle_dsmem<D_, P_>, V);
-    IMGM_DS_CASE(2, 1)
-    IMGM_DS_CASE(2, 2)
-    IMGM_DS_CASE(2, 3)
-    IMGM_DS_CASE(3, 1)
-    IMGM_DS_CASE(3, 2)
-    IMGM_DS_CASE(3, 3)
-#undef IMGM_DS_CASE
-    return cudaErrorInvalidValue;
-}
 
 
 template <typename TZ>

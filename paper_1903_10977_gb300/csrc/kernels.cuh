@@ -79,6 +79,8 @@ enum ApplyMode { APPLY = 0, RESID = 1, RESID_SMOOTH = 2 };
 // whether a 3-D level of m functions per direction takes the z-marching apply (whose task
 // shape, DevLevelT::zm_yt / zm_zc, the setup autotuner picks)
 bool zm_applies(int m);
+// whether a 2-D level takes the y-marching apply (rows per chunk: DevLevelT::zm_zc)
+bool ym_applies(int m);
 
 // y = A x (APPLY), out = rin - A x (RESID), or out = rin - A x followed by
 // xs += gamma * dinv .* out (RESID_SMOOTH).  `out` may alias `rin`.
