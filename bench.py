@@ -520,11 +520,24 @@ def run_learned(args, lib, torch, pr, S64, timed_solves, total_units, t64, res64
                                    "layer's (89 % of the algorithmic flops; all three layers run on the tensor cores)",
                     "frac_of_bf16_peak": (fwd_flops / (fwd_ms * 1e-3) / 1e12) / measured_peaks()["bf16_tflops"]
                     if measured_peaks().get("bf16_tflops") else None,
-                    "kernels": "k_pack, then k_conv_tcz for the 1->16, 16->16 and 16->1 layers (tcgen05 bf16 "
-                               "MMAs of N = 48 with the z taps folded in, FP32 accumulators sliding along z in "
-                               "tensor memory; channels zero-padded to 16)",
+                    "kernels": forward_kernels(),
                     "timing": "20 stream launches of the whole forward, CUDA events"},
     }
+
+
+def forward_kernels():
+    """The network's forward kernels for the IMGM_NET_TC setting the library reads."""
+    mode = os.environ.get("IMGM_NET_TC", "")
+    if mode.startswith("0"):
+        return "k_pack, then k_conv for the three layers (FP32 FMA on the CUDA cores)"
+    if mode == "48":
+        return ("k_pack, then k_conv_tcz for the 1->16, 16->16 and 16->1 layers (tcgen05 bf16 MMAs of N = 48 "
+                "with the z taps folded in, FP32 accumulators sliding along z in tensor memory; channels "
+                "zero-padded to 16)")
+    return ("k_pack, then k_conv16_tc for the 1->16, 16->16 and 16->1 layers (implicit GEMM on tcgen05: an "
+            "8 x 16 voxel patch (M = 128) x 16 output channels per MMA, K = 16 input channels per tap, 27 taps "
+            "into one FP32 accumulator in tensor memory; input planes staged by cp.async in a 4-plane ring; "
+            "channels zero-padded to 16)")
 
 
 def run_ours(args, rank, world, local_rank):

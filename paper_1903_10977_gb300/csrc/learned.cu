@@ -609,10 +609,12 @@ __global__ void __launch_bounds__(TC_THREADS) k_conv_tcz(const TIN* __restrict__
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(TCZ_COLS) : "memory");
 }
 
-// gw[tap][o][i] += sum_v dy[v][o] x[v + off_tap][i]
+// part[block][tap][o][i] = the block's share of sum_v dy[v][o] x[v + off_tap][i]; k_wsum adds
+// the blocks' shares to gw in block order, so the gradient of given inputs is the same bits in
+// every run (FP32 atomics would add them in whatever order the blocks finish)
 template <int CI, int CO>
 __global__ void __launch_bounds__(WTPB) k_wgrad(const float* __restrict__ dy, const uint16_t* __restrict__ x,
-                                                float* __restrict__ gw, int nx, int ny, int nz) {
+                                                float* __restrict__ part, int nx, int ny, int nz) {
     constexpr int P = CI * CO;
     constexpr int S = WTPB / P;
     static_assert(P * S == WTPB, "channel pairs must divide the block");
@@ -659,10 +661,19 @@ __global__ void __launch_bounds__(WTPB) k_wgrad(const float* __restrict__ dy, co
         }
     }
     if (slice == 0) {
+        float* __restrict__ out = part + (int64_t)blockIdx.x * (27 * P);
 #pragma unroll
-        for (int t = 0; t < 27; ++t)
-            if (acc[t] != 0.f) atomicAdd(&gw[(t * CO + co) * CI + ci], acc[t]);
+        for (int t = 0; t < 27; ++t) out[(t * CO + co) * CI + ci] = acc[t];
     }
+}
+
+// gw[k] += sum over the nb blocks of part[b][k], in block order
+__global__ void __launch_bounds__(RTPB) k_wsum(const float* __restrict__ part, int nb, int nw, float* __restrict__ gw) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nw) return;
+    float s = 0.f;
+    for (int b = 0; b < nb; ++b) s += part[(int64_t)b * nw + k];
+    gw[k] += s;
 }
 
 __device__ __forceinline__ double block_sum(double v, double* sh) {
@@ -895,6 +906,9 @@ cudaError_t NetWorkspace::ensure(int nx_, int ny_, int nz_, bool train_) {
             if ((e = cudaMalloc(&d3, n * sizeof(float))) != cudaSuccess) return e;
             if ((e = cudaMalloc(&d2, n * NET_C * sizeof(float))) != cudaSuccess) return e;
             if ((e = cudaMalloc(&d1, n * NET_C * sizeof(float))) != cudaSuccess) return e;
+            // per-block weight-gradient shares: at most 4 blocks per SM (grid_for) x 27 x 16 x 16
+            if ((e = cudaMalloc(&wpart, (size_t)4 * sm_count() * 27 * NET_C * NET_C * sizeof(float))) != cudaSuccess)
+                return e;
         }
         cap = n;
         train = train_;
@@ -904,11 +918,12 @@ cudaError_t NetWorkspace::ensure(int nx_, int ny_, int nz_, bool train_) {
 }
 
 void NetWorkspace::release() {
-    for (void* p : {(void*)a0, (void*)a1, (void*)a2, (void*)o, (void*)d3, (void*)d2, (void*)d1, (void*)partial, (void*)err})
+    for (void* p : {(void*)a0, (void*)a1, (void*)a2, (void*)o, (void*)d3, (void*)d2, (void*)d1, (void*)wpart,
+                    (void*)partial, (void*)err})
         if (p) cudaFree(p);
     a0 = a1 = a2 = nullptr;
     err = nullptr;
-    o = d3 = d2 = d1 = nullptr;
+    o = d3 = d2 = d1 = wpart = nullptr;
     partial = nullptr;
     cap = 0;
     train = false;
@@ -957,12 +972,14 @@ cudaError_t net_backward(const uint16_t* wbt, NetWorkspace& ws, const double* ta
     const int gc = grid_for(nvox, CTPB, 16);
     k_loss<<<elementwise_grid(nvox), RTPB, 0, s>>>(nvox, ws.o, target, mask, scale, ws.d3, loss);
     // layer 3: dW3 from (d3, a2); d2 = (W3^T d3) where a2 > 0
-    k_wgrad<NET_C, 1><<<grid_for(nvox, (WTPB / NET_C) * 32, 4), WTPB, 0, s>>>(ws.d3, ws.a2, grad + NET_OFF3, ws.nx,
-                                                                              ws.ny, ws.nz);
+    const int g13 = grid_for(nvox, (WTPB / NET_C) * 32, 4), g2 = grid_for(nvox, 32, 4);
+    k_wgrad<NET_C, 1><<<g13, WTPB, 0, s>>>(ws.d3, ws.a2, ws.wpart, ws.nx, ws.ny, ws.nz);
+    k_wsum<<<(27 * NET_C + RTPB - 1) / RTPB, RTPB, 0, s>>>(ws.wpart, g13, 27 * NET_C, grad + NET_OFF3);
     k_conv<1, NET_C, float, EPI_GATE><<<gc, CTPB, 0, s>>>(ws.d3, wbt + NET_OFF3, ws.a2, nullptr, nullptr, ws.d2,
                                                           nullptr, ws.nx, ws.ny, ws.nz);
     // layer 2: dW2 from (d2, a1); d1 = (W2^T d2) where a1 > 0
-    k_wgrad<NET_C, NET_C><<<grid_for(nvox, 32, 4), WTPB, 0, s>>>(ws.d2, ws.a1, grad + NET_OFF2, ws.nx, ws.ny, ws.nz);
+    k_wgrad<NET_C, NET_C><<<g2, WTPB, 0, s>>>(ws.d2, ws.a1, ws.wpart, ws.nx, ws.ny, ws.nz);
+    k_wsum<<<(27 * NET_C * NET_C + RTPB - 1) / RTPB, RTPB, 0, s>>>(ws.wpart, g2, 27 * NET_C * NET_C, grad + NET_OFF2);
     if (const int mode = net_tc_mode()) {
         cudaError_t e = conv_tc<float, NET_C, NET_C, EPI_GATE>(mode, ws, ws.d2, wbt + NET_OFF2, ws.a1, nullptr, nullptr,
                                                                ws.d1, nullptr, s);
@@ -972,9 +989,9 @@ cudaError_t net_backward(const uint16_t* wbt, NetWorkspace& ws, const double* ta
                                                                   ws.d1, nullptr, ws.nx, ws.ny, ws.nz);
     }
     // layer 1: dW1 from (d1, a0)
-    k_wgrad<1, NET_C><<<grid_for(nvox, (WTPB / NET_C) * 32, 4), WTPB, 0, s>>>(ws.d1, ws.a0, grad, ws.nx, ws.ny,
-                                                                              ws.nz);
-    add_launches(6);
+    k_wgrad<1, NET_C><<<g13, WTPB, 0, s>>>(ws.d1, ws.a0, ws.wpart, ws.nx, ws.ny, ws.nz);
+    k_wsum<<<(27 * NET_C + RTPB - 1) / RTPB, RTPB, 0, s>>>(ws.wpart, g13, 27 * NET_C, grad);
+    add_launches(9);
     return cudaGetLastError();
 }
 

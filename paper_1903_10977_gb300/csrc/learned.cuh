@@ -34,6 +34,7 @@ struct NetWorkspace {
     uint16_t *a0 = nullptr, *a1 = nullptr, *a2 = nullptr;   // input [v], hidden [v][16]
     float* o = nullptr;              // output [v] (training)
     float *d3 = nullptr, *d2 = nullptr, *d1 = nullptr;      // dL/d(out) [v], dL/d(a2), dL/d(a1) [v][16]
+    float* wpart = nullptr;          // per-block weight-gradient shares [block][27 x 16 x 16] (training)
     double* partial = nullptr;       // [2 * NET_PARTIALS]
     int* err = nullptr;              // set by a tensor-core convolution whose wait gave up
     cudaError_t ensure(int nx, int ny, int nz, bool train);
