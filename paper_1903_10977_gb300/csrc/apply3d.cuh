@@ -25,6 +25,35 @@ namespace {
 // level's counter; the last warp to finish re-arms it.  Modes as k_apply_tile2d.
 // output rows (y) per lane: a template parameter of the kernel (1 or 2), chosen per level
 
+// FP32 marching applies: the output row's table entry, Jacobi scale and input residual,
+// loaded at the start of the step that writes the row, so that these DRAM reads travel together
+// and their latency overlaps the step's plane arithmetic (read after it, behind the table entry,
+// they were two dependent DRAM round trips per step; the smoothing's diagonal and iterate stay
+// at the end, where keeping them across the step would spill registers).  ri = 0 (the id of a
+// stored row, written by the stored-row tasks) where the lane writes nothing.
+template <typename T, int MODE>
+struct OutRow {
+    int ri;
+    T s, rin;
+    __device__ __forceinline__ void load(const DevLevelT<T>& L, const T* rin_, bool w, int64_t oi) {
+        ri = w ? L.rowinfo[oi] : 0;
+        s = w ? ro(L.s + oi) : T(0);
+        rin = (MODE != APPLY && w) ? rin_[oi] : T(0);
+    }
+    // the row's output from its accumulated sum r (in scaled variables); returns y = (A x)_i
+    __device__ __forceinline__ T store(const DevLevelT<T>& L, T r, T* out, T* xs_, T gamma, int64_t oi) const {
+        const T y = (ri == -1) ? r * s : T(0);
+        if (MODE == APPLY) {
+            out[oi] = y;
+        } else {
+            const T rr = (ri == -2) ? T(0) : rin - y;
+            out[oi] = rr;
+            if (MODE == RESID_SMOOTH && ri == -1) xs_[oi] = fmaT(gamma * ro(L.dinv + oi), rr, xs_[oi]);
+        }
+        return y;
+    }
+};
+
 // blocks per SM the z-marching apply is compiled for: two in FP64 (its FP64 pipe is the
 // bound), four in FP32 (latency-bound: more resident warps hide the plane loads)
 template <typename T>
@@ -146,6 +175,15 @@ __global__ void __launch_bounds__(TPB, zm_blocks_per_sm<T>()) k_apply_zm3d(DevLe
                     const int k = base + u;
                     if (k >= nplanes) break;
                     const int zp = zc0 - P + k;                      // input plane
+                    OutRow<T, MODE> orow[YT];                        // FP32: this step's output rows
+                    if constexpr (SC) {
+#pragma unroll
+                        for (int j = 0; j < YT; ++j) {
+                            const int gy = y0 + j, zo = zp - P;
+                            const bool w = own && zo >= zc0 && zo < zend && gy < m;
+                            orow[j].load(L, rin, w, w ? (int64_t)zo * mm + (int64_t)gy * m + gx : 0);
+                        }
+                    }
                     T vn[NV];
                     if constexpr (staged) {
                         stage_plane(k + W - 1);                      // into the buffer of plane k - 1
@@ -232,10 +270,14 @@ __global__ void __launch_bounds__(TPB, zm_blocks_per_sm<T>()) k_apply_zm3d(DevLe
                         const int gy = y0 + j;
                         if (own && zo >= zc0 && zo < zend && gy < m) {
                             const int64_t oi = (int64_t)zo * mm + (int64_t)gy * m + gx;
-                            const int ri = L.rowinfo[oi];
-                            if (ri < 0) {                            // tensor row or inactive row
+                            if constexpr (SC) {
+                                if (orow[j].ri < 0) {
+                                    const T y = orow[j].store(L, r, out, xs, gamma, oi);
+                                    if (DOT && orow[j].ri == -1) acc = fma((double)x[oi], (double)y, acc);
+                                }
+                            } else if (const int ri = L.rowinfo[oi]; ri < 0) {   // tensor or inactive row
                                 T y = T(0);
-                                if (ri == -1) y = SC ? r * ro(L.s + oi) : r;
+                                if (ri == -1) y = r;
                                 if (MODE == APPLY) {
                                     out[oi] = y;
                                 } else {
@@ -412,6 +454,13 @@ __global__ void __launch_bounds__(TPB, 3) k_apply_zmc3d(DevLevelT<float> L, cons
                     const int k = base + u;
                     if (k >= nplanes) break;
                     const int zp = zc0 - P + k;
+                    OutRow<T, MODE> orow[YT];
+#pragma unroll
+                    for (int j = 0; j < YT; ++j) {
+                        const int gy = y0 + j, zo = zp - P;
+                        const bool w = own && zo >= zc0 && zo < zend && gy < m;
+                        orow[j].load(L, rin, w, w ? (int64_t)zo * mm + (int64_t)gy * m + gx : 0);
+                    }
                     asm volatile("cp.async.wait_group %0;" ::"n"(ZMC_DEPTH - 2) : "memory");   // own copies of k
                     __syncthreads();                 // everyone's copies of k; everyone done with k - 1
                     stage(k + ZMC_DEPTH - 1);        // into the buffer of plane k - 1
@@ -489,21 +538,8 @@ __global__ void __launch_bounds__(TPB, 3) k_apply_zmc3d(DevLevelT<float> L, cons
                     for (int j = 0; j < YT; ++j) {
                         T& r = ring[j][(u + 1) % W];
                         const int gy = y0 + j;
-                        if (own && zo >= zc0 && zo < zend && gy < m) {
-                            const int64_t oi = (int64_t)zo * mm + (int64_t)gy * m + gx;
-                            const int ri = L.rowinfo[oi];
-                            if (ri < 0) {
-                                const T y = (ri == -1) ? r * ro(L.s + oi) : T(0);
-                                if (MODE == APPLY) {
-                                    out[oi] = y;
-                                } else {
-                                    const T rr = (ri == -2) ? T(0) : rin[oi] - y;
-                                    out[oi] = rr;
-                                    if (MODE == RESID_SMOOTH && ri == -1)
-                                        xs[oi] = fmaT(gamma * ro(L.dinv + oi), rr, xs[oi]);
-                                }
-                            }
-                        }
+                        if (own && zo >= zc0 && zo < zend && gy < m && orow[j].ri < 0)
+                            orow[j].store(L, r, out, xs, gamma, (int64_t)zo * mm + (int64_t)gy * m + gx);
                         r = T(0);
                     }
                 }
