@@ -174,8 +174,9 @@ def test_learned_stage_arguments_checked_before_the_gpu():
     assert L.imgm_net_get_weights(None, None) == -1
     pr, lay, _, _ = oracle_for("disc1_32_p2")
     S = solver_for(lib, pr, lay, host_only=True)
+    assert L.imgm_set_fcg(None, 3) == -1
     for rc in (L.imgm_set_net(S._h, None), L.imgm_learned_stage(S._h, None, None, None, None),
-               L.imgm_learned_pair(S._h, None, None, None, None, None)):
+               L.imgm_learned_pair(S._h, None, None, None, None, None), L.imgm_set_fcg(S._h, 3)):
         assert rc == -1                                  # a host-only handle has no device data
     S.close()
 
