@@ -29,6 +29,8 @@ CASES = [
     ("discs10_512_p2", {"n": 64, "levels": 4}),
     ("discs10_512_p3", {"n": 64, "levels": 3}),
     ("spheres20_128_p2", {"n": 16, "levels": 2, "depth": 1}),  # 3-D, resized
+    ("spheres20_128_p2", {"n": 8, "levels": 2, "depth": 1, "degree": 1}),   # 3-D, linear
+    ("spheres20_128_p2", {"n": 8, "levels": 2, "depth": 1, "degree": 3}),   # 3-D, cubic
 ]
 
 
